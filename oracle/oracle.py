@@ -1,0 +1,277 @@
+"""FP64 CPU oracle (test infrastructure only; see the package docstring).
+
+Heavy loops (table quadrature, direct sums) live in ``lgf_oracle.c``; the
+staggered-grid operators of App. A and the residual are plain numpy.
+
+Conventions
+-----------
+* Dense boxes are numpy arrays indexed ``[z, y, x]`` (x fastest in memory);
+  vector fields carry a leading component axis ``q = 0, 1, 2`` for the
+  paper's superscripts (1), (2), (3), i.e. the x, y, z components.
+* Values outside a box are zero (the mask operator M of Sec. 4.2).
+* The unit-lattice LGF ``G`` is returned; the physical kernel is
+  ``G_L = dx**2 * G`` (reading of App. B: the 7-point Laplacian carries
+  ``1/dx**2``, so its fundamental solution carries ``dx**2``).
+"""
+from __future__ import annotations
+
+import ctypes
+import functools
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "lib", "gauss_legendre", "bessel_scaled", "lgf_octant", "lgf_cube", "lgf_value",
+    "octant_size", "asymptotic_G", "ifactor_taps", "ifactor_radius", "direct_conv",
+    "direct_conv_box", "ifactor_direct", "shift", "op_G", "op_Gt", "op_C", "op_Ct", "op_D",
+    "op_Dbar", "op_L", "op_N", "residual_L", "WATSON_W", "num_threads",
+]
+
+# Watson's integral for the simple cubic lattice, closed form (Watson 1939):
+#   W = sqrt(6) / (32 pi^3) * Gamma(1/24) Gamma(5/24) Gamma(7/24) Gamma(11/24)
+WATSON_W = (math.sqrt(6.0) / (32.0 * math.pi ** 3) * math.gamma(1 / 24) * math.gamma(5 / 24)
+            * math.gamma(7 / 24) * math.gamma(11 / 24))
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+
+
+@functools.lru_cache(maxsize=1)
+def lib() -> ctypes.CDLL:
+    path = _build.build()
+    L = ctypes.CDLL(path)
+    L.oracle_gauss_legendre.argtypes = [ctypes.c_int, _dp, _dp]
+    L.oracle_bessel_scaled.argtypes = [ctypes.c_double, ctypes.c_int, _dp]
+    L.oracle_octant_size.argtypes = [ctypes.c_int]
+    L.oracle_octant_size.restype = ctypes.c_int64
+    L.oracle_lgf_octant.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_int, _dp]
+    L.oracle_octant_to_cube.argtypes = [ctypes.c_int, _dp, _dp]
+    L.oracle_direct_conv.argtypes = [ctypes.c_int, _dp, ctypes.c_int64, _ip, _dp,
+                                     ctypes.c_int64, _ip, _dp]
+    L.oracle_ifactor_direct.argtypes = [ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, _dp, ctypes.c_int64, _ip, _dp]
+    return L
+
+
+def num_threads() -> int:
+    return int(lib().oracle_num_threads())
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _i(a):
+    return a.ctypes.data_as(_ip)
+
+
+def gauss_legendre(n: int):
+    x = np.zeros(n)
+    w = np.zeros(n)
+    lib().oracle_gauss_legendre(n, _d(x), _d(w))
+    return x, w
+
+
+def bessel_scaled(t: float, nmax: int) -> np.ndarray:
+    """exp(-2t) I_n(2t) for n = 0..nmax (Miller recurrence / Hankel series)."""
+    out = np.zeros(nmax + 1)
+    rc = lib().oracle_bessel_scaled(float(t), int(nmax), _d(out))
+    if rc != 0:
+        raise ValueError("bessel_scaled: bad arguments")
+    return out
+
+
+def octant_size(K: int) -> int:
+    return int(lib().oracle_octant_size(K))
+
+
+# Default quadrature: Gauss-Legendre in s = ln t on [ln 1e-18, ln 1e12],
+# panels of width 1, 16 nodes each, plus the closed-form tail beyond 1e12.
+QUAD_DEFAULT = dict(t_lo=1e-18, T=1e12, panel=1.0, ngl=16)
+
+
+@functools.lru_cache(maxsize=8)
+def lgf_octant(K: int, t_lo: float = QUAD_DEFAULT["t_lo"], T: float = QUAD_DEFAULT["T"],
+               panel: float = QUAD_DEFAULT["panel"], ngl: int = QUAD_DEFAULT["ngl"]) -> np.ndarray:
+    """Unit-lattice G on the sorted octant K >= a >= b >= c >= 0 (App. B, Bessel form)."""
+    out = np.zeros(octant_size(K))
+    rc = lib().oracle_lgf_octant(int(K), t_lo, T, panel, int(ngl), _d(out))
+    if rc != 0:
+        raise RuntimeError("oracle_lgf_octant failed (%d)" % rc)
+    out.setflags(write=False)
+    return out
+
+
+@functools.lru_cache(maxsize=4)
+def lgf_cube(K: int) -> np.ndarray:
+    """Dense table D[|dz|, |dy|, |dx|] = G(dx, dy, dz), 0..K on each axis."""
+    oct_ = np.ascontiguousarray(lgf_octant(K))
+    cube = np.zeros((K + 1, K + 1, K + 1))
+    lib().oracle_octant_to_cube(int(K), _d(oct_), _d(cube))
+    cube.setflags(write=False)
+    return cube
+
+
+def lgf_value(n, K: int | None = None) -> float:
+    a, b, c = sorted((abs(int(v)) for v in n), reverse=True)
+    if K is None:
+        K = max(a, 8)
+    oct_ = lgf_octant(K)
+    return float(oct_[a * (a + 1) * (a + 2) // 6 + b * (b + 1) // 2 + c])
+
+
+def asymptotic_G(n) -> np.ndarray:
+    """Two-term large-|n| expansion of the unit LGF (App. B)."""
+    n = np.asarray(n, dtype=float)
+    r2 = (n ** 2).sum(-1)
+    r = np.sqrt(r2)
+    n4 = (n ** 4).sum(-1)
+    cross = n[..., 0] ** 2 * n[..., 1] ** 2 + n[..., 0] ** 2 * n[..., 2] ** 2 + n[..., 1] ** 2 * n[..., 2] ** 2
+    return -1.0 / (4 * np.pi * r) - (n4 - 3 * cross) / (16 * np.pi * r ** 7)
+
+
+def ifactor_radius(alpha: float, tol: float = 1e-14) -> int:
+    """Largest on-axis offset r with g(r) g(0)^2 >= tol.
+
+    Reading of the truncation rule 'drop the kernel where |E_Q| < tol': the
+    retained support is the box |n_i| <= R (App. B eq. lgf_intfac)."""
+    g = bessel_scaled(alpha, 200)
+    r = 0
+    while r + 1 <= 200 and g[r + 1] * g[0] ** 2 >= tol:
+        r += 1
+    return r
+
+
+def ifactor_taps(alpha: float, tol: float = 1e-14) -> np.ndarray:
+    """1-D factors g(k) = exp(-2 alpha) I_k(2 alpha), k = 0..R (App. B eq. lgf_intfac)."""
+    R = ifactor_radius(alpha, tol)
+    return bessel_scaled(alpha, R)
+
+
+def direct_conv(cube: np.ndarray, src_xyz: np.ndarray, val: np.ndarray, tgt_xyz: np.ndarray) -> np.ndarray:
+    """u(t_j) = sum_i G(t_j - s_i) val_i (Sec. 2.2 eq. dpoisson_conv), FP64, unit lattice."""
+    K = cube.shape[0] - 1
+    cube = np.ascontiguousarray(cube, dtype=np.float64)
+    src = np.ascontiguousarray(src_xyz, dtype=np.int32).reshape(-1, 3)
+    tgt = np.ascontiguousarray(tgt_xyz, dtype=np.int32).reshape(-1, 3)
+    v = np.ascontiguousarray(val, dtype=np.float64).reshape(-1)
+    out = np.zeros(len(tgt))
+    rc = lib().oracle_direct_conv(K, _d(cube), len(src), _i(src), _d(v), len(tgt), _i(tgt), _d(out))
+    if rc != 0:
+        raise ValueError("direct_conv: offset beyond the table (K=%d)" % K)
+    return out
+
+
+def direct_conv_box(cube: np.ndarray, f: np.ndarray, tgt_xyz: np.ndarray, origin=(0, 0, 0)) -> np.ndarray:
+    """Direct sum with the source given as a dense box f[z, y, x] (zeros skipped)."""
+    z, y, x = np.nonzero(f)
+    src = np.stack([x, y, z], axis=1).astype(np.int32) + np.asarray(origin, dtype=np.int32)
+    return direct_conv(cube, src, f[z, y, x], tgt_xyz)
+
+
+def ifactor_direct(g: np.ndarray, x: np.ndarray, tgt_xyz: np.ndarray) -> np.ndarray:
+    """y(n) = sum_m prod_i g(|n_i - m_i|) x(m) over the box |n_i - m_i| <= R (plain 3-D sum)."""
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    tgt = np.ascontiguousarray(tgt_xyz, dtype=np.int32).reshape(-1, 3)
+    nz, ny, nx = x.shape
+    out = np.zeros(len(tgt))
+    lib().oracle_ifactor_direct(len(g) - 1, _d(g), nx, ny, nz, _d(x), len(tgt), _i(tgt), _d(out))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Staggered-grid operators, App. A point-operator forms.  Axis map: paper
+# component (1),(2),(3) = x,y,z = numpy axis 2,1,0 of a [z,y,x] array.
+# ---------------------------------------------------------------------------
+_AX = {0: 2, 1: 1, 2: 0}
+
+
+def shift(a: np.ndarray, q: int, s: int) -> np.ndarray:
+    """b(n) = a(n + s e_q) with zeros beyond the box (mask semantics)."""
+    ax = _AX[q]
+    b = np.zeros_like(a)
+    n = a.shape[ax]
+    if abs(s) >= n:
+        return b
+    src = [slice(None)] * a.ndim
+    dst = [slice(None)] * a.ndim
+    if s > 0:
+        src[ax] = slice(s, n)
+        dst[ax] = slice(0, n - s)
+    else:
+        src[ax] = slice(0, n + s)
+        dst[ax] = slice(-s, n)
+    b[tuple(dst)] = a[tuple(src)]
+    return b
+
+
+def op_G(c: np.ndarray, dx: float = 1.0) -> np.ndarray:
+    """cells -> faces: dx [G c]^(q)_n = c_{n+e_q} - c_n."""
+    return np.stack([(shift(c, q, 1) - c) / dx for q in range(3)])
+
+
+def op_Gt(f: np.ndarray, dx: float = 1.0) -> np.ndarray:
+    """faces -> cells, the adjoint of G:  G^T f = -Dbar f."""
+    return -op_Dbar(f, dx)
+
+
+def op_Dbar(f: np.ndarray, dx: float = 1.0) -> np.ndarray:
+    """faces -> cells: dx [Dbar f]_n = sum_q (f^(q)_n - f^(q)_{n-e_q})."""
+    return sum((f[q] - shift(f[q], q, -1)) for q in range(3)) / dx
+
+
+def op_C(f: np.ndarray, dx: float = 1.0) -> np.ndarray:
+    """faces -> edges: dx [C f]^(1) = f2_n - f2_{n+e3} + f3_{n+e2} - f3_n, cyclic in (1,2,3)."""
+    out = []
+    for q in range(3):
+        r, s = (q + 1) % 3, (q + 2) % 3
+        out.append((f[r] - shift(f[r], s, 1) + shift(f[s], r, 1) - f[s]) / dx)
+    return np.stack(out)
+
+
+def op_Ct(e: np.ndarray, dx: float = 1.0) -> np.ndarray:
+    """edges -> faces: dx [Cbar e]^(1) = e2_{n-e3} - e2_n + e3_n - e3_{n-e2}, cyclic."""
+    out = []
+    for q in range(3):
+        r, s = (q + 1) % 3, (q + 2) % 3
+        out.append((shift(e[r], s, -1) - e[r] + e[s] - shift(e[s], r, -1)) / dx)
+    return np.stack(out)
+
+
+def op_D(e: np.ndarray, dx: float = 1.0) -> np.ndarray:
+    """edges -> vertices: dx [D e]_n = sum_q (e^(q)_{n+e_q} - e^(q)_n)."""
+    return sum((shift(e[q], q, 1) - e[q]) for q in range(3)) / dx
+
+
+def op_L(a: np.ndarray, dx: float = 1.0) -> np.ndarray:
+    """7-point Laplacian: dx^2 [L a]_n = -6 a_n + sum_{q, +-1} a_{n +- e_q} (per component)."""
+    if a.ndim == 4:
+        return np.stack([op_L(a[q], dx) for q in range(a.shape[0])])
+    return (sum(shift(a, q, 1) + shift(a, q, -1) for q in range(3)) - 6.0 * a) / (dx * dx)
+
+
+def op_N(f: np.ndarray, dx: float = 1.0) -> np.ndarray:
+    """Rotational nonlinear term of App. A eq. opr_def_nonlin, e = C f:
+    [N f]^(1) = 1/4 sum_{m in {-1,0}} [ e2_{n+m e3} (f3 + f3_{+e1})_{n+m e3}
+                                         - e3_{n+m e2} (f2 + f2_{+e1})_{n+m e2} ], cyclic."""
+    e = op_C(f, dx)
+    out = []
+    for q in range(3):
+        r, s = (q + 1) % 3, (q + 2) % 3
+        a = e[r] * (f[s] + shift(f[s], q, 1))
+        b = e[s] * (f[r] + shift(f[r], q, 1))
+        out.append(0.25 * sum(shift(a, s, m) - shift(b, r, m) for m in (-1, 0)))
+    return np.stack(out)
+
+
+def residual_L(u: np.ndarray, f: np.ndarray, interior: np.ndarray, dx: float = 1.0) -> float:
+    """||L u - f||_2 / ||f||_2 over the points flagged `interior` (App. A stencil)."""
+    r = op_L(u, dx) - f
+    den = np.sqrt((f[interior] ** 2).sum())
+    return float(np.sqrt((r[interior] ** 2).sum()) / den)
