@@ -1,0 +1,166 @@
+/*
+ * lgf.h -- C-ABI of liblgf.so, a GB300 (sm_103a) implementation of the
+ * lattice-Green's-function (LGF) convolutions of Liska & Colonius,
+ * "A fast lattice Green's function method for solving viscous incompressible
+ * flows on unbounded domains".
+ *
+ * Two operations are provided, each the convolution of block-structured,
+ * compactly supported sources with a lattice Green's function:
+ *
+ *   Poisson   u(n) = scale * dx^2 * sum_m G(n - m) f(m)             (Sec. 2.2,
+ *             eq. dpoisson_conv), G the unit-lattice LGF of the 7-point
+ *             Laplacian (App. B, Bessel form), i.e. u = scale * L^{-1} f with
+ *             L = L_unit / dx^2 and zero values at infinity.  Vector problems
+ *             are solved per component (Sec. 2.2).
+ *   IF        y = M E_Q(alpha) M x                                 (Sec. 2.3
+ *             eq. if_def, App. B eq. lgf_intfac, Sec. 4.4): convolution with
+ *             the kernel prod_i exp(-2 alpha) I_{n_i}(2 alpha), truncated to the
+ *             box |n_i| <= R_alpha outside which the 3-D kernel is < 1e-14;
+ *             M is the mask of the block set (zero outside it).
+ *
+ * Data layout (all user buffers are caller-owned):
+ *   A block is B^3 cells at block coordinate (bx, by, bz) covering cells
+ *   [bx*B, bx*B + B) x [by*B, ...) x [bz*B, ...).  A field over a block list
+ *   is FP32, block-contiguous: index ((blk * ncomp + c) * B + z) * B * B + y * B + x,
+ *   i.e. [nblk][ncomp][B][B][B] with x fastest.  Block coordinates are int32
+ *   triples (bx, by, bz), [n][3], host memory, copied at plan time; the lists
+ *   must not contain duplicates.
+ *
+ * Conventions: every call returns an lgf_status; no call aborts, throws or
+ * exits.  On a non-OK status, lgf_last_error() returns a thread-local message.
+ * Library objects (tables, plans) are library-owned; destroy functions accept
+ * NULL.  A plan is not thread-safe; distinct plans are.  Streams are passed
+ * as `void *` holding a cudaStream_t (NULL = legacy default stream).
+ * Execute calls are asynchronous on the given stream, allocate nothing and
+ * synchronise nothing (so they may be captured in a CUDA graph), except where
+ * stated otherwise.  The library runs on the device that is current at
+ * plan/table creation; later calls must be made with that device current.
+ */
+#ifndef LGF_H
+#define LGF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LGF_OK = 0,
+    LGF_ERR_ARG = -1,     /* invalid argument (NULL pointer, bad size, unsupported shape) */
+    LGF_ERR_OOM = -2,     /* device or host allocation failed */
+    LGF_ERR_CUDA = -3,    /* a CUDA runtime call or kernel launch failed */
+    LGF_ERR_TIMEOUT = -4, /* a bounded device-side wait gave up */
+    LGF_ERR_TOL = -5,     /* requested tolerance not reachable with the given options */
+    LGF_ERR_STATE = -6    /* object used in the wrong state (e.g. wrong kind of table) */
+} lgf_status;
+
+typedef enum {
+    LGF_KERNEL_LAPLACE7 = 0, /* G_L: LGF of the 7-point Laplacian (App. B) */
+    LGF_KERNEL_IFACTOR = 1   /* G_E(alpha): integrating-factor kernel (App. B eq. lgf_intfac) */
+} lgf_kernel;
+
+typedef struct lgf_table lgf_table; /* opaque: device FP64 kernel values */
+typedef struct lgf_plan lgf_plan;   /* opaque: block lookups, spectra, workspaces */
+
+/* One independent problem.  For a Poisson plan: sources live on src_blocks
+ * (D_supp of Sec. 4.2), results are produced on dst_blocks (D_xsoln).  For an
+ * IF plan: src_blocks is the block set of the mask, dst_blocks/n_dst are
+ * ignored (output on the same set). */
+typedef struct {
+    int B;                      /* block edge in cells: 8, 16 or 32 */
+    int ncomp;                  /* components per point, 1..3 (solved independently) */
+    int n_src;                  /* number of source blocks (>= 1) */
+    int n_dst;                  /* number of target blocks (>= 1; Poisson only) */
+    const int32_t *src_blocks;  /* [n_src][3] block coordinates (host) */
+    const int32_t *dst_blocks;  /* [n_dst][3] block coordinates (host) */
+    double dx;                  /* grid spacing; the Poisson kernel is dx^2 * G */
+    double scale;               /* result multiplier, e.g. -1 for a = -L^{-1} w (eq. vel_refresh) */
+} lgf_solve_desc;
+
+typedef struct {
+    int use_graph;   /* 1: capture the execute launch sequence in a CUDA graph on first use */
+    int reserved[7]; /* must be zero */
+} lgf_plan_opts;
+
+/* ---------------------------------------------------------------------------
+ * Tables.
+ *
+ * LGF_KERNEL_LAPLACE7: tabulates the unit-lattice LGF on the sorted octant
+ *   max_offset >= a >= b >= c >= 0 from its Bessel form (App. B)
+ *     G(a,b,c) = -int_0^inf e^{-6t} I_a(2t) I_b(2t) I_c(2t) dt
+ *   in FP64 on the device (Gauss-Legendre in log t plus the closed-form
+ *   large-t tail).  max_offset must cover every offset a plan will sample:
+ *   lgf_conv_plan reports LGF_ERR_ARG with the required value otherwise.
+ *   alpha is ignored.  1 <= max_offset <= 1024.
+ * LGF_KERNEL_IFACTOR: tabulates g(k) = exp(-2 alpha) I_k(2 alpha), k = 0..R,
+ *   R = largest k with g(k) g(0)^2 >= 1e-14 (App. B eq. lgf_intfac; the
+ *   Bessel argument is 2 alpha as fixed by the decay values of the Sec. 2.3
+ *   footnote).  0 < alpha <= 50; max_offset is ignored.
+ * Synchronises `stream` before returning.  *out receives a new table.
+ * ------------------------------------------------------------------------- */
+lgf_status lgf_table_build(lgf_kernel kind, double alpha, int max_offset, void *stream, lgf_table **out);
+
+/* kind, alpha, max_offset (Laplace) and radius R (IF; 0 for Laplace). Any out pointer may be NULL. */
+lgf_status lgf_table_info(const lgf_table *t, int *kind, double *alpha, int *max_offset, int *radius);
+
+/* Copy the FP64 table to host memory: the octant entries in the order
+ * index(a,b,c) = a(a+1)(a+2)/6 + b(b+1)/2 + c (Laplace), or g(0..R) (IF).
+ * n = number of doubles available at host_out; LGF_ERR_ARG if too small.
+ * Synchronous. */
+lgf_status lgf_table_copy(const lgf_table *t, double *host_out, int64_t n);
+int64_t lgf_table_size(const lgf_table *t);
+
+void lgf_table_destroy(lgf_table *t);
+
+/* ---------------------------------------------------------------------------
+ * Plans.  lgf_conv_plan analyses n_solves independent problems, uploads the
+ * block lookups, builds (Poisson) the real, even spectrum of the LGF on the
+ * zero-padded FFT grid of each distinct grid size (Hockney's free-space
+ * embedding of eq. dpoisson_conv: exact up to FP32 rounding, no far-field
+ * approximation), and allocates every workspace.  The table must outlive the
+ * plan.  Synchronises `stream`.  opts may be NULL (defaults).
+ * ------------------------------------------------------------------------- */
+lgf_status lgf_conv_plan(const lgf_table *t, const lgf_solve_desc *solves, int n_solves,
+                         const lgf_plan_opts *opts, void *stream, lgf_plan **out);
+
+/* Device bytes held by the plan (workspaces + spectra + lookups). */
+lgf_status lgf_plan_workspace_bytes(const lgf_plan *p, size_t *bytes);
+
+/* Poisson: for every solve i, dst[i] (device, [n_dst][ncomp][B^3] FP32,
+ * overwritten on every target point) = scale * dx^2 * G * src[i] (device,
+ * [n_src][ncomp][B^3] FP32).  Asynchronous on `stream`; no allocation. */
+lgf_status lgf_conv_execute(lgf_plan *p, const float *const *src, float *const *dst, void *stream);
+
+/* Same as lgf_conv_execute with HOST buffers: copies every src[i] to
+ * plan-owned device staging, executes, copies the results to dst[i] and
+ * synchronises `stream` before returning.  Host buffers should be pinned
+ * for full copy bandwidth. */
+lgf_status lgf_conv_execute_host(lgf_plan *p, const float *const *src, float *const *dst, void *stream);
+
+/* IF plan (table of kind LGF_KERNEL_IFACTOR, one solve): y = M E_Q(alpha) M x
+ * on the block set, x and y device [n_src][ncomp][B^3] FP32 (must not alias).
+ * Requires R_alpha <= B.  Asynchronous; no allocation. */
+lgf_status ifactor_apply(lgf_plan *p, const float *x, float *y, void *stream);
+
+/* FP64 residual of a Poisson result (App. A stencil, Sec. 4.3 definition):
+ *   ||L u - scale f||_2 / ||scale f||_2
+ * over target points whose six neighbours are target points (L = 7-point
+ * Laplacian / dx^2).  src/dst as for lgf_conv_execute, solve = index.
+ * Synchronises `stream`. */
+lgf_status lgf_residual_fp64(lgf_plan *p, int solve, const float *src, const float *dst,
+                             double *rel_residual, void *stream);
+
+void lgf_plan_destroy(lgf_plan *p);
+
+/* Thread-local description of the last non-OK status ("" if none). */
+const char *lgf_last_error(void);
+
+/* Library version string. */
+const char *lgf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LGF_H */

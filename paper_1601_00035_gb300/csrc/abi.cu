@@ -1,0 +1,601 @@
+// C-ABI entry points of liblgf (declared in include/lgf.h): argument
+// validation, plan analysis (bounding boxes, FFT sizes, block lookups),
+// device allocation, and dispatch to the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <unordered_map>
+#include <vector>
+
+#include "plan.hpp"
+
+namespace lgf {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+void clear_error() { g_err[0] = '\0'; }
+
+namespace {
+struct TwTables {
+    float2 *f = nullptr;
+    double2 *d = nullptr;
+};
+std::mutex g_tw_mu;
+std::map<int, TwTables> g_tw;
+
+int current_device()
+{
+    int d = -1;
+    if (cudaGetDevice(&d) != cudaSuccess) return -1;
+    return d;
+}
+
+inline int64_t pack(int32_t x, int32_t y, int32_t z)
+{
+    const int64_t off = 1 << 20;
+    return ((int64_t)(x + off) << 42) | ((int64_t)(y + off) << 21) | (int64_t)(z + off);
+}
+
+bool coords_ok(const int32_t *c, int n)
+{
+    for (int i = 0; i < 3 * n; i++)
+        if (c[i] <= -(1 << 19) || c[i] >= (1 << 19)) return false;
+    return true;
+}
+
+template <typename T>
+lgf_status dalloc(T **p, size_t count, size_t &bytes)
+{
+    *p = nullptr;
+    if (count == 0) return LGF_OK;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+        *p = nullptr;
+        return LGF_ERR_OOM;
+    }
+    bytes += count * sizeof(T);
+    return LGF_OK;
+}
+
+template <typename T>
+lgf_status upload(T *d, const std::vector<T> &h, cudaStream_t s)
+{
+    if (h.empty()) return LGF_OK;
+    LGF_CUDA_TRY(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    LGF_CUDA_TRY(cudaStreamSynchronize(s));
+    return LGF_OK;
+}
+
+void free_plan(lgf_plan *p)
+{
+    if (!p) return;
+    for (auto &ps : p->solves) {
+        cudaFree(ps.d_src_lut);
+        cudaFree(ps.d_dst_lut);
+        cudaFree(ps.d_dst_nbr);
+        cudaFree(ps.d_dst2src);
+        cudaFree(ps.d_stage_src);
+        cudaFree(ps.d_stage_dst);
+    }
+    for (auto &sp : p->spectra) cudaFree(sp.d_Kh);
+    cudaFree(p->d_wsA);
+    cudaFree(p->d_wsB);
+    cudaFree(p->d_acc);
+    cudaFree(p->d_nbr);
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    delete p;
+}
+
+// neighbour table [n][27] of a block list (index of the block at offset
+// (dx,dy,dz) in {-1,0,1}^3, -1 if absent), ordering (dz+1)*9 + (dy+1)*3 + (dx+1)
+std::vector<int> neighbour_table(const int32_t *c, int n)
+{
+    std::unordered_map<int64_t, int> m;
+    m.reserve(2 * n);
+    for (int i = 0; i < n; i++) m[pack(c[3 * i], c[3 * i + 1], c[3 * i + 2])] = i;
+    std::vector<int> out((size_t)n * 27, -1);
+    for (int i = 0; i < n; i++)
+        for (int dz = -1; dz <= 1; dz++)
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    auto it = m.find(pack(c[3 * i] + dx, c[3 * i + 1] + dy, c[3 * i + 2] + dz));
+                    if (it != m.end()) out[(size_t)i * 27 + (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] = it->second;
+                }
+    return out;
+}
+
+bool has_duplicates(const int32_t *c, int n)
+{
+    std::unordered_map<int64_t, int> m;
+    m.reserve(2 * n);
+    for (int i = 0; i < n; i++)
+        if (!m.emplace(pack(c[3 * i], c[3 * i + 1], c[3 * i + 2]), i).second) return true;
+    return false;
+}
+
+}  // namespace
+
+lgf_status ensure_twiddles()
+{
+    const int dev = current_device();
+    if (dev < 0) {
+        set_error("no current CUDA device");
+        return LGF_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lk(g_tw_mu);
+    if (g_tw.count(dev)) return LGF_OK;
+    std::vector<float2> hf(TW_MAX);
+    std::vector<double2> hd(TW_MAX);
+    for (int j = 0; j < TW_MAX; j++) {
+        const double a = -2.0 * 3.14159265358979323846 * (double)j / (double)TW_MAX;
+        hd[j] = make_double2(std::cos(a), std::sin(a));
+        hf[j] = make_float2((float)hd[j].x, (float)hd[j].y);
+    }
+    TwTables t;
+    LGF_CUDA_TRY(cudaMalloc(&t.f, TW_MAX * sizeof(float2)));
+    LGF_CUDA_TRY(cudaMalloc(&t.d, TW_MAX * sizeof(double2)));
+    LGF_CUDA_TRY(cudaMemcpy(t.f, hf.data(), TW_MAX * sizeof(float2), cudaMemcpyHostToDevice));
+    LGF_CUDA_TRY(cudaMemcpy(t.d, hd.data(), TW_MAX * sizeof(double2), cudaMemcpyHostToDevice));
+    g_tw[dev] = t;
+    return LGF_OK;
+}
+
+const float2 *twiddle_table_f32()
+{
+    std::lock_guard<std::mutex> lk(g_tw_mu);
+    auto it = g_tw.find(current_device());
+    return it == g_tw.end() ? nullptr : it->second.f;
+}
+const double2 *twiddle_table_f64()
+{
+    std::lock_guard<std::mutex> lk(g_tw_mu);
+    auto it = g_tw.find(current_device());
+    return it == g_tw.end() ? nullptr : it->second.d;
+}
+
+}  // namespace lgf
+
+using namespace lgf;
+
+extern "C" {
+
+const char *lgf_last_error(void) { return g_err; }
+
+const char *lgf_version(void) { return "lgf 0.1 (sm_103a)"; }
+
+lgf_status lgf_table_build(lgf_kernel kind, double alpha, int max_offset, void *stream, lgf_table **out)
+{
+    clear_error();
+    LGF_CHECK_ARG(out != nullptr, "lgf_table_build: out is NULL");
+    *out = nullptr;
+    LGF_CHECK_ARG(kind == LGF_KERNEL_LAPLACE7 || kind == LGF_KERNEL_IFACTOR, "lgf_table_build: unknown kind %d", (int)kind);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int dev = current_device();
+    if (dev < 0) {
+        set_error("lgf_table_build: no CUDA device");
+        return LGF_ERR_CUDA;
+    }
+    lgf_table *t = new (std::nothrow) lgf_table();
+    if (!t) {
+        set_error("host allocation failed");
+        return LGF_ERR_OOM;
+    }
+    t->kind = kind;
+    t->device = dev;
+    t->d_vals = nullptr;
+    t->d_taps32 = nullptr;
+    size_t bytes = 0;
+    lgf_status st = LGF_OK;
+    if (kind == LGF_KERNEL_LAPLACE7) {
+        if (!(max_offset >= 1 && max_offset <= 1024)) {
+            delete t;
+            set_error("lgf_table_build: max_offset %d outside [1, 1024]", max_offset);
+            return LGF_ERR_ARG;
+        }
+        t->K = max_offset;
+        t->R = 0;
+        t->alpha = 0.0;
+        const int64_t K1 = max_offset + 1;
+        t->n = K1 * (K1 + 1) * (K1 + 2) / 6;
+        st = dalloc(&t->d_vals, (size_t)t->n, bytes);
+        if (st == LGF_OK) st = build_lgf_octant(max_offset, t->d_vals, s);
+    } else {
+        if (!(alpha > 0.0 && alpha <= 50.0)) {
+            delete t;
+            set_error("lgf_table_build: alpha %g outside (0, 50]", alpha);
+            return LGF_ERR_ARG;
+        }
+        t->alpha = alpha;
+        t->K = 0;
+        const int maxr = 64;
+        st = dalloc(&t->d_vals, maxr + 1, bytes);
+        int R = 0;
+        if (st == LGF_OK) st = build_if_taps(alpha, 1e-14, t->d_vals, maxr, &R, s);
+        if (st == LGF_OK && R >= maxr) {
+            set_error("lgf_table_build: alpha %g needs more than %d integrating-factor taps", alpha, maxr);
+            st = LGF_ERR_ARG;
+        }
+        if (st == LGF_OK) {
+            t->R = R;
+            t->n = R + 1;
+            std::vector<double> h(R + 1);
+            std::vector<float> hf(R + 1);
+            if (cudaMemcpy(h.data(), t->d_vals, (R + 1) * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                set_error("taps download failed");
+                st = LGF_ERR_CUDA;
+            } else {
+                for (int i = 0; i <= R; i++) hf[i] = (float)h[i];
+                st = dalloc(&t->d_taps32, R + 1, bytes);
+                if (st == LGF_OK && cudaMemcpy(t->d_taps32, hf.data(), (R + 1) * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+                    set_error("taps upload failed");
+                    st = LGF_ERR_CUDA;
+                }
+            }
+        }
+    }
+    if (st != LGF_OK) {
+        cudaFree(t->d_vals);
+        cudaFree(t->d_taps32);
+        delete t;
+        return st;
+    }
+    *out = t;
+    return LGF_OK;
+}
+
+lgf_status lgf_table_info(const lgf_table *t, int *kind, double *alpha, int *max_offset, int *radius)
+{
+    clear_error();
+    LGF_CHECK_ARG(t != nullptr, "lgf_table_info: table is NULL");
+    if (kind) *kind = t->kind;
+    if (alpha) *alpha = t->alpha;
+    if (max_offset) *max_offset = t->K;
+    if (radius) *radius = t->R;
+    return LGF_OK;
+}
+
+int64_t lgf_table_size(const lgf_table *t) { return t ? t->n : 0; }
+
+lgf_status lgf_table_copy(const lgf_table *t, double *host_out, int64_t n)
+{
+    clear_error();
+    LGF_CHECK_ARG(t != nullptr && host_out != nullptr, "lgf_table_copy: NULL argument");
+    LGF_CHECK_ARG(n >= t->n, "lgf_table_copy: need %lld doubles, got %lld", (long long)t->n, (long long)n);
+    LGF_CUDA_TRY(cudaMemcpy(host_out, t->d_vals, t->n * sizeof(double), cudaMemcpyDeviceToHost));
+    return LGF_OK;
+}
+
+void lgf_table_destroy(lgf_table *t)
+{
+    if (!t) return;
+    cudaFree(t->d_vals);
+    cudaFree(t->d_taps32);
+    delete t;
+}
+
+static lgf_status plan_poisson(lgf_plan *p, const lgf_table *t, const lgf_solve_desc *solves, int n_solves, cudaStream_t s)
+{
+    LGF_TRY(poisson_prepare());
+    std::map<std::vector<int>, int> spec_index;
+    size_t maxA = 0, maxB = 0;
+    for (int i = 0; i < n_solves; i++) {
+        const lgf_solve_desc &d = solves[i];
+        LGF_CHECK_ARG(d.B == 8 || d.B == 16 || d.B == 32, "solve %d: B=%d not in {8,16,32}", i, d.B);
+        LGF_CHECK_ARG(d.ncomp >= 1 && d.ncomp <= 3, "solve %d: ncomp=%d not in 1..3", i, d.ncomp);
+        LGF_CHECK_ARG(d.n_src >= 1 && d.n_dst >= 1, "solve %d: empty block list", i);
+        LGF_CHECK_ARG(d.src_blocks && d.dst_blocks, "solve %d: NULL block list", i);
+        LGF_CHECK_ARG(d.dx > 0.0 && std::isfinite(d.dx) && std::isfinite(d.scale), "solve %d: bad dx/scale", i);
+        LGF_CHECK_ARG(coords_ok(d.src_blocks, d.n_src) && coords_ok(d.dst_blocks, d.n_dst),
+                      "solve %d: block coordinate out of range", i);
+        LGF_CHECK_ARG(!has_duplicates(d.src_blocks, d.n_src), "solve %d: duplicate source block", i);
+        LGF_CHECK_ARG(!has_duplicates(d.dst_blocks, d.n_dst), "solve %d: duplicate target block", i);
+        PoissonSolve ps;
+        Geom &g = ps.g;
+        std::memset(&g, 0, sizeof(g));
+        g.B = d.B;
+        g.ncomp = d.ncomp;
+        ps.nsrc = d.n_src;
+        ps.ndst = d.n_dst;
+        ps.dx = d.dx;
+        ps.scale = d.scale;
+        ps.src_coords.assign(d.src_blocks, d.src_blocks + 3 * d.n_src);
+        ps.dst_coords.assign(d.dst_blocks, d.dst_blocks + 3 * d.n_dst);
+        int smin[3], smax[3], tmin[3], tmax[3];
+        for (int a = 0; a < 3; a++) {
+            smin[a] = tmin[a] = 1 << 30;
+            smax[a] = tmax[a] = -(1 << 30);
+        }
+        for (int b = 0; b < d.n_src; b++)
+            for (int a = 0; a < 3; a++) {
+                smin[a] = std::min(smin[a], d.src_blocks[3 * b + a]);
+                smax[a] = std::max(smax[a], d.src_blocks[3 * b + a]);
+            }
+        for (int b = 0; b < d.n_dst; b++)
+            for (int a = 0; a < 3; a++) {
+                tmin[a] = std::min(tmin[a], d.dst_blocks[3 * b + a]);
+                tmax[a] = std::max(tmax[a], d.dst_blocks[3 * b + a]);
+            }
+        for (int a = 0; a < 3; a++) {
+            g.nbS[a] = smax[a] - smin[a] + 1;
+            g.nbT[a] = tmax[a] - tmin[a] + 1;
+            g.S0[a] = smin[a] * d.B;
+            g.Es[a] = g.nbS[a] * d.B;
+            g.T0[a] = tmin[a] * d.B;
+            g.Et[a] = g.nbT[a] * d.B;
+            const long lo = (long)g.T0[a] - (long)(g.S0[a] + g.Es[a] - 1);
+            const long hi = (long)(g.T0[a] + g.Et[a] - 1) - (long)g.S0[a];
+            const long maxabs = std::max(std::labs(lo), std::labs(hi));
+            const int n = poisson_pick_n((int)std::min<long>(2 * maxabs + 2, 1 << 20));
+            LGF_CHECK_ARG(n > 0, "solve %d: source/target extent %ld along axis %d needs an FFT longer than 1024", i,
+                          maxabs, a);
+            g.N[a] = n;
+        }
+        g.KX = g.N[0] / 2 + 1;
+        g.mul = (float)(d.scale * d.dx * d.dx / ((double)g.N[0] * g.N[1] * g.N[2]));
+        // lookups
+        std::vector<int> slut((size_t)g.nbS[0] * g.nbS[1] * g.nbS[2], -1), tlut((size_t)g.nbT[0] * g.nbT[1] * g.nbT[2], -1);
+        for (int b = 0; b < d.n_src; b++) {
+            const int x = d.src_blocks[3 * b] - smin[0], y = d.src_blocks[3 * b + 1] - smin[1], z = d.src_blocks[3 * b + 2] - smin[2];
+            slut[((size_t)z * g.nbS[1] + y) * g.nbS[0] + x] = b;
+        }
+        for (int b = 0; b < d.n_dst; b++) {
+            const int x = d.dst_blocks[3 * b] - tmin[0], y = d.dst_blocks[3 * b + 1] - tmin[1], z = d.dst_blocks[3 * b + 2] - tmin[2];
+            tlut[((size_t)z * g.nbT[1] + y) * g.nbT[0] + x] = b;
+        }
+        std::vector<int> nbr = neighbour_table(d.dst_blocks, d.n_dst);
+        std::vector<int> d2s(d.n_dst, -1);
+        {
+            std::unordered_map<int64_t, int> m;
+            for (int b = 0; b < d.n_src; b++) m[pack(d.src_blocks[3 * b], d.src_blocks[3 * b + 1], d.src_blocks[3 * b + 2])] = b;
+            for (int b = 0; b < d.n_dst; b++) {
+                auto it = m.find(pack(d.dst_blocks[3 * b], d.dst_blocks[3 * b + 1], d.dst_blocks[3 * b + 2]));
+                if (it != m.end()) d2s[b] = it->second;
+            }
+        }
+        // device copies (pushed before the PoissonSolve is stored so cleanup sees them)
+        p->solves.push_back(ps);
+        PoissonSolve &q = p->solves.back();
+        LGF_TRY(dalloc(&q.d_src_lut, slut.size(), p->bytes));
+        LGF_TRY(dalloc(&q.d_dst_lut, tlut.size(), p->bytes));
+        LGF_TRY(dalloc(&q.d_dst_nbr, nbr.size(), p->bytes));
+        LGF_TRY(dalloc(&q.d_dst2src, d2s.size(), p->bytes));
+        LGF_TRY(upload(q.d_src_lut, slut, s));
+        LGF_TRY(upload(q.d_dst_lut, tlut, s));
+        LGF_TRY(upload(q.d_dst_nbr, nbr, s));
+        LGF_TRY(upload(q.d_dst2src, d2s, s));
+        const size_t B3 = (size_t)d.B * d.B * d.B;
+        LGF_TRY(dalloc(&q.d_stage_src, (size_t)d.n_src * d.ncomp * B3, p->bytes));
+        LGF_TRY(dalloc(&q.d_stage_dst, (size_t)d.n_dst * d.ncomp * B3, p->bytes));
+        q.g.src_lut = q.d_src_lut;
+        q.g.dst_lut = q.d_dst_lut;
+        const size_t KX = g.KX, nc = d.ncomp;
+        q.elemsA = std::max(nc * g.Es[2] * g.Es[1] * KX, nc * g.Et[2] * (size_t)g.N[1] * KX);
+        q.elemsB = std::max(nc * g.Es[2] * (size_t)g.N[1] * KX, nc * g.Et[2] * g.Et[1] * KX);
+        maxA = std::max(maxA, q.elemsA);
+        maxB = std::max(maxB, q.elemsB);
+        std::vector<int> key = {g.N[0], g.N[1], g.N[2]};
+        auto it = spec_index.find(key);
+        if (it == spec_index.end()) {
+            Spectrum sp;
+            sp.N[0] = g.N[0];
+            sp.N[1] = g.N[1];
+            sp.N[2] = g.N[2];
+            p->spectra.push_back(sp);
+            Spectrum &spr = p->spectra.back();
+            const size_t nK = (size_t)(g.N[0] / 2 + 1) * (g.N[1] / 2 + 1) * (g.N[2] / 2 + 1);
+            LGF_TRY(dalloc(&spr.d_Kh, nK, p->bytes));
+            LGF_TRY(build_spectrum(t->d_vals, t->K, g.N, spr.d_Kh, s));
+            it = spec_index.emplace(key, (int)p->spectra.size() - 1).first;
+        }
+        q.spec = it->second;
+    }
+    for (auto &q : p->solves) q.g.Kh = p->spectra[q.spec].d_Kh;
+    LGF_TRY(dalloc(&p->d_wsA, maxA, p->bytes));
+    LGF_TRY(dalloc(&p->d_wsB, maxB, p->bytes));
+    LGF_TRY(dalloc(&p->d_acc, 2, p->bytes));
+    p->wsA = maxA;
+    p->wsB = maxB;
+    return LGF_OK;
+}
+
+static lgf_status plan_ifactor(lgf_plan *p, const lgf_table *t, const lgf_solve_desc *solves, int n_solves, cudaStream_t s)
+{
+    LGF_CHECK_ARG(n_solves == 1, "integrating-factor plans take exactly one block set (got %d)", n_solves);
+    const lgf_solve_desc &d = solves[0];
+    LGF_CHECK_ARG(d.B == 8 || d.B == 16 || d.B == 32, "B=%d not in {8,16,32}", d.B);
+    LGF_CHECK_ARG(d.ncomp >= 1 && d.ncomp <= 3, "ncomp=%d not in 1..3", d.ncomp);
+    LGF_CHECK_ARG(d.n_src >= 1 && d.src_blocks, "empty block set");
+    LGF_CHECK_ARG(coords_ok(d.src_blocks, d.n_src), "block coordinate out of range");
+    LGF_CHECK_ARG(!has_duplicates(d.src_blocks, d.n_src), "duplicate block in the set");
+    LGF_CHECK_ARG(t->R <= d.B, "integrating-factor radius %d exceeds B=%d (alpha too large for this block size)", t->R, d.B);
+    p->B = d.B;
+    p->ncomp = d.ncomp;
+    p->nblk = d.n_src;
+    p->R = t->R;
+    std::vector<int> nbr = neighbour_table(d.src_blocks, d.n_src);
+    LGF_TRY(dalloc(&p->d_nbr, nbr.size(), p->bytes));
+    LGF_TRY(upload(p->d_nbr, nbr, s));
+    return LGF_OK;
+}
+
+lgf_status lgf_conv_plan(const lgf_table *t, const lgf_solve_desc *solves, int n_solves, const lgf_plan_opts *opts,
+                         void *stream, lgf_plan **out)
+{
+    clear_error();
+    LGF_CHECK_ARG(out != nullptr, "lgf_conv_plan: out is NULL");
+    *out = nullptr;
+    LGF_CHECK_ARG(t != nullptr && solves != nullptr && n_solves >= 1, "lgf_conv_plan: bad table/solves/n_solves");
+    if (opts) {
+        for (int i = 0; i < 7; i++) LGF_CHECK_ARG(opts->reserved[i] == 0, "lgf_conv_plan: reserved option fields must be zero");
+    }
+    const int dev = current_device();
+    if (dev != t->device) {
+        set_error("lgf_conv_plan: current device %d differs from the table's device %d", dev, t->device);
+        return LGF_ERR_STATE;
+    }
+    LGF_TRY(ensure_twiddles());
+    cudaStream_t s = (cudaStream_t)stream;
+    lgf_plan *p = new (std::nothrow) lgf_plan();
+    if (!p) {
+        set_error("host allocation failed");
+        return LGF_ERR_OOM;
+    }
+    p->kind = t->kind;
+    p->device = dev;
+    p->table = t;
+    p->use_graph = opts ? opts->use_graph : 0;
+    lgf_status st = t->kind == LGF_KERNEL_LAPLACE7 ? plan_poisson(p, t, solves, n_solves, s)
+                                                   : plan_ifactor(p, t, solves, n_solves, s);
+    if (st != LGF_OK) {
+        free_plan(p);
+        return st;
+    }
+    *out = p;
+    return LGF_OK;
+}
+
+lgf_status lgf_plan_workspace_bytes(const lgf_plan *p, size_t *bytes)
+{
+    clear_error();
+    LGF_CHECK_ARG(p && bytes, "lgf_plan_workspace_bytes: NULL argument");
+    *bytes = p->bytes;
+    return LGF_OK;
+}
+
+static lgf_status run_poisson(lgf_plan *p, const float *const *src, float *const *dst, cudaStream_t s)
+{
+    for (size_t i = 0; i < p->solves.size(); i++)
+        LGF_TRY(poisson_launch(p->solves[i].g, src[i], dst[i], p->d_wsA, p->d_wsB, s));
+    return LGF_OK;
+}
+
+lgf_status lgf_conv_execute(lgf_plan *p, const float *const *src, float *const *dst, void *stream)
+{
+    clear_error();
+    LGF_CHECK_ARG(p && src && dst, "lgf_conv_execute: NULL argument");
+    if (p->kind != LGF_KERNEL_LAPLACE7) {
+        set_error("lgf_conv_execute: plan is not a Poisson plan (use ifactor_apply)");
+        return LGF_ERR_STATE;
+    }
+    for (size_t i = 0; i < p->solves.size(); i++)
+        LGF_CHECK_ARG(src[i] && dst[i], "lgf_conv_execute: NULL buffer for solve %zu", i);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!p->use_graph) return run_poisson(p, src, dst, s);
+    // graph path: one captured launch sequence per distinct set of buffers
+    std::vector<const void *> key;
+    for (size_t i = 0; i < p->solves.size(); i++) {
+        key.push_back(src[i]);
+        key.push_back(dst[i]);
+    }
+    if (!p->graph || key != p->graph_key) {
+        if (p->graph) {
+            cudaGraphExecDestroy(p->graph);
+            p->graph = nullptr;
+        }
+        cudaStream_t cs;
+        LGF_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t gr = nullptr;
+        lgf_status st = LGF_OK;
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            set_error("stream capture failed to start");
+            st = LGF_ERR_CUDA;
+        } else {
+            st = run_poisson(p, src, dst, cs);
+            cudaError_t e = cudaStreamEndCapture(cs, &gr);
+            if (st == LGF_OK && e != cudaSuccess) {
+                set_error("stream capture failed: %s", cudaGetErrorString(e));
+                st = LGF_ERR_CUDA;
+            }
+            if (st == LGF_OK && cudaGraphInstantiate(&p->graph, gr, 0) != cudaSuccess) {
+                set_error("graph instantiation failed");
+                st = LGF_ERR_CUDA;
+                p->graph = nullptr;
+            }
+        }
+        if (gr) cudaGraphDestroy(gr);
+        cudaStreamDestroy(cs);
+        if (st != LGF_OK) return st;
+        p->graph_key = key;
+    }
+    LGF_CUDA_TRY(cudaGraphLaunch(p->graph, s));
+    return LGF_OK;
+}
+
+lgf_status lgf_conv_execute_host(lgf_plan *p, const float *const *src, float *const *dst, void *stream)
+{
+    clear_error();
+    LGF_CHECK_ARG(p && src && dst, "lgf_conv_execute_host: NULL argument");
+    if (p->kind != LGF_KERNEL_LAPLACE7) {
+        set_error("lgf_conv_execute_host: plan is not a Poisson plan");
+        return LGF_ERR_STATE;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<const float *> ds(p->solves.size());
+    std::vector<float *> dd(p->solves.size());
+    for (size_t i = 0; i < p->solves.size(); i++) {
+        const PoissonSolve &q = p->solves[i];
+        LGF_CHECK_ARG(src[i] && dst[i], "lgf_conv_execute_host: NULL buffer for solve %zu", i);
+        const size_t B3 = (size_t)q.g.B * q.g.B * q.g.B;
+        LGF_CUDA_TRY(cudaMemcpyAsync(q.d_stage_src, src[i], (size_t)q.nsrc * q.g.ncomp * B3 * sizeof(float),
+                                     cudaMemcpyHostToDevice, s));
+        ds[i] = q.d_stage_src;
+        dd[i] = q.d_stage_dst;
+    }
+    LGF_TRY(run_poisson(p, ds.data(), dd.data(), s));
+    for (size_t i = 0; i < p->solves.size(); i++) {
+        const PoissonSolve &q = p->solves[i];
+        const size_t B3 = (size_t)q.g.B * q.g.B * q.g.B;
+        LGF_CUDA_TRY(cudaMemcpyAsync(dst[i], q.d_stage_dst, (size_t)q.ndst * q.g.ncomp * B3 * sizeof(float),
+                                     cudaMemcpyDeviceToHost, s));
+    }
+    LGF_CUDA_TRY(cudaStreamSynchronize(s));
+    return LGF_OK;
+}
+
+lgf_status ifactor_apply(lgf_plan *p, const float *x, float *y, void *stream)
+{
+    clear_error();
+    LGF_CHECK_ARG(p && x && y, "ifactor_apply: NULL argument");
+    LGF_CHECK_ARG(x != y, "ifactor_apply: x and y must not alias");
+    if (p->kind != LGF_KERNEL_IFACTOR) {
+        set_error("ifactor_apply: plan was not built from an integrating-factor table");
+        return LGF_ERR_STATE;
+    }
+    return ifactor_launch(p->B, p->ncomp, p->nblk, p->R, p->d_nbr, p->table->d_taps32, x, y, (cudaStream_t)stream);
+}
+
+lgf_status lgf_residual_fp64(lgf_plan *p, int solve, const float *src, const float *dst, double *rel_residual,
+                             void *stream)
+{
+    clear_error();
+    LGF_CHECK_ARG(p && src && dst && rel_residual, "lgf_residual_fp64: NULL argument");
+    if (p->kind != LGF_KERNEL_LAPLACE7) {
+        set_error("lgf_residual_fp64: not a Poisson plan");
+        return LGF_ERR_STATE;
+    }
+    LGF_CHECK_ARG(solve >= 0 && solve < (int)p->solves.size(), "lgf_residual_fp64: solve %d out of range", solve);
+    cudaStream_t s = (cudaStream_t)stream;
+    LGF_CUDA_TRY(cudaMemsetAsync(p->d_acc, 0, 2 * sizeof(double), s));
+    LGF_TRY(residual_launch(p->solves[solve], src, dst, p->d_acc, s));
+    double h[2];
+    LGF_CUDA_TRY(cudaMemcpyAsync(h, p->d_acc, sizeof(h), cudaMemcpyDeviceToHost, s));
+    LGF_CUDA_TRY(cudaStreamSynchronize(s));
+    *rel_residual = h[1] > 0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
+    return LGF_OK;
+}
+
+void lgf_plan_destroy(lgf_plan *p) { free_plan(p); }
+
+}  // extern "C"

@@ -1,0 +1,83 @@
+// Shared helpers of liblgf: status/error plumbing, device complex type,
+// launch checking.  No numerics of the method live here.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+
+#include "lgf.h"
+
+namespace lgf {
+
+// Thread-local last-error message (lgf_last_error).
+void set_error(const char *fmt, ...);
+void clear_error();
+
+#define LGF_CHECK_ARG(cond, ...)                                                              \
+    do {                                                                                      \
+        if (!(cond)) {                                                                        \
+            ::lgf::set_error(__VA_ARGS__);                                                    \
+            return LGF_ERR_ARG;                                                               \
+        }                                                                                     \
+    } while (0)
+
+#define LGF_CUDA_TRY(expr)                                                                    \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            ::lgf::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
+                             __LINE__);                                                       \
+            return e_ == cudaErrorMemoryAllocation ? LGF_ERR_OOM : LGF_ERR_CUDA;              \
+        }                                                                                     \
+    } while (0)
+
+#define LGF_LAUNCH_CHECK(name)                                                                \
+    do {                                                                                      \
+        cudaError_t e_ = cudaGetLastError();                                                  \
+        if (e_ != cudaSuccess) {                                                              \
+            ::lgf::set_error("launch of %s failed: %s", name, cudaGetErrorString(e_));        \
+            return LGF_ERR_CUDA;                                                              \
+        }                                                                                     \
+    } while (0)
+
+#define LGF_TRY(expr)                                                                         \
+    do {                                                                                      \
+        lgf_status s_ = (expr);                                                               \
+        if (s_ != LGF_OK) return s_;                                                          \
+    } while (0)
+
+template <typename T>
+struct cx {
+    T x, y;
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b)
+{
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// a * conj(b)
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> cmulc(cx<T> a, cx<T> b)
+{
+    return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> conj(cx<T> a) { return {a.x, -a.y}; }
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Twiddle table w_1024^j = exp(-2 pi i j / 1024), j = 0..1023, computed on the
+// host in double precision and uploaded once per device (FP32 and FP64 copies).
+const float2 *twiddle_table_f32();   // device pointer, current device
+const double2 *twiddle_table_f64();  // device pointer, current device
+lgf_status ensure_twiddles();
+constexpr int TW_MAX = 1024;
+
+}  // namespace lgf

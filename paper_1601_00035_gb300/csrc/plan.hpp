@@ -1,0 +1,98 @@
+// Host-side objects behind the opaque lgf_table / lgf_plan handles.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "common.cuh"
+
+// Geometry of one Poisson solve as seen by the FFT passes (POD, passed by value).
+// Axis order everywhere: 0 = x, 1 = y, 2 = z.  Positions in cells.
+namespace lgf {
+struct Geom {
+    int B, ncomp;
+    int S0[3], Es[3];  // source bounding box: origin, extent (multiples of B)
+    int T0[3], Et[3];  // target bounding box
+    int N[3];          // zero-padded FFT length per axis
+    int nbS[3], nbT[3];
+    const int *src_lut;  // [nbS_z][nbS_y][nbS_x] -> source block index, -1 if none
+    const int *dst_lut;  // [nbT_z][nbT_y][nbT_x] -> target block index, -1 if none
+    const float *Kh;     // real even spectrum octant [Nz/2+1][Ny/2+1][Nx/2+1]
+    float mul;           // scale * dx^2 / (Nx Ny Nz)
+    int KX;              // Nx/2 + 1
+};
+
+struct PoissonSolve {
+    Geom g;
+    int nsrc, ndst;
+    double dx, scale;
+    std::vector<int32_t> src_coords, dst_coords;  // host copies
+    int spec;                                     // index into lgf_plan::spectra
+    size_t elemsA, elemsB;                        // complex elements needed in workspaces A and B
+    int *d_src_lut = nullptr, *d_dst_lut = nullptr;
+    int *d_dst_nbr = nullptr;   // [ndst][27] target-block neighbours (residual)
+    int *d_dst2src = nullptr;   // [ndst] source block at the same coordinates, -1 if none
+    float *d_stage_src = nullptr, *d_stage_dst = nullptr;  // staging for lgf_conv_execute_host
+};
+
+struct Spectrum {
+    int N[3];
+    float *d_Kh = nullptr;
+};
+
+// launchers (poisson.cu)
+lgf_status poisson_launch(const Geom &g, const float *src, float *dst, cx<float> *wsA, cx<float> *wsB,
+                          cudaStream_t s);
+bool poisson_supported_n(int n);
+lgf_status poisson_prepare();  // per-device constant tables; call outside stream capture
+int poisson_pick_n(int need);  // smallest supported FFT length >= need, 0 if none
+
+// spectrum construction (spectrum.cu): FP64 cosine transforms of the table samples
+lgf_status build_spectrum(const double *d_octant, int K, const int N[3], float *d_Kh, cudaStream_t s);
+
+// tables (table.cu)
+lgf_status build_lgf_octant(int K, double *d_out, cudaStream_t s);
+lgf_status build_if_taps(double alpha, double tol, double *d_taps, int max_r, int *R_out, cudaStream_t s);
+
+// integrating factor (ifactor.cu)
+lgf_status ifactor_launch(int B, int ncomp, int nblk, int R, const int *d_nbr, const float *d_taps,
+                          const float *x, float *y, cudaStream_t s);
+
+// residual (residual.cu)
+lgf_status residual_launch(const PoissonSolve &ps, const float *src, const float *dst, double *d_acc,
+                           cudaStream_t s);
+
+}  // namespace lgf
+
+struct lgf_table {
+    int kind;
+    double alpha;
+    int K;  // max offset (Laplace)
+    int R;  // radius (IF)
+    int device;
+    int64_t n;       // number of doubles
+    double *d_vals;  // FP64 values on the device
+    float *d_taps32; // IF: FP32 copy of the taps
+};
+
+struct lgf_plan {
+    int kind;
+    int device;
+    const lgf_table *table;
+    // Poisson
+    std::vector<lgf::PoissonSolve> solves;
+    std::vector<lgf::Spectrum> spectra;
+    lgf::cx<float> *d_wsA = nullptr, *d_wsB = nullptr;
+    size_t wsA = 0, wsB = 0;
+    double *d_acc = nullptr;  // residual accumulators
+    // IF
+    int B = 0, ncomp = 0, nblk = 0, R = 0;
+    int *d_nbr = nullptr;  // [nblk][27]
+    // graph capture
+    int use_graph = 0;
+    cudaGraphExec_t graph = nullptr;
+    std::vector<const void *> graph_key;
+    size_t bytes = 0;
+};

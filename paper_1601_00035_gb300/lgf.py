@@ -1,0 +1,250 @@
+"""Thin ctypes binding of liblgf.so (the C-ABI in include/lgf.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device buffers are torch CUDA tensors (float32, contiguous) passed by
+data pointer; streams default to torch's current stream.  There is no CPU
+fallback: if the library is missing or fails to load, `load()` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "liblgf.so")
+
+LGF_OK = 0
+LGF_ERR_ARG = -1
+LGF_ERR_OOM = -2
+LGF_ERR_CUDA = -3
+LGF_ERR_TIMEOUT = -4
+LGF_ERR_TOL = -5
+LGF_ERR_STATE = -6
+
+LAPLACE7 = 0
+IFACTOR = 1
+
+
+class LGFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("lgf status %d: %s" % (status, msg))
+        self.status = status
+
+
+class _SolveDesc(ctypes.Structure):
+    _fields_ = [
+        ("B", ctypes.c_int),
+        ("ncomp", ctypes.c_int),
+        ("n_src", ctypes.c_int),
+        ("n_dst", ctypes.c_int),
+        ("src_blocks", ctypes.POINTER(ctypes.c_int32)),
+        ("dst_blocks", ctypes.POINTER(ctypes.c_int32)),
+        ("dx", ctypes.c_double),
+        ("scale", ctypes.c_double),
+    ]
+
+
+class _PlanOpts(ctypes.Structure):
+    _fields_ = [("use_graph", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+
+
+_lib = None
+
+# name -> (restype, argtypes); every function declared in include/lgf.h
+_SIGS = {
+    "lgf_table_build": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    "lgf_table_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "lgf_table_copy": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64]),
+    "lgf_table_size": (ctypes.c_int64, [ctypes.c_void_p]),
+    "lgf_table_destroy": (None, [ctypes.c_void_p]),
+    "lgf_conv_plan": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_SolveDesc), ctypes.c_int,
+                                     ctypes.POINTER(_PlanOpts), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "lgf_plan_workspace_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "lgf_conv_execute": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                                        ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
+    "lgf_conv_execute_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                                             ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
+    "ifactor_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "lgf_residual_fp64": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "lgf_plan_destroy": (None, [ctypes.c_void_p]),
+    "lgf_last_error": (ctypes.c_char_p, []),
+    "lgf_version": (ctypes.c_char_p, []),
+}
+
+
+def load() -> ctypes.CDLL:
+    """Load liblgf.so; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("liblgf.so not built (expected %s); run paper_1601_00035_gb300/build.py "
+                           "or __graft_entry__.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(st: int):
+    if st != LGF_OK:
+        raise LGFError(st, load().lgf_last_error().decode())
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float32 CUDA tensor")
+    return t.data_ptr()
+
+
+class Table:
+    """FP64 kernel table on the device (lgf_table_build)."""
+
+    def __init__(self, kind: int, alpha: float = 0.0, max_offset: int = 0, stream=None):
+        L = load()
+        h = ctypes.c_void_p()
+        _check(L.lgf_table_build(kind, float(alpha), int(max_offset), _stream(stream), ctypes.byref(h)))
+        self._h = h
+        k, a, K, R = ctypes.c_int(), ctypes.c_double(), ctypes.c_int(), ctypes.c_int()
+        _check(L.lgf_table_info(h, ctypes.byref(k), ctypes.byref(a), ctypes.byref(K), ctypes.byref(R)))
+        self.kind, self.alpha, self.max_offset, self.radius = k.value, a.value, K.value, R.value
+
+    def values(self) -> np.ndarray:
+        L = load()
+        n = L.lgf_table_size(self._h)
+        out = np.zeros(n)
+        _check(L.lgf_table_copy(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lgf_table_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class Solve:
+    """One independent problem (lgf_solve_desc)."""
+    B: int
+    ncomp: int
+    src_blocks: np.ndarray            # [n_src, 3] int (bx, by, bz)
+    dst_blocks: Optional[np.ndarray]  # [n_dst, 3] (Poisson) or None (IF)
+    dx: float = 1.0
+    scale: float = 1.0
+
+
+class Plan:
+    """lgf_conv_plan over one or more solves."""
+
+    def __init__(self, table: Table, solves: Sequence[Solve], use_graph: bool = False, stream=None):
+        L = load()
+        self.table = table  # keep alive
+        self.solves = list(solves)
+        descs = (_SolveDesc * len(self.solves))()
+        self._keep = []
+        for d, s in zip(descs, self.solves):
+            src = np.ascontiguousarray(s.src_blocks, dtype=np.int32).reshape(-1, 3)
+            dst = src if s.dst_blocks is None else np.ascontiguousarray(s.dst_blocks, dtype=np.int32).reshape(-1, 3)
+            self._keep += [src, dst]
+            d.B, d.ncomp, d.n_src, d.n_dst = s.B, s.ncomp, len(src), len(dst)
+            d.src_blocks = src.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            d.dst_blocks = dst.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            d.dx, d.scale = float(s.dx), float(s.scale)
+        opts = _PlanOpts()
+        opts.use_graph = 1 if use_graph else 0
+        h = ctypes.c_void_p()
+        _check(L.lgf_conv_plan(table._h, descs, len(self.solves), ctypes.byref(opts), _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    def workspace_bytes(self) -> int:
+        b = ctypes.c_size_t()
+        _check(load().lgf_plan_workspace_bytes(self._h, ctypes.byref(b)))
+        return b.value
+
+    def execute(self, src, dst, stream=None):
+        """Poisson: dst[i] = scale dx^2 G * src[i] (device tensors)."""
+        n = len(self.solves)
+        a = (ctypes.c_void_p * n)(*[_ptr(t) for t in src])
+        b = (ctypes.c_void_p * n)(*[_ptr(t) for t in dst])
+        _check(load().lgf_conv_execute(self._h, a, b, _stream(stream)))
+
+    def execute_host(self, src: Sequence[np.ndarray], dst: Sequence[np.ndarray], stream=None):
+        """Poisson with host float32 arrays (pinned for full bandwidth); synchronous."""
+        n = len(self.solves)
+
+        def hp(x):
+            if hasattr(x, "data_ptr"):
+                return x.data_ptr()
+            assert x.dtype == np.float32 and x.flags.c_contiguous
+            return x.ctypes.data
+
+        a = (ctypes.c_void_p * n)(*[hp(t) for t in src])
+        b = (ctypes.c_void_p * n)(*[hp(t) for t in dst])
+        _check(load().lgf_conv_execute_host(self._h, a, b, _stream(stream)))
+
+    def ifactor(self, x, y, stream=None):
+        """IF plan: y = M E_Q(alpha) M x."""
+        _check(load().ifactor_apply(self._h, _ptr(x), _ptr(y), _stream(stream)))
+
+    def residual(self, solve: int, src, dst, stream=None) -> float:
+        out = ctypes.c_double()
+        _check(load().lgf_residual_fp64(self._h, int(solve), _ptr(src), _ptr(dst), ctypes.byref(out), _stream(stream)))
+        return out.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lgf_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def version() -> str:
+    return load().lgf_version().decode()
+
+
+def required_max_offset(src_blocks: np.ndarray, dst_blocks: np.ndarray, B: int) -> int:
+    """Smallest table max_offset a Poisson plan over these block lists needs
+    (half the zero-padded FFT length minus one, per the plan's size rule)."""
+    s = np.asarray(src_blocks).reshape(-1, 3)
+    t = np.asarray(dst_blocks).reshape(-1, 3)
+    need = 0
+    for a in range(3):
+        S0, S1 = s[:, a].min() * B, (s[:, a].max() + 1) * B - 1
+        T0, T1 = t[:, a].min() * B, (t[:, a].max() + 1) * B - 1
+        m = max(abs(T0 - S1), abs(T1 - S0))
+        n = 16
+        while n < 2 * m + 2:
+            n *= 2
+        need = max(need, n // 2 - 1)
+    return int(need)

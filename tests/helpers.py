@@ -1,0 +1,45 @@
+"""Test helpers: build-once fixtures and comparisons (tests only)."""
+import functools
+
+import numpy as np
+
+import oracle as O
+from paper_1601_00035_gb300 import inputs
+
+
+@functools.lru_cache(maxsize=1)
+def built():
+    from paper_1601_00035_gb300 import build
+    build.build()
+    from paper_1601_00035_gb300 import lgf
+    lgf.load()
+    return lgf
+
+
+def rel_l2(got, ref):
+    return float(np.linalg.norm(np.ravel(got) - np.ravel(ref)) / np.linalg.norm(np.ravel(ref)))
+
+
+def rel_linf(got, ref):
+    return float(np.abs(np.ravel(got) - np.ravel(ref)).max() / np.abs(np.ravel(ref)).max())
+
+
+def oracle_poisson_blocks(src_blocks_vals, src_coords, B, tgt_pts, K, comp=0, scale=1.0, dx=1.0):
+    """FP64 direct sum (eq. dpoisson_conv) with sources given block-contiguously.
+
+    src_blocks_vals: [nblk, ncomp, B, B, B]; returns u at tgt_pts ([n,3] x,y,z)."""
+    pts = inputs.block_points(src_coords, B)
+    vals = np.asarray(src_blocks_vals[:, comp], dtype=np.float64).reshape(-1)
+    nz = vals != 0
+    cube = O.lgf_cube(K)
+    return scale * dx * dx * O.direct_conv(cube, pts[nz], vals[nz], tgt_pts)
+
+
+def block_values_at(blocks_vals, coords, B, pts, comp=0):
+    """Values of a block-contiguous field at integer points (must lie in listed blocks)."""
+    lut = {tuple(c): i for i, c in enumerate(np.asarray(coords).tolist())}
+    out = np.empty(len(pts))
+    for j, (x, y, z) in enumerate(np.asarray(pts).tolist()):
+        i = lut[(x // B, y // B, z // B)]
+        out[j] = blocks_vals[i, comp, z % B, y % B, x % B]
+    return out

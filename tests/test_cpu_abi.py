@@ -1,0 +1,42 @@
+"""CPU-side checks of the C-ABI library: it builds for sm_103a, loads, and
+exports every function declared in include/lgf.h (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "lgf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*([a-z_0-9]+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for n in ["lgf_table_build", "lgf_conv_plan", "lgf_conv_execute", "ifactor_apply", "lgf_residual_fp64",
+              "lgf_last_error"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    if not os.path.exists("/usr/local/cuda/bin/nvcc") and not os.environ.get("NVCC"):
+        pytest.skip("no CUDA toolkit")
+    from paper_1601_00035_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    for n in _declared():
+        assert hasattr(lib, n), n
+    from paper_1601_00035_gb300 import lgf
+    lgf.load()
+    assert set(lgf._SIGS) == set(_declared())
+
+
+def test_required_max_offset():
+    import numpy as np
+    from paper_1601_00035_gb300 import lgf
+    b = np.array([[0, 0, 0], [7, 7, 7]])
+    assert lgf.required_max_offset(b, b, 16) == 127
