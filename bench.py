@@ -1,0 +1,351 @@
+"""Benchmark: unbounded LGF Poisson solve throughput on one GB300 (or N replicas).
+
+Workload (default): the 128^3 vector streamfunction solve a = -L^{-1} w of a
+tilted Gaussian-core vortex ring (R = 32, sigma = 3 cells, circulation 1),
+16^3 blocks, sources on the blocks where |w| > 1e-14 max, results on all 512
+blocks, FP32 data, seeded synthetic input.  One step = one lgf_conv_execute
+(all three components).  Points = target points x components.
+
+Timing: W warm-up steps, then exactly K steps, each bracketed by CUDA events
+on the launching stream; a 256 MiB buffer (> the 129 MB L2) is rewritten
+between steps, outside the events.  Barrier + synchronize on both sides; the
+max over ranks is reported.  Under torchrun every rank runs its own replica of
+the solve (weak scaling, no data-path collective).
+
+Extra keys: roofline (dominant kernel, bytes moved by that pass / its mean
+event time, against the measured HBM copy bandwidth), cpu_baseline (the FP64
+oracle's direct sum on a bounded sample of target points, host cores),
+e2e (the same solve through lgf_conv_execute_host with pinned host buffers,
+copies included), gpu_launches, clocks (nvidia-smi sampled during the run).
+
+--impl reference runs the FP64 CPU oracle (direct summation, the reference of
+this build) on the same workload, each step a bounded sample of target points.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mpoints/s per unbounded LGF Poisson solve at 1e-6 rel err; % of roofline"
+UNIT = "Mpoints/s"
+B = 16
+
+
+def workload():
+    from paper_1601_00035_gb300 import inputs
+    w, axis = inputs.ring_128()
+    src_c = inputs.active_blocks(w, B, 1e-14)
+    dst_c = inputs.block_grid(w.shape[1:], B)
+    f = inputs.to_blocks(w, B, src_c)
+    cfg = {"workload": "vortex-ring streamfunction a = -L^-1 w, 128^3 box, 3 components, 16^3 blocks",
+           "box": [128, 128, 128], "block": B, "components": 3, "src_blocks": int(len(src_c)),
+           "dst_blocks": int(len(dst_c)), "ring": {"R": 32, "sigma": 3, "gamma": 1, "axis": [round(float(a), 4) for a in axis]},
+           "source_threshold": "blocks with |w| > 1e-14 max"}
+    return f, src_c, dst_c, cfg
+
+
+def rank_info():
+    r = int(os.environ.get("RANK", "0"))
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    return r, ws, lr
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def clock_sampler(gpu_index: int):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        return subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except Exception:
+        return None
+
+
+def clock_summary(proc):
+    if proc is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    proc.terminate()
+    try:
+        out, _ = proc.communicate(timeout=5)
+    except Exception:
+        proc.kill()
+        out = ""
+    sms, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in out.strip().splitlines():
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sms.append(float(f[1]))
+            mx = float(f[2])
+        except ValueError:
+            continue
+        for n, v in zip(names, f[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(n)
+    return {"sm_mhz": statistics.median(sms) if sms else None, "sm_max_mhz": mx, "samples": len(sms),
+            "reasons": sorted(reasons)}
+
+
+def pass_bytes(plan_geom):
+    """Bytes each FFT pass must read and write (its own input and output arrays),
+    from the plan geometry; complex FP32 = 8 B, real FP32 = 4 B."""
+    g = plan_geom
+    nc, KX = g["ncomp"], g["N"][0] // 2 + 1
+    Es, Et, N = g["Es"], g["Et"], g["N"]
+    X1 = nc * Es[2] * Es[1] * KX * 8
+    X2 = nc * Es[2] * N[1] * KX * 8
+    X3 = nc * Et[2] * N[1] * KX * 8
+    X4 = nc * Et[2] * Et[1] * KX * 8
+    Kh = (N[0] // 2 + 1) * (N[1] // 2 + 1) * (N[2] // 2 + 1) * 4
+    src = g["nsrc"] * nc * B ** 3 * 4
+    dst = g["ndst"] * nc * B ** 3 * 4
+    return {"x_fwd_gather_r2c": src + X1, "y_fwd": X1 + X2, "z_fwd_mul_inv": X2 + Kh + X3, "y_inv": X3 + X4,
+            "x_inv_c2r_scatter": X4 + dst}
+
+
+def geometry(src_c, dst_c, ncomp):
+    s, t = np.asarray(src_c), np.asarray(dst_c)
+    Es = [int((s[:, a].max() - s[:, a].min() + 1) * B) for a in range(3)]
+    Et = [int((t[:, a].max() - t[:, a].min() + 1) * B) for a in range(3)]
+    N = []
+    for a in range(3):
+        S0, S1 = s[:, a].min() * B, (s[:, a].max() + 1) * B - 1
+        T0, T1 = t[:, a].min() * B, (t[:, a].max() + 1) * B - 1
+        m = max(abs(T0 - S1), abs(T1 - S0))
+        n = 16
+        while n < 2 * m + 2:
+            n *= 2
+        N.append(n)
+    return {"Es": Es, "Et": Et, "N": N, "ncomp": ncomp, "nsrc": len(s), "ndst": len(t)}
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
+    summary was taken on the current kernel source (sha256 prefix recorded)."""
+    path = os.path.join(ROOT, "profiles", "poisson_ring128_ncu.md")
+    src = os.path.join(ROOT, "paper_1601_00035_gb300", "csrc", "poisson.cu")
+    try:
+        txt = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    m = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
+    if not m or m.group(1) != sha:
+        return None
+    m = re.search(r"traffic\[%s\]:\s*([0-9.e+]+)" % re.escape(kernel), txt)
+    return float(m.group(1)) if m else None
+
+
+def cpu_oracle_rate(f, src_c, target_seconds: float, rng_seed: int = 11):
+    """Time the FP64 direct sum (the oracle, as it stands) on a bounded sample of
+    target points of the same workload; returns (Mpoints/s, points, seconds, threads)."""
+    import oracle as O
+    from paper_1601_00035_gb300 import inputs
+    cube = O.lgf_cube(127)
+    pts_src = inputs.block_points(src_c, B)
+    comps = []
+    for c in range(f.shape[1]):
+        v = f[:, c].reshape(-1).astype(np.float64)
+        nz = v != 0
+        comps.append((pts_src[nz], v[nz]))
+    rng = np.random.default_rng(rng_seed)
+
+    def run(n):
+        tgt = rng.integers(0, 128, size=(n, 3)).astype(np.int32)
+        t0 = time.perf_counter()
+        for sp, sv in comps:
+            O.direct_conv(cube, sp, -sv, tgt)
+        return time.perf_counter() - t0
+
+    t_small = run(24)
+    n = max(24, int(24 * target_seconds / max(t_small, 1e-3)))
+    dt = run(n)
+    pts = n * len(comps)
+    return pts / dt / 1e6, pts, dt, O.num_threads()
+
+
+def bench_reference(args):
+    r, ws, lr = rank_info()
+    if r != 0:
+        return 0
+    f, src_c, dst_c, cfg = workload()
+    per_step = float(os.environ.get("LGF_REF_STEP_SECONDS", "2.0"))
+    times, pts_tot = [], 0
+    for i in range(args.warmup + args.steps):
+        rate, pts, dt, thr = cpu_oracle_rate(f, src_c, per_step, rng_seed=100 + i)
+        if i >= args.warmup:
+            times.append(dt)
+            pts_tot += pts
+    total = sum(times)
+    value = pts_tot / total / 1e6
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
+                             "sample": "FP64 direct sum at %d random target points x 3 components per step "
+                                       "(~%.0f s of host work each)" % (pts_tot // len(times) // 3, per_step)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def bench_gpu(args):
+    import torch
+    r, ws, lr = rank_info()
+    dist = ws > 1
+    if dist:
+        import torch.distributed as tdist
+        torch.cuda.set_device(lr)
+        tdist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1601_00035_gb300 import build as libbuild
+    libbuild.build()
+    from paper_1601_00035_gb300 import lgf
+
+    f, src_c, dst_c, cfg = workload()
+    geom = geometry(src_c, dst_c, 3)
+    K = lgf.required_max_offset(src_c, dst_c, B)
+    table = lgf.Table(lgf.LAPLACE7, max_offset=K)
+    plan = lgf.Plan(table, [lgf.Solve(B, 3, src_c, dst_c, scale=-1.0)])
+    stream = torch.cuda.current_stream()
+    d_src = torch.from_numpy(f).cuda()
+    d_dst = torch.zeros((len(dst_c), 3, B, B, B), device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    pts_per_step = len(dst_c) * B ** 3 * 3
+
+    sampler = clock_sampler(torch.cuda.current_device()) if r == 0 else None
+    time.sleep(0.5)
+    for _ in range(args.warmup):
+        plan.execute([d_src], [d_dst])
+        flush.fill_(1.0)
+    torch.cuda.synchronize()
+    if dist:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    plan.set_profiling(2)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        plan.execute([d_src], [d_dst])
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    plan.set_profiling(0)
+    kt = plan.kernel_times()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([dev_ms], device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        dev_ms = float(t.item())
+        tdist.barrier()
+    torch.cuda.synchronize()
+    clocks = clock_summary(sampler) if r == 0 else None
+
+    # e2e: host (pinned) buffers through lgf_conv_execute_host, copies included
+    h_src = torch.from_numpy(f).pin_memory()
+    h_dst = torch.empty((len(dst_c), 3, B, B, B), dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, min(args.steps, 50))
+    for _ in range(2):
+        plan.execute_host([h_src], [h_dst])
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.execute_host([h_src], [h_dst])
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if r != 0:
+        if dist:
+            tdist.destroy_process_group()
+        return 0
+
+    value = pts_per_step * args.steps * ws / (dev_ms / 1e3) / 1e6
+    e2e_value = pts_per_step * e2e_steps * ws / e2e_s / 1e6
+    # roofline of the dominant kernel
+    pb = pass_bytes(geom)
+    dom = max(kt, key=lambda k: kt[k][1])
+    launches, tot_ms = kt[dom]
+    per_launch_ms = tot_ms / launches
+    hbm, src_kind = peaks()
+    achieved = pb[dom] / (per_launch_ms / 1e3) / 1e9
+    traffic = ncu_traffic(dom)
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "traffic": traffic,
+            "algorithmic_bytes_per_launch": pb[dom], "mean_launch_ms": round(per_launch_ms, 5),
+            "peak_source": src_kind + " (MEASURED_PEAKS.json hbm_gbs)" if src_kind == "measured" else src_kind}
+    shares = {k: {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / sum(x[1] for x in kt.values()), 4),
+                  "gbs": round(pb[k] * v[0] / (v[1] / 1e3) / 1e9, 1)} for k, v in kt.items()}
+    # CPU baseline: oracle on a bounded sample (rank 0, N=1 only)
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        rate, pts, dt, thr = cpu_oracle_rate(f, src_c, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": "FP64 direct sum (oracle) at %d random target points x 3 components, %.1f s" % (pts // 3, dt)}
+    cfg = dict(cfg)
+    cfg.update({"fft_grid": geom["N"], "l2": "256 MiB buffer rewritten between timed steps (outside the events)",
+                "precision": "FP32 data and FFTs; FP64 LGF table and kernel spectrum",
+                "parity": "rel L2 <= 1e-6 vs FP64 direct sum (tests/test_gpu_poisson.py)"})
+    line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(dev_ms / args.steps, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+            "roofline": roof, "kernels": shares, "cpu_baseline": cpu,
+            "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": int(f.nbytes),
+                    "d2h_bytes_per_step": int(h_dst.numel() * 4)},
+            "gpu_launches": int(sum(v[0] for v in kt.values())), "clocks": clocks,
+            "wall_s_timed_region": round(wall, 4)}
+    print(json.dumps(line))
+    if dist:
+        tdist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return bench_reference(args)
+    return bench_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -152,6 +152,18 @@ lgf_status ifactor_apply(lgf_plan *p, const float *x, float *y, void *stream);
 lgf_status lgf_residual_fp64(lgf_plan *p, int solve, const float *src, const float *dst,
                              double *rel_residual, void *stream);
 
+/* Diagnostics.  While profiling is enabled on a plan, every kernel launch made
+ * by lgf_conv_execute / lgf_conv_execute_host / ifactor_apply is bracketed by
+ * a pair of CUDA events recorded on the launching stream, and its device time
+ * and launch count are accumulated per kernel name (graph capture is bypassed
+ * while enabled).  enable = 0 stops recording; 2 also clears the totals. */
+lgf_status lgf_plan_set_profiling(lgf_plan *p, int enable);
+/* Number of kernel names with accumulated times (waits for pending events). */
+lgf_status lgf_plan_kernel_count(lgf_plan *p, int *count);
+/* Totals of kernel i (0 <= i < count): name (library-owned string, valid
+ * until the plan is destroyed), launches and summed device milliseconds. */
+lgf_status lgf_plan_kernel_times(lgf_plan *p, int i, const char **name, long long *launches, double *total_ms);
+
 void lgf_plan_destroy(lgf_plan *p);
 
 /* Thread-local description of the last non-OK status ("" if none). */

@@ -93,7 +93,11 @@ void free_plan(lgf_plan *p)
     cudaFree(p->d_wsA);
     cudaFree(p->d_wsB);
     cudaFree(p->d_acc);
-    cudaFree(p->d_nbr);
+    cudaFree(p->ifp.nbz);
+    cudaFree(p->ifp.nby);
+    cudaFree(p->ifp.nbx);
+    cudaFree(p->ifp.y1);
+    cudaFree(p->ifp.y2);
     if (p->graph) cudaGraphExecDestroy(p->graph);
     delete p;
 }
@@ -163,6 +167,72 @@ const double2 *twiddle_table_f64()
     std::lock_guard<std::mutex> lk(g_tw_mu);
     auto it = g_tw.find(current_device());
     return it == g_tw.end() ? nullptr : it->second.d;
+}
+
+
+int Profiler::rec_of(const char *name)
+{
+    for (size_t i = 0; i < recs.size(); i++)
+        if (recs[i].name == name) return (int)i;
+    recs.push_back(Rec{name, 0, 0.0});
+    return (int)recs.size() - 1;
+}
+
+cudaEvent_t Profiler::take()
+{
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+void Profiler::begin(cudaStream_t s)
+{
+    cur_a = take();
+    if (cur_a) cudaEventRecord(cur_a, s);
+}
+
+void Profiler::end(const char *name, cudaStream_t s)
+{
+    cudaEvent_t b = take();
+    if (!cur_a || !b) return;
+    cudaEventRecord(b, s);
+    pending.push_back(Pending{rec_of(name), cur_a, b});
+    cur_a = nullptr;
+}
+
+lgf_status Profiler::collect()
+{
+    for (auto &p : pending) {
+        LGF_CUDA_TRY(cudaEventSynchronize(p.b));
+        float ms = 0.f;
+        LGF_CUDA_TRY(cudaEventElapsedTime(&ms, p.a, p.b));
+        recs[p.rec].launches += 1;
+        recs[p.rec].ms += ms;
+        pool.push_back(p.a);
+        pool.push_back(p.b);
+    }
+    pending.clear();
+    return LGF_OK;
+}
+
+void Profiler::clear()
+{
+    collect();
+    recs.clear();
+}
+
+Profiler::~Profiler()
+{
+    for (auto &p : pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
 }
 
 }  // namespace lgf
@@ -237,6 +307,7 @@ lgf_status lgf_table_build(lgf_kernel kind, double alpha, int max_offset, void *
                 st = LGF_ERR_CUDA;
             } else {
                 for (int i = 0; i <= R; i++) hf[i] = (float)h[i];
+                t->h_taps32 = hf;
                 st = dalloc(&t->d_taps32, R + 1, bytes);
                 if (st == LGF_OK && cudaMemcpy(t->d_taps32, hf.data(), (R + 1) * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
                     set_error("taps upload failed");
@@ -414,19 +485,86 @@ static lgf_status plan_ifactor(lgf_plan *p, const lgf_table *t, const lgf_solve_
 {
     LGF_CHECK_ARG(n_solves == 1, "integrating-factor plans take exactly one block set (got %d)", n_solves);
     const lgf_solve_desc &d = solves[0];
-    LGF_CHECK_ARG(d.B == 8 || d.B == 16 || d.B == 32, "B=%d not in {8,16,32}", d.B);
+    LGF_CHECK_ARG(d.B == 8 || d.B == 16, "integrating factor: B=%d not in {8,16}", d.B);
     LGF_CHECK_ARG(d.ncomp >= 1 && d.ncomp <= 3, "ncomp=%d not in 1..3", d.ncomp);
     LGF_CHECK_ARG(d.n_src >= 1 && d.src_blocks, "empty block set");
     LGF_CHECK_ARG(coords_ok(d.src_blocks, d.n_src), "block coordinate out of range");
     LGF_CHECK_ARG(!has_duplicates(d.src_blocks, d.n_src), "duplicate block in the set");
-    LGF_CHECK_ARG(t->R <= d.B, "integrating-factor radius %d exceeds B=%d (alpha too large for this block size)", t->R, d.B);
+    LGF_CHECK_ARG(t->R <= d.B && t->R <= 16,
+                  "integrating-factor radius %d exceeds min(B=%d, 16) (alpha too large for this block size)", t->R, d.B);
     p->B = d.B;
     p->ncomp = d.ncomp;
     p->nblk = d.n_src;
     p->R = t->R;
-    std::vector<int> nbr = neighbour_table(d.src_blocks, d.n_src);
-    LGF_TRY(dalloc(&p->d_nbr, nbr.size(), p->bytes));
-    LGF_TRY(upload(p->d_nbr, nbr, s));
+    // block lists of the three passes (see ifactor.cu)
+    const int n = d.n_src;
+    const int32_t *c = d.src_blocks;
+    std::unordered_map<int64_t, int> S, A1, Z1, A2, YZ;
+    for (int i = 0; i < n; i++) S[pack(c[3 * i], c[3 * i + 1], c[3 * i + 2])] = i;
+    auto add = [](std::unordered_map<int64_t, int> &m, int32_t x, int32_t y, int32_t z) { m.emplace(pack(x, y, z), 0); };
+    for (int i = 0; i < n; i++) {
+        const int32_t x = c[3 * i], y = c[3 * i + 1], z = c[3 * i + 2];
+        for (int a = -1; a <= 1; a++) {
+            add(Z1, x, y, z + a);
+            add(A2, x + a, y, z);
+            for (int b = -1; b <= 1; b++) {
+                add(A1, x + a, y + b, z);
+                add(YZ, x, y + a, z + b);
+            }
+        }
+    }
+    std::vector<int32_t> L1, L2;
+    std::unordered_map<int64_t, int> L1i, L2i;
+    for (auto &kv : A1)
+        if (Z1.count(kv.first)) { L1i[kv.first] = 0; }
+    for (auto &kv : A2)
+        if (YZ.count(kv.first)) { L2i[kv.first] = 0; }
+    auto unpack = [](int64_t k, int32_t &x, int32_t &y, int32_t &z) {
+        const int64_t off = 1 << 20, m = (1 << 21) - 1;
+        x = (int32_t)(((k >> 42) & m) - off);
+        y = (int32_t)(((k >> 21) & m) - off);
+        z = (int32_t)((k & m) - off);
+    };
+    // deterministic order: sort keys
+    std::vector<int64_t> k1, k2;
+    for (auto &kv : L1i) k1.push_back(kv.first);
+    for (auto &kv : L2i) k2.push_back(kv.first);
+    std::sort(k1.begin(), k1.end());
+    std::sort(k2.begin(), k2.end());
+    for (size_t i = 0; i < k1.size(); i++) L1i[k1[i]] = (int)i;
+    for (size_t i = 0; i < k2.size(); i++) L2i[k2[i]] = (int)i;
+    auto find = [](const std::unordered_map<int64_t, int> &m, int32_t x, int32_t y, int32_t z) {
+        auto it = m.find(pack(x, y, z));
+        return it == m.end() ? -1 : it->second;
+    };
+    std::vector<int> nbz(3 * k1.size()), nby(3 * k2.size()), nbx(3 * (size_t)n);
+    for (size_t i = 0; i < k1.size(); i++) {
+        int32_t x, y, z;
+        unpack(k1[i], x, y, z);
+        for (int a = -1; a <= 1; a++) nbz[3 * i + a + 1] = find(S, x, y, z + a);
+    }
+    for (size_t i = 0; i < k2.size(); i++) {
+        int32_t x, y, z;
+        unpack(k2[i], x, y, z);
+        for (int a = -1; a <= 1; a++) nby[3 * i + a + 1] = find(L1i, x, y + a, z);
+    }
+    for (int i = 0; i < n; i++)
+        for (int a = -1; a <= 1; a++) nbx[3 * i + a + 1] = find(L2i, c[3 * i] + a, c[3 * i + 1], c[3 * i + 2]);
+    IfPlan &ip = p->ifp;
+    ip.B = d.B;
+    ip.R = t->R;
+    ip.n0 = n;
+    ip.n1 = (int)k1.size();
+    ip.n2 = (int)k2.size();
+    const size_t B3 = (size_t)d.B * d.B * d.B;
+    LGF_TRY(dalloc(&ip.nbz, nbz.size(), p->bytes));
+    LGF_TRY(dalloc(&ip.nby, nby.size(), p->bytes));
+    LGF_TRY(dalloc(&ip.nbx, nbx.size(), p->bytes));
+    LGF_TRY(upload(ip.nbz, nbz, s));
+    LGF_TRY(upload(ip.nby, nby, s));
+    LGF_TRY(upload(ip.nbx, nbx, s));
+    LGF_TRY(dalloc(&ip.y1, (size_t)ip.n1 * d.ncomp * B3, p->bytes));
+    LGF_TRY(dalloc(&ip.y2, (size_t)ip.n2 * d.ncomp * B3, p->bytes));
     return LGF_OK;
 }
 
@@ -474,10 +612,11 @@ lgf_status lgf_plan_workspace_bytes(const lgf_plan *p, size_t *bytes)
     return LGF_OK;
 }
 
-static lgf_status run_poisson(lgf_plan *p, const float *const *src, float *const *dst, cudaStream_t s)
+static lgf_status run_poisson(lgf_plan *p, const float *const *src, float *const *dst, cudaStream_t s,
+                              bool capturing = false)
 {
     for (size_t i = 0; i < p->solves.size(); i++)
-        LGF_TRY(poisson_launch(p->solves[i].g, src[i], dst[i], p->d_wsA, p->d_wsB, s));
+        LGF_TRY(poisson_launch(p->solves[i].g, src[i], dst[i], p->d_wsA, p->d_wsB, s, capturing ? nullptr : &p->prof));
     return LGF_OK;
 }
 
@@ -492,7 +631,7 @@ lgf_status lgf_conv_execute(lgf_plan *p, const float *const *src, float *const *
     for (size_t i = 0; i < p->solves.size(); i++)
         LGF_CHECK_ARG(src[i] && dst[i], "lgf_conv_execute: NULL buffer for solve %zu", i);
     cudaStream_t s = (cudaStream_t)stream;
-    if (!p->use_graph) return run_poisson(p, src, dst, s);
+    if (!p->use_graph || p->prof.on) return run_poisson(p, src, dst, s);
     // graph path: one captured launch sequence per distinct set of buffers
     std::vector<const void *> key;
     for (size_t i = 0; i < p->solves.size(); i++) {
@@ -512,7 +651,7 @@ lgf_status lgf_conv_execute(lgf_plan *p, const float *const *src, float *const *
             set_error("stream capture failed to start");
             st = LGF_ERR_CUDA;
         } else {
-            st = run_poisson(p, src, dst, cs);
+            st = run_poisson(p, src, dst, cs, true);
             cudaError_t e = cudaStreamEndCapture(cs, &gr);
             if (st == LGF_OK && e != cudaSuccess) {
                 set_error("stream capture failed: %s", cudaGetErrorString(e));
@@ -573,7 +712,7 @@ lgf_status ifactor_apply(lgf_plan *p, const float *x, float *y, void *stream)
         set_error("ifactor_apply: plan was not built from an integrating-factor table");
         return LGF_ERR_STATE;
     }
-    return ifactor_launch(p->B, p->ncomp, p->nblk, p->R, p->d_nbr, p->table->d_taps32, x, y, (cudaStream_t)stream);
+    return ifactor_launch(p->ifp, p->ncomp, p->table->h_taps32.data(), x, y, (cudaStream_t)stream, &p->prof);
 }
 
 lgf_status lgf_residual_fp64(lgf_plan *p, int solve, const float *src, const float *dst, double *rel_residual,
@@ -593,6 +732,36 @@ lgf_status lgf_residual_fp64(lgf_plan *p, int solve, const float *src, const flo
     LGF_CUDA_TRY(cudaMemcpyAsync(h, p->d_acc, sizeof(h), cudaMemcpyDeviceToHost, s));
     LGF_CUDA_TRY(cudaStreamSynchronize(s));
     *rel_residual = h[1] > 0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
+    return LGF_OK;
+}
+
+lgf_status lgf_plan_set_profiling(lgf_plan *p, int enable)
+{
+    clear_error();
+    LGF_CHECK_ARG(p != nullptr && enable >= 0 && enable <= 2, "lgf_plan_set_profiling: bad argument");
+    if (enable == 2) p->prof.clear();
+    p->prof.on = enable != 0;
+    return LGF_OK;
+}
+
+lgf_status lgf_plan_kernel_count(lgf_plan *p, int *count)
+{
+    clear_error();
+    LGF_CHECK_ARG(p && count, "lgf_plan_kernel_count: NULL argument");
+    LGF_TRY(p->prof.collect());
+    *count = (int)p->prof.recs.size();
+    return LGF_OK;
+}
+
+lgf_status lgf_plan_kernel_times(lgf_plan *p, int i, const char **name, long long *launches, double *total_ms)
+{
+    clear_error();
+    LGF_CHECK_ARG(p != nullptr, "lgf_plan_kernel_times: NULL plan");
+    LGF_TRY(p->prof.collect());
+    LGF_CHECK_ARG(i >= 0 && i < (int)p->prof.recs.size(), "lgf_plan_kernel_times: index %d out of range", i);
+    if (name) *name = p->prof.recs[i].name.c_str();
+    if (launches) *launches = p->prof.recs[i].launches;
+    if (total_ms) *total_ms = p->prof.recs[i].ms;
     return LGF_OK;
 }
 

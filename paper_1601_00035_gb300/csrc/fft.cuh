@@ -1,18 +1,22 @@
-// Batched 1-D complex FFTs of power-of-two length N (16..1024) on data held
-// in shared memory, in FP32 or FP64.
+// 1-D complex FFTs of power-of-two length N (16..1024) with the data held in
+// registers, for batches of lines processed by one thread block.
 //
-// Layout: a tile of LS lines, element n of line l at buf[n * LSP + l]
-// (LSP = LS + 1 to spread shared-memory banks).  Thread t works on line
-// l = t % LS as lane t / LS of G = blockDim / LS lanes.
+// A line is transformed by G lanes (threads); lane j holds E = N / G elements.
+// Algorithm: Stockham autosort, mixed radix R_0 .. R_{S-1} (product N).  In
+// stage s (span L = R_0 ... R_{s-1}) butterfly jb reads the elements at
+// positions jb + m N/R_s (m < R_s), multiplies element m by w_{R_s L}^{m (jb mod L)},
+// takes a length-R_s DFT and writes output q to position
+// (jb div L) R_s L + q L + (jb mod L).  Lane j owns butterflies jb = j + b G,
+// b < E / R_s, and keeps them in registers as v[b R_s + m].
 //
-// Algorithm: Stockham autosort with mixed radices (each stage one radix-R
-// butterfly per lane, R <= 32, done in registers by an unrolled radix-2
-// decimation-in-time DFT).  Stage with span L (product of earlier radices):
-// butterfly j reads x[j + m N/R], m < R, multiplies by w_{R L}^{m (j mod L)},
-// does a length-R DFT and writes y[(j div L) R L + q L + (j mod L)], q < R.
-// Forward transforms use w = exp(-2 pi i / N); inverse ones the conjugate
-// (unnormalised).  Every stage ends in __syncthreads(): all threads of the
-// block must call the line routines.
+// Between stages the elements move once through shared memory (write at the
+// output positions, barrier, read at the next input positions, barrier).
+// Before the first stage the caller loads v[b R_0 + m] = x[jb + m N/R_0]
+// directly; after the last stage v[b R + q] holds X[jb + q N/R] (R = R_{S-1}),
+// which is exactly the input layout of an inverse transform whose first
+// radix is R: a forward transform, a pointwise multiply and an inverse
+// transform (radices reversed) therefore chain in registers.  Forward uses
+// w = exp(-2 pi i/N), inverse the conjugate (unnormalised).
 #pragma once
 #include <cmath>
 
@@ -71,7 +75,7 @@ __host__ __device__ constexpr int bitrev(int i, int bits)
     return r;
 }
 
-// multiply v by w_len^k (conjugated for the inverse); k, len compile-time after unrolling
+// multiply v by w_len^k (conjugated for the inverse); k, len compile-time
 template <bool INV, typename T>
 __device__ __forceinline__ cx<T> twiddle_len(cx<T> v, int k, int len)
 {
@@ -79,145 +83,227 @@ __device__ __forceinline__ cx<T> twiddle_len(cx<T> v, int k, int len)
     if (4 * k == len) {  // w = -i (forward) or +i (inverse)
         return INV ? cx<T>{-v.y, v.x} : cx<T>{v.y, -v.x};
     }
+    if (8 * k == len || 8 * k == 3 * len) {
+        // w = h (s - i) forward, h (s + i) inverse, h = 1/sqrt2, s = +1 (k = len/8) or -1 (k = 3 len/8)
+        const T h = (T)0.70710678118654752440;
+        const T s = (8 * k == len) ? (T)1 : (T)-1;
+        if (!INV) return {h * (s * v.x + v.y), h * (s * v.y - v.x)};
+        return {h * (s * v.x - v.y), h * (s * v.y + v.x)};
+    }
     const cx<T> w = tw64<T>(k * (64 / len));
     return INV ? cmulc(v, w) : cmul(v, w);
 }
 
-// Bit-reversal permutation by template recursion, so every index is a
-// compile-time constant and the array stays in registers.
-template <int R, typename T, int I = 0>
-__device__ __forceinline__ void bitrev_perm(cx<T> (&a)[R])
+// Bit-reversal permutation by template recursion (compile-time indices).
+template <int R, typename T, int OFF, int I = 0>
+__device__ __forceinline__ void bitrev_perm(cx<T> *a)
 {
     if constexpr (I < R) {
         constexpr int J = bitrev(I, ilog2(R));
         if constexpr (J > I) {
-            const cx<T> t = a[I];
-            a[I] = a[J];
-            a[J] = t;
+            const cx<T> t = a[OFF + I];
+            a[OFF + I] = a[OFF + J];
+            a[OFF + J] = t;
         }
-        bitrev_perm<R, T, I + 1>(a);
+        bitrev_perm<R, T, OFF, I + 1>(a);
     }
 }
 
 // Butterflies of one radix-2 level (span LEN) by template recursion over (I, K).
-template <int R, bool INV, typename T, int LEN, int I = 0, int K = 0>
-__device__ __forceinline__ void level(cx<T> (&a)[R])
+template <int R, bool INV, typename T, int OFF, int LEN, int I = 0, int K = 0>
+__device__ __forceinline__ void level(cx<T> *a)
 {
     if constexpr (I < R) {
         if constexpr (K < LEN / 2) {
-            const cx<T> u = a[I + K];
-            const cx<T> v = twiddle_len<INV>(a[I + K + LEN / 2], K, LEN);
-            a[I + K] = u + v;
-            a[I + K + LEN / 2] = u - v;
-            level<R, INV, T, LEN, I, K + 1>(a);
+            const cx<T> u = a[OFF + I + K];
+            const cx<T> v = twiddle_len<INV>(a[OFF + I + K + LEN / 2], K, LEN);
+            a[OFF + I + K] = u + v;
+            a[OFF + I + K + LEN / 2] = u - v;
+            level<R, INV, T, OFF, LEN, I, K + 1>(a);
         } else {
-            level<R, INV, T, LEN, I + LEN, 0>(a);
+            level<R, INV, T, OFF, LEN, I + LEN, 0>(a);
         }
     }
 }
 
-template <int R, bool INV, typename T, int LEN = 2>
-__device__ __forceinline__ void levels(cx<T> (&a)[R])
+template <int R, bool INV, typename T, int OFF, int LEN = 2>
+__device__ __forceinline__ void levels(cx<T> *a)
 {
     if constexpr (LEN <= R) {
-        level<R, INV, T, LEN>(a);
-        levels<R, INV, T, LEN * 2>(a);
+        level<R, INV, T, OFF, LEN>(a);
+        levels<R, INV, T, OFF, LEN * 2>(a);
     }
 }
 
-// In-register DFT of length R (power of two, <= 32), natural order in and out
+// In-register DFT of length R on a[OFF .. OFF+R), natural order in and out
 // (radix-2 decimation in time).
-template <int R, bool INV, typename T>
-__device__ __forceinline__ void dft_reg(cx<T> (&a)[R])
+template <int R, bool INV, typename T, int OFF>
+__device__ __forceinline__ void dft_reg(cx<T> *a)
 {
-    bitrev_perm<R, T>(a);
-    levels<R, INV, T>(a);
+    bitrev_perm<R, T, OFF>(a);
+    levels<R, INV, T, OFF>(a);
 }
 
-// One Stockham stage of radix R and span L on every line of the tile.
-// tw: shared table of w_N^j, j < N.
-template <int N, int R, int L, bool INV, typename T>
-__device__ __forceinline__ void stage(cx<T> *buf, const cx<T> *tw, int LSP, int l, int lane, bool line_ok)
-{
-    constexpr int NB = N / R;
-    constexpr int STEP = N / (R * L);
-    cx<T> a[R];
-    const bool active = line_ok && lane < NB;
-    const int j = lane;
-    const int k = j % L;
-    if (active) {
-#pragma unroll
-        for (int m = 0; m < R; m++) a[m] = buf[(j + m * NB) * LSP + l];
-        if (L > 1) {
-#pragma unroll
-            for (int m = 1; m < R; m++) {
-                const cx<T> w = tw[(m * k * STEP) % N];
-                a[m] = INV ? cmulc(a[m], w) : cmul(a[m], w);
-            }
-        }
-        dft_reg<R, INV>(a);
-    }
-    __syncthreads();
-    if (active) {
-        const int base = (j / L) * R * L + k;
-#pragma unroll
-        for (int q = 0; q < R; q++) buf[(base + q * L) * LSP + l] = a[q];
-    }
-    __syncthreads();
-}
-
-template <int N, int L, bool INV, typename T, int R, int... Rest>
-__device__ __forceinline__ void stages(cx<T> *buf, const cx<T> *tw, int LSP, int l, int lane, bool line_ok)
-{
-    stage<N, R, L, INV, T>(buf, tw, LSP, l, lane, line_ok);
-    if constexpr (sizeof...(Rest) > 0) stages<N, L * R, INV, T, Rest...>(buf, tw, LSP, l, lane, line_ok);
-}
-
-// Radix plans and the lanes each line needs (max butterflies in a stage).
+// G lanes per line, E = N / G elements per lane, radices (forward order).
 template <int N>
 struct Plan;
 template <>
 struct Plan<16> {
-    static constexpr int lanes = 1;
+    static constexpr int G = 1, E = 16, S = 1;
+    static constexpr int R[1] = {16};
 };
 template <>
 struct Plan<32> {
-    static constexpr int lanes = 1;
+    static constexpr int G = 1, E = 32, S = 1;
+    static constexpr int R[1] = {32};
 };
 template <>
 struct Plan<64> {
-    static constexpr int lanes = 8;
+    static constexpr int G = 8, E = 8, S = 2;
+    static constexpr int R[2] = {8, 8};
 };
 template <>
 struct Plan<128> {
-    static constexpr int lanes = 16;
+    static constexpr int G = 8, E = 16, S = 2;
+    static constexpr int R[2] = {16, 8};
 };
 template <>
 struct Plan<256> {
-    static constexpr int lanes = 16;
+    static constexpr int G = 16, E = 16, S = 2;
+    static constexpr int R[2] = {16, 16};
 };
 template <>
 struct Plan<512> {
-    static constexpr int lanes = 64;
+    static constexpr int G = 64, E = 8, S = 3;
+    static constexpr int R[3] = {8, 8, 8};
 };
 template <>
 struct Plan<1024> {
-    static constexpr int lanes = 128;
+    static constexpr int G = 64, E = 16, S = 3;
+    static constexpr int R[3] = {16, 16, 4};
 };
 
-// Transform every line of the tile in place.  line_ok masks partial tiles
-// (inactive lines still take part in the barriers).
-template <int N, bool INV, typename T>
-__device__ __forceinline__ void line_fft(cx<T> *buf, const cx<T> *tw, int LSP, int l, int lane, bool line_ok)
+// Radix and span of stage s of the forward (INV = false) or inverse
+// (INV = true, radices reversed) transform.
+template <int N, bool INV>
+__host__ __device__ constexpr int radix(int s)
 {
-    if constexpr (N == 16) stages<N, 1, INV, T, 16>(buf, tw, LSP, l, lane, line_ok);
-    else if constexpr (N == 32) stages<N, 1, INV, T, 32>(buf, tw, LSP, l, lane, line_ok);
-    else if constexpr (N == 64) stages<N, 1, INV, T, 8, 8>(buf, tw, LSP, l, lane, line_ok);
-    else if constexpr (N == 128) stages<N, 1, INV, T, 16, 8>(buf, tw, LSP, l, lane, line_ok);
-    else if constexpr (N == 256) stages<N, 1, INV, T, 16, 16>(buf, tw, LSP, l, lane, line_ok);
-    else if constexpr (N == 512) stages<N, 1, INV, T, 8, 8, 8>(buf, tw, LSP, l, lane, line_ok);
-    else if constexpr (N == 1024) stages<N, 1, INV, T, 16, 8, 8>(buf, tw, LSP, l, lane, line_ok);
-    else static_assert(N == 16, "unsupported FFT length");
+    return INV ? Plan<N>::R[Plan<N>::S - 1 - s] : Plan<N>::R[s];
+}
+template <int N, bool INV>
+__host__ __device__ constexpr int span(int s)
+{
+    int L = 1;
+    for (int i = 0; i < s; i++) L *= radix<N, INV>(i);
+    return L;
+}
+
+// Shared-memory addressing of element `pos` of line `l`:
+//   LINE_FAST (threads of a warp run across lines):  pos * LSP + l
+//   lane-fast (threads of a warp run along a line):   l * NP + pos + pos / 32
+template <int N, bool LINE_FAST>
+struct Smem {
+    int LSP;
+    static constexpr int NP = N + (N >= 32 ? N / 32 : 1);
+    __device__ __forceinline__ int at(int pos, int l) const
+    {
+        if constexpr (LINE_FAST) return pos * LSP + l;
+        else return l * NP + pos + pos / 32;
+    }
+};
+
+template <int N, bool INV, int s, typename T, int b = 0>
+__device__ __forceinline__ void dft_all(cx<T> (&v)[Plan<N>::E])
+{
+    constexpr int R = radix<N, INV>(s);
+    if constexpr (b < Plan<N>::E / R) {
+        dft_reg<R, INV, T, b * R>(v);
+        dft_all<N, INV, s, T, b + 1>(v);
+    }
+}
+
+// Stage s: twiddles (s > 0) and the DFTs, all in registers.
+template <int N, bool INV, int s, typename T>
+__device__ __forceinline__ void stage_compute(cx<T> (&v)[Plan<N>::E], const cx<T> *tw, int j)
+{
+    constexpr int R = radix<N, INV>(s);
+    constexpr int L = span<N, INV>(s);
+    constexpr int STEP = N / (R * L);
+    constexpr int G = Plan<N>::G;
+    if constexpr (L > 1) {
+#pragma unroll
+        for (int b = 0; b < Plan<N>::E / R; b++) {
+            const int k = (j + b * G) % L;
+#pragma unroll
+            for (int m = 1; m < R; m++) {
+                const cx<T> w = tw[m * k * STEP];
+                v[b * R + m] = INV ? cmulc(v[b * R + m], w) : cmul(v[b * R + m], w);
+            }
+        }
+    }
+    dft_all<N, INV, s, T>(v);
+}
+
+// Move from the output layout of stage s to the input layout of stage s+1.
+template <int N, bool INV, int s, bool LINE_FAST, typename T>
+__device__ __forceinline__ void exchange(cx<T> (&v)[Plan<N>::E], cx<T> *buf, Smem<N, LINE_FAST> sm, int l, int j)
+{
+    constexpr int R = radix<N, INV>(s);
+    constexpr int L = span<N, INV>(s);
+    constexpr int R2 = radix<N, INV>(s + 1);
+    constexpr int G = Plan<N>::G;
+    constexpr int E = Plan<N>::E;
+#pragma unroll
+    for (int b = 0; b < E / R; b++) {
+        const int jb = j + b * G;
+        const int base = (jb / L) * R * L + (jb % L);
+#pragma unroll
+        for (int q = 0; q < R; q++) buf[sm.at(base + q * L, l)] = v[b * R + q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < E / R2; b++) {
+        const int jb = j + b * G;
+#pragma unroll
+        for (int m = 0; m < R2; m++) v[b * R2 + m] = buf[sm.at(jb + m * (N / R2), l)];
+    }
+    __syncthreads();
+}
+
+// The whole transform: registers in (input layout of stage 0), registers out
+// (output layout of the last stage).  Every thread of the block must call it.
+template <int N, bool INV, bool LINE_FAST, typename T, int s = 0>
+__device__ __forceinline__ void transform(cx<T> (&v)[Plan<N>::E], cx<T> *buf, const cx<T> *tw,
+                                          Smem<N, LINE_FAST> sm, int l, int j)
+{
+    if constexpr (s < Plan<N>::S) {
+        stage_compute<N, INV, s, T>(v, tw, j);
+        if constexpr (s + 1 < Plan<N>::S) exchange<N, INV, s, LINE_FAST, T>(v, buf, sm, l, j);
+        transform<N, INV, LINE_FAST, T, s + 1>(v, buf, tw, sm, l, j);
+    }
+}
+
+// Position of register element e before the first stage / after the last.
+template <int N, bool INV>
+__host__ __device__ constexpr int in_pos(int e, int j)
+{
+    constexpr int R = radix<N, INV>(0);
+    return (j + (e / R) * Plan<N>::G) + (e % R) * (N / R);
+}
+template <int N, bool INV>
+__host__ __device__ constexpr int out_pos(int e, int j)
+{
+    constexpr int R = radix<N, INV>(Plan<N>::S - 1);
+    return (j + (e / R) * Plan<N>::G) + (e % R) * (N / R);
+}
+// Whether input element e can be non-zero when only positions < N/2 carry
+// data (true for every forward transform here: the data extent is <= N/2).
+// Lane-independent when N/R_0 divides N/2, which holds for every plan.
+template <int N, bool INV>
+__host__ __device__ constexpr bool in_lower_half(int e)
+{
+    constexpr int R = radix<N, INV>(0);
+    return (e % R) * (N / R) < N / 2;
 }
 
 // Load w_N^j (j < N) into shared memory from the 1024-entry global table.
@@ -226,18 +312,10 @@ __device__ __forceinline__ void load_twiddles(cx<T> *tw_s, const void *tw_global
 {
     static_assert(N <= TW_MAX, "N too large");
     constexpr int STRIDE = TW_MAX / N;
-    if constexpr (sizeof(T) == 4) {
-        const float2 *g = (const float2 *)tw_global;
-        for (int j = threadIdx.x; j < N; j += blockDim.x) {
-            float2 w = __ldg(g + j * STRIDE);
-            tw_s[j] = {w.x, w.y};
-        }
-    } else {
-        const double2 *g = (const double2 *)tw_global;
-        for (int j = threadIdx.x; j < N; j += blockDim.x) {
-            double2 w = __ldg(g + j * STRIDE);
-            tw_s[j] = {w.x, w.y};
-        }
+    const float2 *g = (const float2 *)tw_global;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        float2 w = __ldg(g + j * STRIDE);
+        tw_s[j] = {(T)w.x, (T)w.y};
     }
 }
 

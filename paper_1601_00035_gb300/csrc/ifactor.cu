@@ -1,115 +1,167 @@
 // Integrating factor y = M E_Q(alpha) M x (Sec. 2.3 eq. if_def; Sec. 4.4),
 // evaluated in real space as the convolution with the separable kernel
 // prod_i g(n_i), g(k) = e^{-2 alpha} I_k(2 alpha) (App. B eq. lgf_intfac),
-// truncated to |n_i| <= R (R <= B).  M keeps the block set and zeroes the rest.
+// truncated to the box |n_i| <= R (R <= min(B, 16); B in {8, 16}).  M keeps the block set S
+// and zeroes everything else.
 //
-// One thread block per (block, component); one thread per (x, y) column.
-// The kernel marches through the input slices z_in in [-R, B + R): each slice
-// of (B + 2R)^2 values is staged in shared memory from the up-to-9 blocks
-// that cover it at that height (zeros where no block exists), filtered along
-// x, then along y, and the resulting value is scattered into the B outputs
-// of the thread's column with the z taps (kept in registers).  HBM traffic is
-// one read of every input block (halo reads hit L2) and one write.
+// The box kernel factorises, so the sum is taken as three 1-D passes
+//   y1 = g *_z x,   y2 = g *_y y1,   y = g *_x y2,
+// which is the same finite sum in another order.  With x zero outside S the
+// intermediates are needed, and non-zero, only on small dilations of S:
+//   y1 on L1 = (S + {dx,dy}) n (S + {dz}),
+//   y2 on L2 = (S + {dx})    n (S + {dy,dz}),
+//   y  on S,
+// (block offsets in {-1,0,1}); the plan builds L1, L2 and the neighbour
+// tables along each pass axis.  A block missing from a pass's input list is
+// zero there.
+//
+// Each pass: one thread block per output block, one thread per line along the
+// pass axis; the thread loads its B + 2R inputs (own block plus both
+// neighbours) into registers and produces its B outputs with the symmetric
+// taps (g0 v + sum_d g_d (v_{+d} + v_{-d})).  Taps travel as kernel parameters
+// (constant bank), padded with zeros up to the instantiated radius RM.
 #include "plan.hpp"
 
 namespace lgf {
 namespace {
 
-template <int B>
-__global__ void __launch_bounds__(B *B) k_ifactor(const float *__restrict__ x, float *__restrict__ y,
-                                                  const int *__restrict__ nbr, const float *__restrict__ taps,
-                                                  int ncomp, int R)
+template <int RM>
+struct Taps {
+    float g[RM + 1];
+};
+
+// AXIS 2: z pass (thread per (x, y)), AXIS 1: y pass (thread per (x, z)),
+// AXIS 0: x pass (thread per (y, z), rows read as aligned float4 groups).
+template <int B, int RM, int AXIS>
+__global__ void __launch_bounds__(B *B) k_if_pass(const float *__restrict__ in, float *__restrict__ out,
+                                                  const int *__restrict__ nbr3, int ncomp, Taps<RM> t)
 {
-    extern __shared__ float sm[];
-    const int W = B + 2 * R;
-    float *S = sm;                 // [W][W] input slice
-    float *T = S + W * W;          // [W][B] after the x pass
-    float *g = T + W * B;          // [R + 1] taps
-    const int blk = blockIdx.x;
+    const int ob = blockIdx.x;  // output block
     const int c = blockIdx.y;
-    const int tx = threadIdx.x % B, ty = threadIdx.x / B;
-    for (int i = threadIdx.x; i <= R; i += blockDim.x) g[i] = taps[i];
-    __shared__ int nb[27];
-    if (threadIdx.x < 27) nb[threadIdx.x] = nbr[blk * 27 + threadIdx.x];
-
-    float acc[B];
+    const int a = threadIdx.x % B, b = threadIdx.x / B;
+    const int n_lo = __ldg(nbr3 + 3 * ob), n_mid = __ldg(nbr3 + 3 * ob + 1), n_hi = __ldg(nbr3 + 3 * ob + 2);
+    constexpr int W = B + 2 * RM;
+    float v[W];
+    if constexpr (AXIS == 0) {
+        // v[k] = value at x = k - RM of row (y = a, z = b); rows of neighbours as float4
+        constexpr int Q = B / 4;
+        float rl[B], rm[B], rh[B];
+        auto row = [&](int n, float *r) {
+            if (n >= 0) {
+                const float4 *p = reinterpret_cast<const float4 *>(in + ((size_t)(n * ncomp + c) * B + b) * B * B + a * B);
 #pragma unroll
-    for (int z = 0; z < B; z++) acc[z] = 0.f;
-    __syncthreads();
-
-    for (int zin = -R; zin < B + R; zin++) {
-        const int dz = zin < 0 ? -1 : (zin >= B ? 1 : 0);
-        const int zl = zin - dz * B;
-        for (int i = threadIdx.x; i < W * W; i += blockDim.x) {
-            const int yy = i / W - R, xx = i % W - R;
-            const int dy = yy < 0 ? -1 : (yy >= B ? 1 : 0);
-            const int dxb = xx < 0 ? -1 : (xx >= B ? 1 : 0);
-            const int n = nb[(dz + 1) * 9 + (dy + 1) * 3 + (dxb + 1)];
-            float v = 0.f;
-            if (n >= 0) v = __ldg(x + ((size_t)(n * ncomp + c) * B + zl) * B * B + (yy - dy * B) * B + (xx - dxb * B));
-            S[i] = v;
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < W * B; i += blockDim.x) {
-            const int yy = i / B, xo = i % B;
-            const float *row = S + yy * W + xo + R;
-            float s = g[0] * row[0];
-            for (int d = 1; d <= R; d++) s = fmaf(g[d], row[d] + row[-d], s);
-            T[i] = s;
-        }
-        __syncthreads();
-        {
-            const float *col = T + (ty + R) * B + tx;
-            float v = g[0] * col[0];
-            for (int d = 1; d <= R; d++) v = fmaf(g[d], col[d * B] + col[-d * B], v);
+                for (int q = 0; q < Q; q++) {
+                    const float4 w = __ldg(p + q);
+                    r[4 * q] = w.x;
+                    r[4 * q + 1] = w.y;
+                    r[4 * q + 2] = w.z;
+                    r[4 * q + 3] = w.w;
+                }
+            } else {
 #pragma unroll
-            for (int z = 0; z < B; z++) {
-                const int d = z - zin;
-                const int ad = d < 0 ? -d : d;
-                if (ad <= R) acc[z] = fmaf(g[ad], v, acc[z]);
+                for (int q = 0; q < B; q++) r[q] = 0.f;
             }
-        }
-        __syncthreads();
-    }
-    float *out = y + ((size_t)(blk * ncomp + c) * B) * B * B + ty * B + tx;
+        };
+        row(n_mid, rm);
+        row(RM > 0 ? n_lo : -1, rl);
+        row(RM > 0 ? n_hi : -1, rh);
 #pragma unroll
-    for (int z = 0; z < B; z++) out[(size_t)z * B * B] = acc[z];
+        for (int k = 0; k < W; k++) {
+            const int x = k - RM;
+            v[k] = x < 0 ? rl[x + B] : (x < B ? rm[x] : rh[x - B]);
+        }
+    } else {
+        const size_t cs = (size_t)B * B * B;
+        const float *pm = in + (size_t)(n_mid >= 0 ? n_mid : 0) * ncomp * cs + (size_t)c * cs;
+        const float *pl = in + (size_t)(n_lo >= 0 ? n_lo : 0) * ncomp * cs + (size_t)c * cs;
+        const float *ph = in + (size_t)(n_hi >= 0 ? n_hi : 0) * ncomp * cs + (size_t)c * cs;
+        // element (line index j along the axis) of this thread's line
+        auto off = [&](int j) -> int {
+            if constexpr (AXIS == 2) return j * B * B + b * B + a;  // (x=a, y=b, z=j)
+            else return b * B * B + j * B + a;                     // (x=a, y=j, z=b)
+        };
+#pragma unroll
+        for (int k = 0; k < W; k++) {
+            const int j = k - RM;
+            float val = 0.f;
+            if (j < 0) {
+                if (n_lo >= 0) val = __ldg(pl + off(j + B));
+            } else if (j < B) {
+                if (n_mid >= 0) val = __ldg(pm + off(j));
+            } else {
+                if (n_hi >= 0) val = __ldg(ph + off(j - B));
+            }
+            v[k] = val;
+        }
+    }
+    float r[B];
+#pragma unroll
+    for (int j = 0; j < B; j++) {
+        float s = t.g[0] * v[j + RM];
+#pragma unroll
+        for (int d = 1; d <= RM; d++) s = fmaf(t.g[d], v[j + RM + d] + v[j + RM - d], s);
+        r[j] = s;
+    }
+    float *o = out + (size_t)(ob * ncomp + c) * B * B * B;
+    if constexpr (AXIS == 0) {
+        float4 *p = reinterpret_cast<float4 *>(o + (size_t)b * B * B + a * B);
+#pragma unroll
+        for (int q = 0; q < B / 4; q++) p[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < B; j++) {
+            if constexpr (AXIS == 2) o[(size_t)j * B * B + b * B + a] = r[j];
+            else o[(size_t)b * B * B + j * B + a] = r[j];
+        }
+    }
+}
+
+template <int B, int RM>
+lgf_status launch3(const IfPlan &ip, int ncomp, const float *taps, const float *x, float *y, cudaStream_t s,
+                   Profiler *prof)
+{
+    Taps<RM> t;
+    for (int i = 0; i <= RM; i++) t.g[i] = i <= ip.R ? taps[i] : 0.f;
+    const bool P = prof && prof->on;
+    if (P) prof->begin(s);
+    k_if_pass<B, RM, 2><<<dim3(ip.n1, ncomp), B * B, 0, s>>>(x, ip.y1, ip.nbz, ncomp, t);
+    LGF_LAUNCH_CHECK("if_z_pass");
+    if (P) prof->end("if_z_pass", s);
+    if (P) prof->begin(s);
+    k_if_pass<B, RM, 1><<<dim3(ip.n2, ncomp), B * B, 0, s>>>(ip.y1, ip.y2, ip.nby, ncomp, t);
+    LGF_LAUNCH_CHECK("if_y_pass");
+    if (P) prof->end("if_y_pass", s);
+    if (P) prof->begin(s);
+    k_if_pass<B, RM, 0><<<dim3(ip.n0, ncomp), B * B, 0, s>>>(ip.y2, y, ip.nbx, ncomp, t);
+    LGF_LAUNCH_CHECK("if_x_pass");
+    if (P) prof->end("if_x_pass", s);
+    return LGF_OK;
 }
 
 }  // namespace
 
-lgf_status ifactor_launch(int B, int ncomp, int nblk, int R, const int *d_nbr, const float *d_taps, const float *x,
-                          float *y, cudaStream_t s)
+lgf_status ifactor_launch(const IfPlan &ip, int ncomp, const float *h_taps, const float *x, float *y, cudaStream_t s,
+                          Profiler *prof)
 {
-    if (R > B) {
-        set_error("integrating-factor radius %d exceeds the block size %d", R, B);
+    const int B = ip.B, R = ip.R;
+    if (R > B || R > 16) {
+        set_error("integrating-factor radius %d exceeds min(B=%d, 16)", R, B);
         return LGF_ERR_ARG;
     }
-    const int W = B + 2 * R;
-    const size_t smem = (size_t)(W * W + W * B + R + 1) * sizeof(float);
-    dim3 grid(nblk, ncomp);
+    const int RM = R <= 4 ? 4 : (R <= 8 ? 8 : (R <= 12 ? 12 : 16));
     switch (B) {
         case 8:
-            k_ifactor<8><<<grid, 64, smem, s>>>(x, y, d_nbr, d_taps, ncomp, R);
-            break;
+            if (RM == 4) return launch3<8, 4>(ip, ncomp, h_taps, x, y, s, prof);
+            return launch3<8, 8>(ip, ncomp, h_taps, x, y, s, prof);
         case 16:
-            k_ifactor<16><<<grid, 256, smem, s>>>(x, y, d_nbr, d_taps, ncomp, R);
-            break;
-        case 32:
-            if (smem > 48 * 1024) {
-                if (cudaFuncSetAttribute(k_ifactor<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-                    set_error("cannot raise shared memory for B=32");
-                    return LGF_ERR_CUDA;
-                }
-            }
-            k_ifactor<32><<<grid, 1024, smem, s>>>(x, y, d_nbr, d_taps, ncomp, R);
-            break;
+            if (RM == 4) return launch3<16, 4>(ip, ncomp, h_taps, x, y, s, prof);
+            if (RM == 8) return launch3<16, 8>(ip, ncomp, h_taps, x, y, s, prof);
+            if (RM == 12) return launch3<16, 12>(ip, ncomp, h_taps, x, y, s, prof);
+            return launch3<16, 16>(ip, ncomp, h_taps, x, y, s, prof);
         default:
             set_error("unsupported block size %d", B);
             return LGF_ERR_ARG;
     }
-    LGF_LAUNCH_CHECK("ifactor");
-    return LGF_OK;
 }
 
 }  // namespace lgf

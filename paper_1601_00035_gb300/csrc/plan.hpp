@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -42,9 +43,34 @@ struct Spectrum {
     float *d_Kh = nullptr;
 };
 
+// Optional per-kernel event timing (lgf_plan_set_profiling).
+struct Profiler {
+    bool on = false;
+    struct Rec {
+        std::string name;
+        long long launches = 0;
+        double ms = 0.0;
+    };
+    std::vector<Rec> recs;
+    struct Pending {
+        int rec;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t cur_a = nullptr;
+    int rec_of(const char *name);
+    cudaEvent_t take();
+    void begin(cudaStream_t s);               // before a launch
+    void end(const char *name, cudaStream_t s);  // after it
+    lgf_status collect();                     // wait for pending pairs, accumulate
+    void clear();
+    ~Profiler();
+};
+
 // launchers (poisson.cu)
 lgf_status poisson_launch(const Geom &g, const float *src, float *dst, cx<float> *wsA, cx<float> *wsB,
-                          cudaStream_t s);
+                          cudaStream_t s, Profiler *prof = nullptr);
 bool poisson_supported_n(int n);
 lgf_status poisson_prepare();  // per-device constant tables; call outside stream capture
 int poisson_pick_n(int need);  // smallest supported FFT length >= need, 0 if none
@@ -56,9 +82,17 @@ lgf_status build_spectrum(const double *d_octant, int K, const int N[3], float *
 lgf_status build_lgf_octant(int K, double *d_out, cudaStream_t s);
 lgf_status build_if_taps(double alpha, double tol, double *d_taps, int max_r, int *R_out, cudaStream_t s);
 
-// integrating factor (ifactor.cu)
-lgf_status ifactor_launch(int B, int ncomp, int nblk, int R, const int *d_nbr, const float *d_taps,
-                          const float *x, float *y, cudaStream_t s);
+// integrating factor (ifactor.cu): block lists of the three passes
+struct IfPlan {
+    int B = 0, R = 0;
+    int n0 = 0, n1 = 0, n2 = 0;          // |S|, |L1|, |L2|
+    int *nbz = nullptr;                  // [n1][3]: S index of block L1[i] + (0,0,-1..1), -1 if absent
+    int *nby = nullptr;                  // [n2][3]: L1 index of block L2[i] + (0,-1..1,0)
+    int *nbx = nullptr;                  // [n0][3]: L2 index of block S[i] + (-1..1,0,0)
+    float *y1 = nullptr, *y2 = nullptr;  // intermediates [n1|n2][ncomp][B^3]
+};
+lgf_status ifactor_launch(const IfPlan &ip, int ncomp, const float *h_taps, const float *x, float *y, cudaStream_t s,
+                          Profiler *prof = nullptr);
 
 // residual (residual.cu)
 lgf_status residual_launch(const PoissonSolve &ps, const float *src, const float *dst, double *d_acc,
@@ -75,6 +109,7 @@ struct lgf_table {
     int64_t n;       // number of doubles
     double *d_vals;  // FP64 values on the device
     float *d_taps32; // IF: FP32 copy of the taps
+    std::vector<float> h_taps32;  // IF: host copy (kernel parameters)
 };
 
 struct lgf_plan {
@@ -89,10 +124,11 @@ struct lgf_plan {
     double *d_acc = nullptr;  // residual accumulators
     // IF
     int B = 0, ncomp = 0, nblk = 0, R = 0;
-    int *d_nbr = nullptr;  // [nblk][27]
+    lgf::IfPlan ifp;
     // graph capture
     int use_graph = 0;
     cudaGraphExec_t graph = nullptr;
     std::vector<const void *> graph_key;
+    lgf::Profiler prof;
     size_t bytes = 0;
 };

@@ -5,7 +5,7 @@
 // The kernel samples G(wrap(j)) are real and even, so their spectrum is real
 // and even and only its octant is stored (built in FP64, spectrum.cu).
 //
-// Five passes, each a batch of 1-D FFTs on shared-memory tiles (fft.cuh):
+// Five passes, each a batch of register-resident 1-D FFTs (fft.cuh):
 //   x_fwd : gather source rows from the block list (two real rows packed into
 //           one complex line), R2C along x                 src -> A[c][z][y][kx]
 //   y_fwd : along y (input rows beyond the source box are zero)  A -> B[c][z][ky][kx]
@@ -23,14 +23,22 @@ namespace lgf {
 
 namespace {
 
-constexpr int kThreads = 256;
+using fft::Plan;
 
+// Lines per block: y/z passes run LS consecutive kx lines (line-fast thread
+// mapping, coalesced rows of kx); x passes run whole rows (lane-fast mapping).
 template <int N>
-struct Tile {
-    static constexpr int G = fft::Plan<N>::lanes;          // lanes per line
-    static constexpr int LS = (kThreads / G) < 64 ? (kThreads / G) : 64;  // lines per block
+struct TileY {
+    static constexpr int G = Plan<N>::G;
+    static constexpr int LS = G == 1 ? 64 : (G >= 64 ? 8 : (G == 8 ? 32 : 16));
     static constexpr int LSP = LS + 1;
     static constexpr int threads = LS * G;
+};
+template <int N>
+struct TileX {
+    static constexpr int G = Plan<N>::G;
+    static constexpr int threads = G == 1 ? 64 : 256;
+    static constexpr int LS = threads / G;
 };
 
 __device__ __forceinline__ int wrap_mod(int v, int n)
@@ -40,191 +48,205 @@ __device__ __forceinline__ int wrap_mod(int v, int n)
 }
 
 // ---------------------------------------------------------------------------
+// x forward: gather two source rows per complex line from the block list, R2C.
 template <int N>
-__global__ void __launch_bounds__(Tile<N>::threads) k_x_fwd(Geom g, const float *__restrict__ src,
-                                                             cx<float> *__restrict__ out, const float2 *tw_g)
+__global__ void __launch_bounds__(TileX<N>::threads) k_x_fwd(Geom g, const float *__restrict__ src,
+                                                              cx<float> *__restrict__ out, const float2 *tw_g)
 {
-    using TL = Tile<N>;
-    __shared__ cx<float> buf[N * TL::LSP];
+    using TL = TileX<N>;
+    constexpr int E = Plan<N>::E;
+    using SM = fft::Smem<N, false>;
+    __shared__ cx<float> buf[TL::LS * SM::NP + 8];
     __shared__ cx<float> tw[N];
     fft::load_twiddles<N, float>(tw, tw_g);
     const int c = blockIdx.y;
-    const int t = threadIdx.x;
+    const int j = threadIdx.x % TL::G, l = threadIdx.x / TL::G;
     const int nrows = g.Es[1] * g.Es[2];
-    const int pair0 = blockIdx.x * TL::LS;
+    const int r0 = 2 * (blockIdx.x * TL::LS + l);
     const int B = g.B;
-    for (int idx = t; idx < TL::LS * N; idx += TL::threads) {
-        const int ll = idx / N, n = idx - ll * N;
-        const int r0 = 2 * (pair0 + ll);
-        cx<float> v = {0.f, 0.f};
-        if (n < g.Es[0] && r0 < nrows) {
-            const int z = r0 / g.Es[1], y = r0 - z * g.Es[1];
-            const int blk = g.src_lut[((z / B) * g.nbS[1] + y / B) * g.nbS[0] + n / B];
-            if (blk >= 0) {
-                const float *p = src + ((size_t)(blk * g.ncomp + c) * B + (z % B)) * B * B + (y % B) * B + (n % B);
-                v.x = __ldg(p);
-                v.y = __ldg(p + B);
+    const bool row_ok = r0 < nrows;
+    const int z = row_ok ? r0 / g.Es[1] : 0, y = row_ok ? r0 - z * g.Es[1] : 0;
+    const int lut_row = ((z / B) * g.nbS[1] + y / B) * g.nbS[0];
+    const size_t in_blk = (size_t)(z % B) * B * B + (size_t)(y % B) * B;
+    cx<float> v[E];
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+        v[e] = {0.f, 0.f};
+        if (fft::in_lower_half<N, false>(e)) {
+            const int pos = fft::in_pos<N, false>(e, j);
+            if (row_ok && pos < g.Es[0]) {
+                const int blk = __ldg(g.src_lut + lut_row + pos / B);
+                if (blk >= 0) {
+                    const float *p = src + (size_t)(blk * g.ncomp + c) * B * B * B + in_blk + (pos % B);
+                    v[e] = {__ldg(p), __ldg(p + B)};
+                }
             }
         }
-        buf[n * TL::LSP + ll] = v;
     }
+    __syncthreads();  // twiddles
+    SM sm{0};
+    fft::transform<N, false, false, float>(v, buf, tw, sm, l, j);
+#pragma unroll
+    for (int e = 0; e < E; e++) buf[sm.at(fft::out_pos<N, false>(e, j), l)] = v[e];
     __syncthreads();
-    fft::line_fft<N, false, float>(buf, tw, TL::LSP, t % TL::LS, t / TL::LS, true);
+    // split the two real rows: A(k) = (Z_k + conj Z_{N-k})/2, B(k) = (Z_k - conj Z_{N-k})/(2i)
     constexpr int KX = N / 2 + 1;
-    for (int idx = t; idx < TL::LS * KX; idx += TL::threads) {
+    for (int idx = threadIdx.x; idx < TL::LS * KX; idx += TL::threads) {
         const int ll = idx / KX, k = idx - ll * KX;
-        const int r0 = 2 * (pair0 + ll);
-        if (r0 >= nrows) continue;
-        const cx<float> zk = buf[k * TL::LSP + ll];
-        const cx<float> zn = buf[((N - k) & (N - 1)) * TL::LSP + ll];
-        const cx<float> a = {0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y)};
-        const cx<float> b = {0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x)};
-        const size_t row = ((size_t)c * nrows + r0) * KX;
-        out[row + k] = a;
-        out[row + KX + k] = b;
+        const int rr = 2 * (blockIdx.x * TL::LS + ll);
+        if (rr >= nrows) continue;
+        const cx<float> zk = buf[sm.at(k, ll)];
+        const cx<float> zn = buf[sm.at((N - k) & (N - 1), ll)];
+        const size_t row = ((size_t)c * nrows + rr) * KX;
+        out[row + k] = {0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y)};
+        out[row + KX + k] = {0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x)};
     }
 }
 
-// Generic line pass over [c][plane][line-axis][kx] arrays, lines along the
-// middle axis, LS consecutive kx per block.
-//   MODE 0 (y_fwd): in  [c][Es_z][Es_y][KX] (n < Es_y), out [c][Es_z][Ny][KX]
-//   MODE 1 (z_mid): in  [c][Es_z][Ny][KX] lines along z, out [c][Et_z][Ny][KX]
-//   MODE 2 (y_inv): in  [c][Et_z][Ny][KX], out [c][Et_z][Et_y][KX]
+// y forward (MODE 0), z forward + spectral multiply + z inverse (MODE 1),
+// y inverse (MODE 2) over [c][plane][line][kx] arrays, LS consecutive kx per block.
+//   MODE 0: in [c][Es_z][Es_y][KX] -> out [c][Es_z][Ny][KX]
+//   MODE 1: in [c][Es_z][Ny][KX]   -> out [c][Et_z][Ny][KX]
+//   MODE 2: in [c][Et_z][Ny][KX]   -> out [c][Et_z][Et_y][KX]
 template <int N, int MODE>
-__global__ void __launch_bounds__(Tile<N>::threads) k_line(Geom g, const cx<float> *__restrict__ in,
-                                                            cx<float> *__restrict__ out, const float2 *tw_g)
+__global__ void __launch_bounds__(TileY<N>::threads) k_line(Geom g, const cx<float> *__restrict__ in,
+                                                             cx<float> *__restrict__ out, const float2 *tw_g)
 {
-    using TL = Tile<N>;
+    using TL = TileY<N>;
+    constexpr int E = Plan<N>::E;
+    using SM = fft::Smem<N, true>;
     __shared__ cx<float> buf[N * TL::LSP];
     __shared__ cx<float> tw[N];
     fft::load_twiddles<N, float>(tw, tw_g);
     const int KX = g.KX;
-    const int kx0 = blockIdx.x * TL::LS;
-    const int p = blockIdx.y;  // plane: z (MODE 0), ky (MODE 1), zt (MODE 2)
+    const int l = threadIdx.x % TL::LS, j = threadIdx.x / TL::LS;
+    const int kx = blockIdx.x * TL::LS + l;
+    const bool ok = kx < KX;
+    const int p = blockIdx.y;
     const int c = blockIdx.z;
-    const int t = threadIdx.x;
     const int Ny = g.N[1];
-
-    int nin;
-    if (MODE == 0) nin = g.Es[1];
-    else if (MODE == 1) nin = g.Es[2];
-    else nin = Ny;
-    for (int idx = t; idx < TL::LS * N; idx += TL::threads) {
-        const int n = idx / TL::LS, ll = idx - n * TL::LS;
-        const int kx = kx0 + ll;
-        cx<float> v = {0.f, 0.f};
-        if (n < nin && kx < KX) {
-            size_t off;
-            if (MODE == 0) off = (((size_t)c * g.Es[2] + p) * g.Es[1] + n) * KX + kx;
-            else if (MODE == 1) off = (((size_t)c * g.Es[2] + n) * Ny + p) * KX + kx;
-            else off = (((size_t)c * g.Et[2] + p) * Ny + n) * KX + kx;
-            v = in[off];
+    SM sm{TL::LSP};
+    cx<float> v[E];
+    constexpr bool INV0 = MODE == 2;  // first transform direction
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+        v[e] = {0.f, 0.f};
+        const int pos = fft::in_pos<N, INV0>(e, j);
+        if constexpr (MODE == 0) {
+            if (fft::in_lower_half<N, false>(e) && ok && pos < g.Es[1])
+                v[e] = in[(((size_t)c * g.Es[2] + p) * g.Es[1] + pos) * KX + kx];
+        } else if constexpr (MODE == 1) {
+            if (fft::in_lower_half<N, false>(e) && ok && pos < g.Es[2])
+                v[e] = in[(((size_t)c * g.Es[2] + pos) * Ny + p) * KX + kx];
+        } else {
+            if (ok) v[e] = in[(((size_t)c * g.Et[2] + p) * Ny + pos) * KX + kx];
         }
-        buf[n * TL::LSP + ll] = v;
     }
-    __syncthreads();
-    const int l = t % TL::LS, lane = t / TL::LS;
-    if (MODE == 0) {
-        fft::line_fft<N, false, float>(buf, tw, TL::LSP, l, lane, true);
-        for (int idx = t; idx < TL::LS * N; idx += TL::threads) {
-            const int n = idx / TL::LS, ll = idx - n * TL::LS;
-            const int kx = kx0 + ll;
-            if (kx < KX) out[(((size_t)c * g.Es[2] + p) * N + n) * KX + kx] = buf[n * TL::LSP + ll];
+    __syncthreads();  // twiddles
+    if constexpr (MODE == 0) {
+        fft::transform<N, false, true, float>(v, buf, tw, sm, l, j);
+        if (ok) {
+#pragma unroll
+            for (int e = 0; e < E; e++)
+                out[(((size_t)c * g.Es[2] + p) * N + fft::out_pos<N, false>(e, j)) * KX + kx] = v[e];
         }
-    } else if (MODE == 1) {
-        fft::line_fft<N, false, float>(buf, tw, TL::LSP, l, lane, true);
-        // multiply by the real, even kernel spectrum (octant storage)
-        const int ky = p;
-        const int kyf = ky <= Ny / 2 ? ky : Ny - ky;
-        const int NyH = Ny / 2 + 1;
-        for (int idx = t; idx < TL::LS * N; idx += TL::threads) {
-            const int n = idx / TL::LS, ll = idx - n * TL::LS;
-            const int kx = kx0 + ll;
-            if (kx < KX) {
-                const int kzf = n <= N / 2 ? n : N - n;
-                const float w = g.mul * __ldg(g.Kh + ((size_t)kzf * NyH + kyf) * KX + kx);
-                cx<float> v = buf[n * TL::LSP + ll];
-                buf[n * TL::LSP + ll] = {v.x * w, v.y * w};
-            }
+    } else if constexpr (MODE == 1) {
+        fft::transform<N, false, true, float>(v, buf, tw, sm, l, j);
+        const int kyf = p <= Ny / 2 ? p : Ny - p;
+        const float *krow = g.Kh + (size_t)kyf * KX + (ok ? kx : 0);
+        const size_t kstride = (size_t)(Ny / 2 + 1) * KX;
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+            const int pos = fft::out_pos<N, false>(e, j);
+            const int kzf = pos <= N / 2 ? pos : N - pos;
+            const float w = g.mul * __ldg(krow + kzf * kstride);
+            v[e] = {v[e].x * w, v[e].y * w};
         }
-        __syncthreads();
-        fft::line_fft<N, true, float>(buf, tw, TL::LSP, l, lane, true);
-        const int dz = g.T0[2] - g.S0[2];
-        for (int idx = t; idx < TL::LS * g.Et[2]; idx += TL::threads) {
-            const int zt = idx / TL::LS, ll = idx - zt * TL::LS;
-            const int kx = kx0 + ll;
-            if (kx < KX) {
-                const int n = wrap_mod(dz + zt, N);
-                out[(((size_t)c * g.Et[2] + zt) * Ny + p) * KX + kx] = buf[n * TL::LSP + ll];
+        fft::transform<N, true, true, float>(v, buf, tw, sm, l, j);
+        if (ok) {
+            const int dz = g.T0[2] - g.S0[2];
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                const int zt = wrap_mod(fft::out_pos<N, true>(e, j) - dz, N);
+                if (zt < g.Et[2]) out[(((size_t)c * g.Et[2] + zt) * Ny + p) * KX + kx] = v[e];
             }
         }
     } else {
-        fft::line_fft<N, true, float>(buf, tw, TL::LSP, l, lane, true);
-        const int dy = g.T0[1] - g.S0[1];
-        for (int idx = t; idx < TL::LS * g.Et[1]; idx += TL::threads) {
-            const int yt = idx / TL::LS, ll = idx - yt * TL::LS;
-            const int kx = kx0 + ll;
-            if (kx < KX) {
-                const int n = wrap_mod(dy + yt, N);
-                out[(((size_t)c * g.Et[2] + p) * g.Et[1] + yt) * KX + kx] = buf[n * TL::LSP + ll];
+        fft::transform<N, true, true, float>(v, buf, tw, sm, l, j);
+        if (ok) {
+            const int dy = g.T0[1] - g.S0[1];
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                const int yt = wrap_mod(fft::out_pos<N, true>(e, j) - dy, N);
+                if (yt < g.Et[1]) out[(((size_t)c * g.Et[2] + p) * g.Et[1] + yt) * KX + kx] = v[e];
             }
         }
     }
 }
 
+// x inverse: two target rows per complex line (Z = A + i B with Hermitian
+// extension), C2R, scatter into the target block list.
 template <int N>
-__global__ void __launch_bounds__(Tile<N>::threads) k_x_inv(Geom g, const cx<float> *__restrict__ in,
-                                                             float *__restrict__ dst, const float2 *tw_g)
+__global__ void __launch_bounds__(TileX<N>::threads) k_x_inv(Geom g, const cx<float> *__restrict__ in,
+                                                              float *__restrict__ dst, const float2 *tw_g)
 {
-    using TL = Tile<N>;
-    __shared__ cx<float> buf[N * TL::LSP];
+    using TL = TileX<N>;
+    constexpr int E = Plan<N>::E;
+    using SM = fft::Smem<N, false>;
+    __shared__ cx<float> buf[TL::LS * SM::NP + 8];
     __shared__ cx<float> tw[N];
     fft::load_twiddles<N, float>(tw, tw_g);
     constexpr int KX = N / 2 + 1;
     const int c = blockIdx.y;
-    const int t = threadIdx.x;
+    const int j = threadIdx.x % TL::G, l = threadIdx.x / TL::G;
     const int nrows = g.Et[1] * g.Et[2];
-    const int pair0 = blockIdx.x * TL::LS;
-    for (int idx = t; idx < TL::LS * N; idx += TL::threads) {
-        const int ll = idx / N, k = idx - ll * N;
-        const int r0 = 2 * (pair0 + ll);
-        cx<float> zv = {0.f, 0.f};
-        if (r0 < nrows) {
-            const size_t row = ((size_t)c * nrows + r0) * KX;
+    const int r0 = 2 * (blockIdx.x * TL::LS + l);
+    const bool row_ok = r0 < nrows;
+    const size_t row = ((size_t)c * nrows + (row_ok ? r0 : 0)) * KX;
+    cx<float> v[E];
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+        v[e] = {0.f, 0.f};
+        if (row_ok) {
+            const int pos = fft::in_pos<N, true>(e, j);
             cx<float> a, b;
-            if (k <= N / 2) {
-                a = in[row + k];
-                b = in[row + KX + k];
+            if (pos <= N / 2) {
+                a = in[row + pos];
+                b = in[row + KX + pos];
             } else {
-                a = conj(in[row + (N - k)]);
-                b = conj(in[row + KX + (N - k)]);
+                a = conj(in[row + (N - pos)]);
+                b = conj(in[row + KX + (N - pos)]);
             }
-            zv = {a.x - b.y, a.y + b.x};  // a + i b
+            v[e] = {a.x - b.y, a.y + b.x};
         }
-        buf[k * TL::LSP + ll] = zv;
     }
-    __syncthreads();
-    fft::line_fft<N, true, float>(buf, tw, TL::LSP, t % TL::LS, t / TL::LS, true);
+    __syncthreads();  // twiddles
+    SM sm{0};
+    fft::transform<N, true, false, float>(v, buf, tw, sm, l, j);
+    if (!row_ok) return;
     const int B = g.B;
+    const int zt = r0 / g.Et[1], yt = r0 - zt * g.Et[1];
+    const int lut_row = ((zt / B) * g.nbT[1] + yt / B) * g.nbT[0];
+    const size_t out_blk = (size_t)(zt % B) * B * B + (size_t)(yt % B) * B;
     const int dx0 = g.T0[0] - g.S0[0];
-    for (int idx = t; idx < TL::LS * g.Et[0]; idx += TL::threads) {
-        const int ll = idx / g.Et[0], xt = idx - ll * g.Et[0];
-        const int r0 = 2 * (pair0 + ll);
-        if (r0 >= nrows) continue;
-        const int zt = r0 / g.Et[1], yt = r0 - zt * g.Et[1];
-        const int blk = g.dst_lut[((zt / B) * g.nbT[1] + yt / B) * g.nbT[0] + xt / B];
-        if (blk < 0) continue;
-        const cx<float> zv = buf[wrap_mod(dx0 + xt, N) * TL::LSP + ll];
-        float *p = dst + ((size_t)(blk * g.ncomp + c) * B + (zt % B)) * B * B + (yt % B) * B + (xt % B);
-        p[0] = zv.x;
-        p[B] = zv.y;
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+        const int xt = wrap_mod(fft::out_pos<N, true>(e, j) - dx0, N);
+        if (xt < g.Et[0]) {
+            const int blk = __ldg(g.dst_lut + lut_row + xt / B);
+            if (blk >= 0) {
+                float *p = dst + (size_t)(blk * g.ncomp + c) * B * B * B + out_blk + (xt % B);
+                p[0] = v[e].x;
+                p[B] = v[e].y;
+            }
+        }
     }
 }
 
 template <int N>
 lgf_status launch_x_fwd(const Geom &g, const float *src, cx<float> *out, cudaStream_t s)
 {
-    using TL = Tile<N>;
+    using TL = TileX<N>;
     const int nrows = g.Es[1] * g.Es[2];
     dim3 grid(ceil_div(nrows / 2, TL::LS), g.ncomp);
     k_x_fwd<N><<<grid, TL::threads, 0, s>>>(g, src, out, twiddle_table_f32());
@@ -234,7 +256,7 @@ lgf_status launch_x_fwd(const Geom &g, const float *src, cx<float> *out, cudaStr
 template <int N, int MODE>
 lgf_status launch_line(const Geom &g, const cx<float> *in, cx<float> *out, cudaStream_t s)
 {
-    using TL = Tile<N>;
+    using TL = TileY<N>;
     int planes = MODE == 0 ? g.Es[2] : (MODE == 1 ? g.N[1] : g.Et[2]);
     dim3 grid(ceil_div(g.KX, TL::LS), planes, g.ncomp);
     k_line<N, MODE><<<grid, TL::threads, 0, s>>>(g, in, out, twiddle_table_f32());
@@ -244,7 +266,7 @@ lgf_status launch_line(const Geom &g, const cx<float> *in, cx<float> *out, cudaS
 template <int N>
 lgf_status launch_x_inv(const Geom &g, const cx<float> *in, float *dst, cudaStream_t s)
 {
-    using TL = Tile<N>;
+    using TL = TileX<N>;
     const int nrows = g.Et[1] * g.Et[2];
     dim3 grid(ceil_div(nrows / 2, TL::LS), g.ncomp);
     k_x_inv<N><<<grid, TL::threads, 0, s>>>(g, in, dst, twiddle_table_f32());
@@ -288,17 +310,28 @@ int poisson_pick_n(int need)
 }
 
 lgf_status poisson_launch(const Geom &g, const float *src, float *dst, cx<float> *wsA, cx<float> *wsB,
-                          cudaStream_t s)
+                          cudaStream_t s, Profiler *prof)
 {
     if (fft::upload_tw64() != cudaSuccess) {
         set_error("twiddle upload failed");
         return LGF_ERR_CUDA;
     }
+    const bool P = prof && prof->on;
+    if (P) prof->begin(s);
     LGF_DISPATCH_N(g.N[0], LGF_TRY((launch_x_fwd<NN>(g, src, wsA, s))));
+    if (P) prof->end("x_fwd_gather_r2c", s);
+    if (P) prof->begin(s);
     LGF_DISPATCH_N(g.N[1], LGF_TRY((launch_line<NN, 0>(g, wsA, wsB, s))));
+    if (P) prof->end("y_fwd", s);
+    if (P) prof->begin(s);
     LGF_DISPATCH_N(g.N[2], LGF_TRY((launch_line<NN, 1>(g, wsB, wsA, s))));
+    if (P) prof->end("z_fwd_mul_inv", s);
+    if (P) prof->begin(s);
     LGF_DISPATCH_N(g.N[1], LGF_TRY((launch_line<NN, 2>(g, wsA, wsB, s))));
+    if (P) prof->end("y_inv", s);
+    if (P) prof->begin(s);
     LGF_DISPATCH_N(g.N[0], LGF_TRY((launch_x_inv<NN>(g, wsB, dst, s))));
+    if (P) prof->end("x_inv_c2r_scatter", s);
     return LGF_OK;
 }
 

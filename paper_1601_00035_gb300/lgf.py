@@ -73,6 +73,10 @@ _SIGS = {
     "ifactor_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "lgf_residual_fp64": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "lgf_plan_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "lgf_plan_kernel_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "lgf_plan_kernel_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
+                                             ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
     "lgf_plan_destroy": (None, [ctypes.c_void_p]),
     "lgf_last_error": (ctypes.c_char_p, []),
     "lgf_version": (ctypes.c_char_p, []),
@@ -216,6 +220,22 @@ class Plan:
         out = ctypes.c_double()
         _check(load().lgf_residual_fp64(self._h, int(solve), _ptr(src), _ptr(dst), ctypes.byref(out), _stream(stream)))
         return out.value
+
+    def set_profiling(self, enable: int):
+        """1: record per-kernel device times; 0: stop; 2: clear totals and record."""
+        _check(load().lgf_plan_set_profiling(self._h, int(enable)))
+
+    def kernel_times(self) -> dict:
+        """{kernel name: (launches, total device ms)} accumulated while profiling."""
+        L = load()
+        n = ctypes.c_int()
+        _check(L.lgf_plan_kernel_count(self._h, ctypes.byref(n)))
+        out = {}
+        for i in range(n.value):
+            nm, la, ms = ctypes.c_char_p(), ctypes.c_longlong(), ctypes.c_double()
+            _check(L.lgf_plan_kernel_times(self._h, i, ctypes.byref(nm), ctypes.byref(la), ctypes.byref(ms)))
+            out[nm.value.decode()] = (la.value, ms.value)
+        return out
 
     def close(self):
         if getattr(self, "_h", None):
