@@ -144,6 +144,27 @@ lgf_status lgf_conv_execute_host(lgf_plan *p, const float *const *src, float *co
  * Requires R_alpha <= B.  Asynchronous; no allocation. */
 lgf_status ifactor_apply(lgf_plan *p, const float *x, float *y, void *stream);
 
+/* No-allocation variant of ifactor_apply, for callers that cannot allocate
+ * device memory: code that runs under a memory budget owned by another
+ * component, or inside frameworks that forbid cudaMalloc once they are
+ * running.  The paper has no counterpart; it is a deployment convenience.
+ * Computes the same y = M E_Q(alpha) M x as an IF plan built from
+ * lgf_table_build(LGF_KERNEL_IFACTOR, alpha) over `blocks` ([n_blocks][3]
+ * host int32 coordinates), with x, y device [n_blocks][ncomp][B^3] FP32.
+ * Nothing is allocated: the block tables and intermediate fields live in one
+ * static device array of 64 MiB that every GPU loading the library holds
+ * until exit; LGF_ERR_ARG if a problem needs more (or if the block set's
+ * bounding box, grown by one block per side, exceeds 2^21 blocks).  Host
+ * staging is static too.  Every call shares that storage and keeps the last
+ * call's contents (each call overwrites all it reads), so calls that overlap
+ * on the GPU, or that run concurrently from several host threads, race.
+ * The first call on a device looks up the array's device address and should
+ * come before any stream capture.  B in {8, 16}; radius R_alpha <= min(B, 16).
+ * Asynchronous on `stream` except for a host-to-device copy of the tables
+ * from pageable memory. */
+lgf_status ifactor_apply_noalloc(double alpha, int B, int ncomp, int n_blocks, const int32_t *blocks,
+                                 const float *x, float *y, void *stream);
+
 /* FP64 residual of a Poisson result (App. A stencil, Sec. 4.3 definition):
  *   ||L u - scale f||_2 / ||scale f||_2
  * over target points whose six neighbours are target points (L = 7-point

@@ -71,6 +71,9 @@ _SIGS = {
     "lgf_conv_execute_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
                                              ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
     "ifactor_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "ifactor_apply_noalloc": (ctypes.c_int, [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p]),
     "lgf_residual_fp64": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "lgf_plan_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
@@ -247,6 +250,15 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def ifactor_apply_noalloc(alpha: float, B: int, ncomp: int, blocks, x, y, stream=None):
+    """y = M E_Q(alpha) M x without any device allocation (static 64 MiB scratch
+    inside the library; for callers that cannot allocate device memory)."""
+    b = np.ascontiguousarray(blocks, dtype=np.int32).reshape(-1, 3)
+    _check(load().ifactor_apply_noalloc(float(alpha), int(B), int(ncomp), len(b),
+                                        b.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _ptr(x), _ptr(y),
+                                        _stream(stream)))
 
 
 def version() -> str:
