@@ -185,6 +185,44 @@ lgf_status lgf_plan_kernel_count(lgf_plan *p, int *count);
  * until the plan is destroyed), launches and summed device milliseconds. */
 lgf_status lgf_plan_kernel_times(lgf_plan *p, int i, const char **name, long long *launches, double *total_ms);
 
+/* ---------------------------------------------------------------------------
+ * One time step of the IF-HERK scheme on a finite block set (Sec. 3.2
+ * algorithm, Sec. 3.3 eq. proj_final, Sec. 5 xIF-HERK masks), Scheme A of
+ * eq. ifherk_schemes.  D_soln = D_supp = soln_blocks (Sec. 6); D_xsoln is
+ * D_soln dilated by N_b = 1 block (eq. def_xsoln).  Fields live on D_xsoln in
+ * the order returned by lgf_rk_blocks(p, 0, ...) (the soln blocks first):
+ * face velocity u is [n_xsoln][3][B^3] FP32 (component q is the x_q-face value).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int B;                       /* 8 or 16 */
+    int n_soln;                  /* number of D_soln (= D_supp) blocks */
+    const int32_t *soln_blocks;  /* [n_soln][3] block coordinates (host) */
+    double dx, dt, re;           /* grid spacing, time step, Reynolds number: alpha = dt / (dx^2 re) */
+    int scheme;                  /* 0 = Scheme A */
+    int reserved[3];             /* must be zero */
+} lgf_rk_desc;
+
+/* Builds the LGF and integrating-factor tables, a scalar Poisson plan
+ * D_supp -> D_xsoln and an E(alpha/2) plan on D_xsoln, and all workspaces.
+ * Synchronises `stream`.  The result is used only with the lgf_rk_* and
+ * lgf_op_apply calls (and destroyed with lgf_plan_destroy). */
+lgf_status lgf_rk_plan(const lgf_rk_desc *d, void *stream, lgf_plan **out);
+/* Number of blocks of D_xsoln (which = 0) or D_soln (which = 1); -1 if p is not an RK plan. */
+int lgf_rk_block_count(const lgf_plan *p, int which);
+/* Copy the block coordinates of D_xsoln (which = 0) or D_soln (which = 1) to coords ([n][3], host). */
+lgf_status lgf_rk_blocks(const lgf_plan *p, int which, int32_t *coords, int n);
+/* u_out = IF-HERK(u_in) over one step, freestream uinf (host, 3 doubles, constant over the step);
+ * u_in and u_out device buffers [n_xsoln][3][B^3], must not alias.  Three scalar Poisson solves,
+ * five integrating-factor applications, three nonlinear terms.  Asynchronous; no allocation. */
+lgf_status lgf_rk_step(lgf_plan *p, const float *u_in, float *u_out, const double uinf[3], void *stream);
+/* One App. A operator on the D_xsoln block set (zero outside it):
+ *   op 0: e = C f (faces -> edges)      op 1: f = C^T e (edges -> faces)
+ *   op 2: c = G^T f (faces -> cells)    op 3: f = G c (cells -> faces)
+ *   op 4: f = coef * M^soln N~(M^xsoln (u + uinf)) (faces -> faces, eq. opr_def_nonlin)
+ * Vector fields [n_xsoln][3][B^3], scalar fields [n_xsoln][1][B^3]; uinf only for op 4. */
+lgf_status lgf_op_apply(lgf_plan *p, int op, const float *in, float *out, double coef, const double uinf[3],
+                        void *stream);
+
 void lgf_plan_destroy(lgf_plan *p);
 
 /* Thread-local description of the last non-OK status ("" if none). */

@@ -28,7 +28,8 @@ __all__ = [
     "lib", "gauss_legendre", "bessel_scaled", "lgf_octant", "lgf_cube", "lgf_value",
     "octant_size", "asymptotic_G", "ifactor_taps", "ifactor_radius", "direct_conv",
     "direct_conv_box", "ifactor_direct", "shift", "op_G", "op_Gt", "op_C", "op_Ct", "op_D",
-    "op_Dbar", "op_L", "op_N", "residual_L", "WATSON_W", "num_threads",
+    "op_Dbar", "op_L", "op_N", "residual_L", "WATSON_W", "num_threads", "SCHEME_A", "shifted_tableau",
+    "block_mask", "ifactor_masked", "poisson_masked", "if_herk_step",
 ]
 
 # Watson's integral for the simple cubic lattice, closed form (Watson 1939):
@@ -275,3 +276,106 @@ def residual_L(u: np.ndarray, f: np.ndarray, interior: np.ndarray, dx: float = 1
     r = op_L(u, dx) - f
     den = np.sqrt((f[interior] ** 2).sum())
     return float(np.sqrt((r[interior] ** 2).sum()) / den)
+
+
+# ---------------------------------------------------------------------------
+# IF-HERK step on a finite block set (Sec. 3.2 algorithm, Sec. 3.3 eq.
+# proj_final, Sec. 5 xIF-HERK masks), FP64, written in the paper's order:
+# q and w recursions, one integrating factor per quantity.
+# ---------------------------------------------------------------------------
+SCHEME_A = {
+    "A": np.array([[0.0, 0.0, 0.0],
+                   [0.5, 0.0, 0.0],
+                   [math.sqrt(3) / 3, (3 - math.sqrt(3)) / 3, 0.0]]),
+    "b": np.array([(3 + math.sqrt(3)) / 6, -math.sqrt(3) / 3, (3 + math.sqrt(3)) / 6]),
+    "c": np.array([0.0, 0.5, 1.0]),
+}
+
+
+def shifted_tableau(tab=SCHEME_A):
+    """Shifted coefficients of eq. herk_shift: a~_{i,j} = a_{i+1,j} (i < s), b_j (i = s);
+    c~_i = c_{i+1} (i < s), 1 (i = s).  Returned 1-based as dicts for readability."""
+    A, b, c = tab["A"], tab["b"], tab["c"]
+    s = len(b)
+    at = {}
+    for i in range(1, s + 1):
+        for j in range(1, i + 1):
+            at[(i, j)] = A[i, j - 1] if i < s else b[j - 1]
+    ct = {i: (c[i] if i < s else 1.0) for i in range(1, s + 1)}
+    ct[0] = c[0]  # reading: c~_0 = c_1 (the first stage starts at t_k)
+    return at, ct, s
+
+
+def block_mask(shape, B, blocks, origin_blocks=(0, 0, 0)):
+    """Boolean mask [z,y,x] of the listed blocks inside a dense box whose block (0,0,0)
+    is origin_blocks."""
+    m = np.zeros(shape, dtype=bool)
+    o = np.asarray(origin_blocks)
+    for bx, by, bz in (np.asarray(blocks) - o).tolist():
+        m[bz * B:(bz + 1) * B, by * B:(by + 1) * B, bx * B:(bx + 1) * B] = True
+    return m
+
+
+def ifactor_masked(g, f, mask):
+    """M E(alpha) M f on a dense box (per component), plain 3-D sum over all points."""
+    z, y, x = np.nonzero(mask)
+    tgt = np.stack([x, y, z], 1).astype(np.int32)
+    if f.ndim == 4:
+        return np.stack([ifactor_masked(g, f[q], mask) for q in range(f.shape[0])])
+    out = np.zeros_like(f)
+    out[z, y, x] = ifactor_direct(g, np.where(mask, f, 0.0), tgt)
+    return out
+
+
+def poisson_masked(cube, f, supp_mask, xsoln_mask, dx):
+    """M^xsoln L^{-1} M^supp f by the direct sum (eq. dpoisson_conv), G_L = dx^2 G."""
+    z, y, x = np.nonzero(xsoln_mask)
+    tgt = np.stack([x, y, z], 1).astype(np.int32)
+    out = np.zeros_like(f)
+    out[z, y, x] = dx * dx * direct_conv_box(cube, np.where(supp_mask, f, 0.0), tgt)
+    return out
+
+
+def if_herk_step(u, dt, re, dx, uinf, masks, cube, nonlinear=True, tab=SCHEME_A):
+    """One xIF-HERK step u_k -> u_{k+1} on a dense box.
+
+    u: face velocity [3, z, y, x] (zero outside D_xsoln); masks: dict of boolean
+    [z,y,x] arrays 'supp', 'soln', 'xsoln'; uinf: constant freestream (3,).
+    Integrating factors H^i = E((c~_i - c~_{i-1}) dt / (dx^2 Re)) (eq. ifherk_aux_1);
+    g^i = -a~_{ii} dt M^soln N~(M^xsoln(u^{i-1} + u_inf)) (eq. ifherk_g, with the
+    sign of eq. ifherk_g rather than eq. rhs_final); projection eq. proj_final with
+    d^ = -M^xsoln L^{-1} M^supp G^T M^xsoln r (eq. dpoisson_final)."""
+    at, ct, s = shifted_tableau(tab)
+    xs = masks["xsoln"]
+    alpha = dt / (dx * dx * re)
+    H = {}
+    for i in range(1, s + 1):
+        a = (ct[i] - ct[i - 1]) * alpha
+        H[i] = None if a == 0.0 else ifactor_taps(a)
+
+    def applyH(i, f):
+        return f * xs if H[i] is None else ifactor_masked(H[i], f, xs)
+
+    uinf = np.asarray(uinf, dtype=float).reshape(3, 1, 1, 1)
+    q = {1: u.copy()}
+    w = {}
+    u_prev = u
+    for i in range(1, s + 1):
+        if nonlinear:
+            g = -at[(i, i)] * dt * op_N((u_prev + uinf) * xs, dx) * masks["soln"]
+        else:
+            g = np.zeros_like(u)
+        r = q[i] + g
+        for j in range(1, i):
+            r = r + dt * at[(i, j)] * w[(i, j)]
+        r = r * xs
+        dhat = -poisson_masked(cube, op_Gt(r, dx), masks["supp"], xs, dx)
+        gd = op_G(dhat, dx) * xs
+        u_i = applyH(i, r - gd)
+        w[(i, i)] = (g - gd) / (at[(i, i)] * dt)
+        if i < s:
+            q[i + 1] = applyH(i, q[i])
+            for j in range(1, i + 1):
+                w[(i + 1, j)] = applyH(i, w[(i, j)])
+        u_prev = u_i
+    return u_prev

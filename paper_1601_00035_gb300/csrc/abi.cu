@@ -99,6 +99,7 @@ void free_plan(lgf_plan *p)
     cudaFree(p->ifp.y1);
     cudaFree(p->ifp.y2);
     if (p->graph) cudaGraphExecDestroy(p->graph);
+    if (p->rk) free_rk(p->rk);
     delete p;
 }
 

@@ -1,0 +1,235 @@
+// Local operators of the staggered grid (App. A point forms) on a block set,
+// with the mask semantics of Sec. 4.2: values outside the listed blocks are
+// zero.  Axis map: component (1),(2),(3) = x, y, z; position index n = (i, j, k).
+//
+//   G^T f  (faces -> cells):   sum_q (f^q_{n-e_q} - f^q_n) / dx            (G^T = -Dbar)
+//   G c    (cells -> faces):   (c_{n+e_q} - c_n) / dx
+//   C f    (faces -> edges):   (f^r_n - f^r_{n+e_s} + f^s_{n+e_r} - f^s_n) / dx,  (q,r,s) cyclic
+//   C^T e  (edges -> faces):   (e^r_{n-e_s} - e^r_n + e^s_n - e^s_{n-e_r}) / dx
+//   N~(f)  (faces -> faces, eq. opr_def_nonlin, e = C f):
+//     1/4 sum_{m in {-1,0}} [ e^r_{n+m e_s} (f^s + f^s_{+e_q})_{n+m e_s} - e^s_{n+m e_r} (f^r + f^r_{+e_q})_{n+m e_r} ]
+//
+// One thread block per block of the set, one thread per (x, y) column looping
+// over z; neighbour values come through the 27-neighbour table (L1/L2).
+#include <algorithm>
+
+#include "plan.hpp"
+
+namespace lgf {
+namespace {
+
+template <int B>
+struct Fetch {
+    const float *f;
+    int ncomp;
+    const int *nb;  // 27 neighbours of this block
+    // value of component c at local position (x, y, z), which may lie in a neighbour
+    __device__ __forceinline__ float operator()(int c, int x, int y, int z) const
+    {
+        const int dx = x < 0 ? -1 : (x >= B ? 1 : 0);
+        const int dy = y < 0 ? -1 : (y >= B ? 1 : 0);
+        const int dz = z < 0 ? -1 : (z >= B ? 1 : 0);
+        const int n = nb[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)];
+        if (n < 0) return 0.f;
+        return __ldg(f + ((size_t)(n * ncomp + c) * B + (z - dz * B)) * B * B + (y - dy * B) * B + (x - dx * B));
+    }
+};
+
+__device__ __forceinline__ void axis_shift(int q, int d, int &x, int &y, int &z)
+{
+    if (q == 0) x += d;
+    else if (q == 1) y += d;
+    else z += d;
+}
+
+// OP: 0 curl (faces->edges), 1 curl^T (edges->faces), 2 G^T (faces->cells),
+//     3 G (cells->faces), 4 nonlinear (faces->faces)
+template <int B, int OP>
+__global__ void __launch_bounds__(B *B) k_op(const float *__restrict__ in, float *__restrict__ out,
+                                             const int *__restrict__ nbr27, const unsigned char *__restrict__ out_keep,
+                                             float inv_dx, float coef, float u0, float u1, float u2)
+{
+    const int blk = blockIdx.x;
+    __shared__ int nb[27];
+    if (threadIdx.x < 27) nb[threadIdx.x] = nbr27[blk * 27 + threadIdx.x];
+    __syncthreads();
+    const int x = threadIdx.x % B, y = threadIdx.x / B;
+    constexpr int nin = (OP == 3) ? 1 : 3;
+    constexpr int nout = (OP == 2) ? 1 : 3;
+    Fetch<B> F{in, nin, nb};
+    const float uinf[3] = {u0, u1, u2};
+    const bool keep = (OP != 4) || out_keep == nullptr || out_keep[blk];
+    for (int z = 0; z < B; z++) {
+        if constexpr (OP == 0) {
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                const int r = (q + 1) % 3, s = (q + 2) % 3;
+                int xs = x, ys = y, zs = z, xr = x, yr = y, zr = z;
+                axis_shift(s, 1, xs, ys, zs);
+                axis_shift(r, 1, xr, yr, zr);
+                const float v = F(r, x, y, z) - F(r, xs, ys, zs) + F(s, xr, yr, zr) - F(s, x, y, z);
+                out[((size_t)(blk * 3 + q) * B + z) * B * B + y * B + x] = v * inv_dx;
+            }
+        } else if constexpr (OP == 1) {
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                const int r = (q + 1) % 3, s = (q + 2) % 3;
+                int xs = x, ys = y, zs = z, xr = x, yr = y, zr = z;
+                axis_shift(s, -1, xs, ys, zs);
+                axis_shift(r, -1, xr, yr, zr);
+                const float v = F(r, xs, ys, zs) - F(r, x, y, z) + F(s, x, y, z) - F(s, xr, yr, zr);
+                out[((size_t)(blk * 3 + q) * B + z) * B * B + y * B + x] = v * inv_dx;
+            }
+        } else if constexpr (OP == 2) {
+            float v = 0.f;
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                int xm = x, ym = y, zm = z;
+                axis_shift(q, -1, xm, ym, zm);
+                v += F(q, xm, ym, zm) - F(q, x, y, z);
+            }
+            out[((size_t)blk * B + z) * B * B + y * B + x] = v * inv_dx;
+        } else if constexpr (OP == 3) {
+            const float c0 = F(0, x, y, z);
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                int xp = x, yp = y, zp = z;
+                axis_shift(q, 1, xp, yp, zp);
+                out[((size_t)(blk * 3 + q) * B + z) * B * B + y * B + x] = (F(0, xp, yp, zp) - c0) * inv_dx;
+            }
+        } else {
+            // f = M(u + u_inf): u_inf added only inside the block set
+            auto fv = [&](int c, int px, int py, int pz) -> float {
+                const int dx = px < 0 ? -1 : (px >= B ? 1 : 0);
+                const int dy = py < 0 ? -1 : (py >= B ? 1 : 0);
+                const int dz = pz < 0 ? -1 : (pz >= B ? 1 : 0);
+                const int n = nb[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)];
+                if (n < 0) return 0.f;
+                return __ldg(in + ((size_t)(n * 3 + c) * B + (pz - dz * B)) * B * B + (py - dy * B) * B +
+                             (px - dx * B)) + uinf[c];
+            };
+            // component c of e = C f at a position
+            auto ev = [&](int c, int px, int py, int pz) -> float {
+                const int r = (c + 1) % 3, s = (c + 2) % 3;
+                int xs = px, ys = py, zs = pz, xr = px, yr = py, zr = pz;
+                axis_shift(s, 1, xs, ys, zs);
+                axis_shift(r, 1, xr, yr, zr);
+                return (fv(r, px, py, pz) - fv(r, xs, ys, zs) + fv(s, xr, yr, zr) - fv(s, px, py, pz)) * inv_dx;
+            };
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                float v = 0.f;
+                if (keep) {
+                    const int r = (q + 1) % 3, s = (q + 2) % 3;
+#pragma unroll
+                    for (int m = -1; m <= 0; m++) {
+                        int xa = x, ya = y, za = z;
+                        axis_shift(s, m, xa, ya, za);
+                        int xa1 = xa, ya1 = ya, za1 = za;
+                        axis_shift(q, 1, xa1, ya1, za1);
+                        v += ev(r, xa, ya, za) * (fv(s, xa, ya, za) + fv(s, xa1, ya1, za1));
+                        int xb = x, yb = y, zb = z;
+                        axis_shift(r, m, xb, yb, zb);
+                        int xb1 = xb, yb1 = yb, zb1 = zb;
+                        axis_shift(q, 1, xb1, yb1, zb1);
+                        v -= ev(s, xb, yb, zb) * (fv(r, xb, yb, zb) + fv(r, xb1, yb1, zb1));
+                    }
+                    v *= 0.25f * coef;
+                }
+                out[((size_t)(blk * 3 + q) * B + z) * B * B + y * B + x] = v;
+            }
+        }
+    }
+}
+
+// out = sum_t c_t x_t over n floats (up to 4 terms; null x_t skipped).  out may
+// alias an input (each element is read and written by the same thread), so no
+// __restrict__ and no read-only-cache loads here.
+__global__ void k_lincomb(float *out, int64_t n, const float *x0, float c0, const float *x1, float c1,
+                          const float *x2, float c2, const float *x3, float c3)
+{
+    const int64_t n4 = n / 4;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+        auto acc = [&](const float *x, float c) {
+            if (!x) return;
+            const float4 v = reinterpret_cast<const float4 *>(x)[i];
+            a.x = fmaf(c, v.x, a.x);
+            a.y = fmaf(c, v.y, a.y);
+            a.z = fmaf(c, v.z, a.z);
+            a.w = fmaf(c, v.w, a.w);
+        };
+        acc(x0, c0);
+        acc(x1, c1);
+        acc(x2, c2);
+        acc(x3, c3);
+        reinterpret_cast<float4 *>(out)[i] = a;
+    }
+}
+
+// out[i] = in[idx[i]] block by block ([n][ncomp][B^3] each)
+__global__ void k_gather_blocks(const float *__restrict__ in, float *__restrict__ out, const int *__restrict__ idx,
+                                int block_floats)
+{
+    const int i = blockIdx.x;
+    const float4 *src = reinterpret_cast<const float4 *>(in + (size_t)__ldg(idx + i) * block_floats);
+    float4 *dst = reinterpret_cast<float4 *>(out + (size_t)i * block_floats);
+    for (int t = threadIdx.x; t < block_floats / 4; t += blockDim.x) dst[t] = __ldg(src + t);
+}
+
+}  // namespace
+
+lgf_status op_launch(int op, int B, int nblk, const int *d_nbr27, const unsigned char *d_keep, const float *in,
+                     float *out, double dx, double coef, const double uinf[3], cudaStream_t s)
+{
+    const float inv_dx = (float)(1.0 / dx);
+    const float u0 = uinf ? (float)uinf[0] : 0.f, u1 = uinf ? (float)uinf[1] : 0.f, u2 = uinf ? (float)uinf[2] : 0.f;
+    const float cf = (float)coef;
+#define LGF_OPCASE(BB, OPV)                                                                                     \
+    k_op<BB, OPV><<<nblk, BB * BB, 0, s>>>(in, out, d_nbr27, d_keep, inv_dx, cf, u0, u1, u2);
+#define LGF_OPSWITCH(BB)                                                                                        \
+    switch (op) {                                                                                               \
+        case 0: LGF_OPCASE(BB, 0) break;                                                                        \
+        case 1: LGF_OPCASE(BB, 1) break;                                                                        \
+        case 2: LGF_OPCASE(BB, 2) break;                                                                        \
+        case 3: LGF_OPCASE(BB, 3) break;                                                                        \
+        case 4: LGF_OPCASE(BB, 4) break;                                                                        \
+        default: set_error("unknown operator %d", op); return LGF_ERR_ARG;                                      \
+    }
+    if (B == 8) {
+        LGF_OPSWITCH(8)
+    } else if (B == 16) {
+        LGF_OPSWITCH(16)
+    } else {
+        set_error("operators support B in {8, 16} (got %d)", B);
+        return LGF_ERR_ARG;
+    }
+#undef LGF_OPSWITCH
+#undef LGF_OPCASE
+    LGF_LAUNCH_CHECK("local operator");
+    return LGF_OK;
+}
+
+lgf_status lincomb_launch(float *out, int64_t n, const float *x0, double c0, const float *x1, double c1, const float *x2,
+                          double c2, const float *x3, double c3, cudaStream_t s)
+{
+    if (n % 4 != 0) {
+        set_error("lincomb length %lld not a multiple of 4", (long long)n);
+        return LGF_ERR_ARG;
+    }
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>((n / 4 + threads - 1) / threads, 152 * 16);
+    k_lincomb<<<blocks, threads, 0, s>>>(out, n, x0, (float)c0, x1, (float)c1, x2, (float)c2, x3, (float)c3);
+    LGF_LAUNCH_CHECK("lincomb");
+    return LGF_OK;
+}
+
+lgf_status gather_launch(const float *in, float *out, const int *d_idx, int n, int block_floats, cudaStream_t s)
+{
+    if (n == 0) return LGF_OK;
+    k_gather_blocks<<<n, 256, 0, s>>>(in, out, d_idx, block_floats);
+    LGF_LAUNCH_CHECK("gather");
+    return LGF_OK;
+}
+
+}  // namespace lgf

@@ -94,6 +94,30 @@ struct IfPlan {
 lgf_status ifactor_launch(const IfPlan &ip, int ncomp, const float *h_taps, const float *x, float *y, cudaStream_t s,
                           Profiler *prof = nullptr);
 
+// local operators (ops.cu): op 0 curl, 1 curl^T, 2 G^T, 3 G, 4 nonlinear
+lgf_status op_launch(int op, int B, int nblk, const int *d_nbr27, const unsigned char *d_keep, const float *in,
+                     float *out, double dx, double coef, const double uinf[3], cudaStream_t s);
+lgf_status lincomb_launch(float *out, int64_t n, const float *x0, double c0, const float *x1, double c1,
+                          const float *x2, double c2, const float *x3, double c3, cudaStream_t s);
+lgf_status gather_launch(const float *in, float *out, const int *d_idx, int n, int block_floats, cudaStream_t s);
+
+// one IF-HERK step on a block set (rk.cu)
+struct RkPlan {
+    int B = 0, n_soln = 0, n_x = 0;
+    double dx = 0, dt = 0, re = 0, alpha = 0;
+    std::vector<int32_t> xsoln;  // [n_x][3]; the first n_soln blocks are D_soln = D_supp
+    lgf_table *lgf_table = nullptr, *if_table = nullptr;
+    lgf_plan *poisson = nullptr, *ifp = nullptr;
+    int *d_nbr27 = nullptr;
+    unsigned char *d_soln_keep = nullptr;
+    int *d_supp_idx = nullptr;
+    float *work = nullptr;
+    size_t vec = 0, scal_x = 0, scal_s = 0;
+    size_t bytes = 0;
+};
+void free_rk(RkPlan *r);
+constexpr int LGF_PLAN_RK = 2;
+
 // residual (residual.cu)
 lgf_status residual_launch(const PoissonSolve &ps, const float *src, const float *dst, double *d_acc,
                            cudaStream_t s);
@@ -130,5 +154,6 @@ struct lgf_plan {
     cudaGraphExec_t graph = nullptr;
     std::vector<const void *> graph_key;
     lgf::Profiler prof;
+    lgf::RkPlan *rk = nullptr;  // kind == LGF_PLAN_RK
     size_t bytes = 0;
 };

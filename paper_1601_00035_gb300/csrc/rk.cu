@@ -1,0 +1,313 @@
+// One step of the IF-HERK scheme on the finite block set (Sec. 3.2 algorithm,
+// Sec. 3.3 eq. proj_final, Sec. 5 xIF-HERK), Scheme A of eq. ifherk_schemes.
+//
+// Domains (Sec. 4.2): D_soln = D_supp (Sec. 6) = the caller's block list,
+// D_xsoln = D_soln dilated by N_b = 1 block (eq. def_xsoln).  Fields live on
+// D_xsoln: face velocity u [n_x][3][B^3]; the pressure-like d^ on cells [n_x][1][B^3].
+//
+// Scheme A has c~ = (1/2, 1, 1) with c~_0 = c_1 = 0, so H^1 = H^2 = E(alpha/2),
+// H^3 = I, alpha = dt / (dx^2 Re).  Carrying the q and w recursions through
+// the integrating factors (E(a) E(b) = E(a + b) and the linearity of E) gives
+// the same step with five integrating-factor applications:
+//   stage 1:  g1 = -a~11 dt M^soln N~(M(u0 + u_inf));  r1 = u0 + g1
+//             gd1 = G d^1, d^1 = -L^{-1} M^supp G^T r1;  u1 = H(r1 - gd1)
+//             w11 = (g1 - gd1) / (a~11 dt)
+//   stage 2:  g2 = -a~22 dt M^soln N~(M(u1 + u_inf));  r2 = H(u0 + dt a~21 w11) + g2
+//             gd2 = G d^2;  u2 = H(r2 - gd2);  w22 = (g2 - gd2) / (a~22 dt)
+//   stage 3:  g3 = -a~33 dt M^soln N~(M(u2 + u_inf))
+//             r3 = H(H(u0 + dt a~31 w11) + dt a~32 w22) + g3
+//             gd3 = G d^3;  u_{k+1} = r3 - gd3
+// (H = M^xsoln E(alpha/2) M^xsoln).  The sign of g follows eq. ifherk_g.
+// The oracle runs the paper's form (explicit q and w recursions) instead, so
+// the parity test also checks this rearrangement.
+#include <algorithm>
+#include <cmath>
+#include <unordered_map>
+#include <vector>
+
+#include "plan.hpp"
+
+namespace lgf {
+namespace {
+
+inline int64_t pack3(int32_t x, int32_t y, int32_t z)
+{
+    const int64_t off = 1 << 20;
+    return ((int64_t)(x + off) << 42) | ((int64_t)(y + off) << 21) | (int64_t)(z + off);
+}
+
+template <typename T>
+lgf_status alloc_upload(T **d, const std::vector<T> &h, size_t &bytes)
+{
+    *d = nullptr;
+    if (h.empty()) return LGF_OK;
+    LGF_CUDA_TRY(cudaMalloc((void **)d, h.size() * sizeof(T)));
+    bytes += h.size() * sizeof(T);
+    LGF_CUDA_TRY(cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return LGF_OK;
+}
+
+}  // namespace
+
+void free_rk(RkPlan *r)
+{
+    if (!r) return;
+    lgf_plan_destroy(r->poisson);
+    lgf_plan_destroy(r->ifp);
+    lgf_table_destroy(r->lgf_table);
+    lgf_table_destroy(r->if_table);
+    cudaFree(r->d_nbr27);
+    cudaFree(r->d_soln_keep);
+    cudaFree(r->d_supp_idx);
+    cudaFree(r->work);
+    delete r;
+}
+
+}  // namespace lgf
+
+using namespace lgf;
+
+extern "C" {
+
+lgf_status lgf_rk_plan(const lgf_rk_desc *d, void *stream, lgf_plan **out)
+{
+    clear_error();
+    LGF_CHECK_ARG(d && out, "lgf_rk_plan: NULL argument");
+    *out = nullptr;
+    LGF_CHECK_ARG(d->B == 8 || d->B == 16, "lgf_rk_plan: B=%d not in {8,16}", d->B);
+    LGF_CHECK_ARG(d->n_soln >= 1 && d->soln_blocks, "lgf_rk_plan: empty soln block list");
+    LGF_CHECK_ARG(d->dx > 0 && d->dt > 0 && d->re > 0, "lgf_rk_plan: dx, dt, re must be positive");
+    LGF_CHECK_ARG(d->scheme == 0, "lgf_rk_plan: only Scheme A (0) is implemented");
+    for (int i = 0; i < 3; i++) LGF_CHECK_ARG(d->reserved[i] == 0, "lgf_rk_plan: reserved fields must be zero");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int B = d->B;
+    // blocks: soln as given, xsoln = soln dilated by one block, soln first
+    std::unordered_map<int64_t, int> xi;
+    std::vector<int32_t> xs;
+    for (int i = 0; i < d->n_soln; i++) {
+        const int32_t *c = d->soln_blocks + 3 * i;
+        LGF_CHECK_ARG(c[0] > -(1 << 19) && c[0] < (1 << 19) && c[1] > -(1 << 19) && c[1] < (1 << 19) &&
+                          c[2] > -(1 << 19) && c[2] < (1 << 19),
+                      "lgf_rk_plan: block coordinate out of range");
+        LGF_CHECK_ARG(xi.emplace(pack3(c[0], c[1], c[2]), (int)(xs.size() / 3)).second, "lgf_rk_plan: duplicate block");
+        xs.insert(xs.end(), c, c + 3);
+    }
+    const int nsoln = d->n_soln;
+    for (int i = 0; i < nsoln; i++)
+        for (int dz = -1; dz <= 1; dz++)
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    const int32_t x = xs[3 * i] + dx, y = xs[3 * i + 1] + dy, z = xs[3 * i + 2] + dz;
+                    if (xi.emplace(pack3(x, y, z), (int)(xs.size() / 3)).second) {
+                        xs.push_back(x);
+                        xs.push_back(y);
+                        xs.push_back(z);
+                    }
+                }
+    const int nx = (int)(xs.size() / 3);
+    RkPlan *r = new (std::nothrow) RkPlan();
+    if (!r) {
+        set_error("host allocation failed");
+        return LGF_ERR_OOM;
+    }
+    r->B = B;
+    r->n_soln = nsoln;
+    r->n_x = nx;
+    r->dx = d->dx;
+    r->dt = d->dt;
+    r->re = d->re;
+    r->alpha = d->dt / (d->dx * d->dx * d->re);
+    r->xsoln = xs;
+    lgf_status st = LGF_OK;
+    auto fail = [&](lgf_status e) {
+        free_rk(r);
+        return e;
+    };
+    // neighbour table, soln flags, supp (= soln) indices
+    std::vector<int> nbr((size_t)nx * 27, -1);
+    for (int i = 0; i < nx; i++)
+        for (int dz = -1; dz <= 1; dz++)
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    auto it = xi.find(pack3(xs[3 * i] + dx, xs[3 * i + 1] + dy, xs[3 * i + 2] + dz));
+                    if (it != xi.end()) nbr[(size_t)i * 27 + (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] = it->second;
+                }
+    std::vector<unsigned char> keep(nx, 0);
+    std::vector<int> supp(nsoln);
+    for (int i = 0; i < nsoln; i++) {
+        keep[i] = 1;
+        supp[i] = i;
+    }
+    if ((st = alloc_upload(&r->d_nbr27, nbr, r->bytes)) != LGF_OK) return fail(st);
+    if ((st = alloc_upload(&r->d_soln_keep, keep, r->bytes)) != LGF_OK) return fail(st);
+    if ((st = alloc_upload(&r->d_supp_idx, supp, r->bytes)) != LGF_OK) return fail(st);
+    // Poisson sub-plan: supp -> xsoln, scalar, d^ = -L^{-1} f (scale -1)
+    const int K = [&] {
+        int need = 0;
+        int slo[3], shi[3], tlo[3], thi[3];
+        for (int a = 0; a < 3; a++) {
+            slo[a] = tlo[a] = 1 << 30;
+            shi[a] = thi[a] = -(1 << 30);
+        }
+        for (int i = 0; i < nx; i++)
+            for (int a = 0; a < 3; a++) {
+                const int v = xs[3 * i + a];
+                if (i < nsoln) {
+                    slo[a] = std::min(slo[a], v);
+                    shi[a] = std::max(shi[a], v);
+                }
+                tlo[a] = std::min(tlo[a], v);
+                thi[a] = std::max(thi[a], v);
+            }
+        for (int a = 0; a < 3; a++) {
+            const long m = std::max(std::labs((long)tlo[a] * B - ((long)shi[a] * B + B - 1)),
+                                    std::labs(((long)thi[a] * B + B - 1) - (long)slo[a] * B));
+            const int n = poisson_pick_n((int)std::min<long>(2 * m + 2, 1 << 20));
+            need = std::max(need, n / 2 - 1);
+        }
+        return need;
+    }();
+    LGF_CHECK_ARG(K >= 1 && K <= 1024, "lgf_rk_plan: block set too large for the FFT sizes");
+    if ((st = lgf_table_build(LGF_KERNEL_LAPLACE7, 0.0, K, stream, &r->lgf_table)) != LGF_OK) return fail(st);
+    lgf_solve_desc pd;
+    pd.B = B;
+    pd.ncomp = 1;
+    pd.n_src = nsoln;
+    pd.n_dst = nx;
+    pd.src_blocks = xs.data();
+    pd.dst_blocks = xs.data();
+    pd.dx = d->dx;
+    pd.scale = -1.0;
+    if ((st = lgf_conv_plan(r->lgf_table, &pd, 1, nullptr, stream, &r->poisson)) != LGF_OK) return fail(st);
+    // integrating factor E(alpha/2) on D_xsoln, three components
+    if ((st = lgf_table_build(LGF_KERNEL_IFACTOR, 0.5 * r->alpha, 0, stream, &r->if_table)) != LGF_OK) return fail(st);
+    lgf_solve_desc id = pd;
+    id.ncomp = 3;
+    id.n_src = nx;
+    id.src_blocks = xs.data();
+    id.n_dst = 0;
+    id.dst_blocks = nullptr;
+    if ((st = lgf_conv_plan(r->if_table, &id, 1, nullptr, stream, &r->ifp)) != LGF_OK) return fail(st);
+    // workspaces: vector fields g, r, w11, w22, t1, t2, u1, u2 ; scalars s_supp, dhat
+    const size_t B3 = (size_t)B * B * B;
+    r->vec = (size_t)nx * 3 * B3;
+    r->scal_x = (size_t)nx * B3;
+    r->scal_s = (size_t)nsoln * B3;
+    const size_t total = 8 * r->vec + r->scal_x + r->scal_s;
+    if (cudaMalloc(&r->work, total * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("lgf_rk_plan: workspace allocation of %zu bytes failed", total * sizeof(float));
+        return fail(LGF_ERR_OOM);
+    }
+    r->bytes += total * sizeof(float);
+    (void)s;
+    lgf_plan *p = new (std::nothrow) lgf_plan();
+    if (!p) return fail(LGF_ERR_OOM);
+    p->kind = LGF_PLAN_RK;
+    p->rk = r;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    p->device = dev;
+    p->bytes = r->bytes;
+    *out = p;
+    return LGF_OK;
+}
+
+int lgf_rk_block_count(const lgf_plan *p, int which)
+{
+    if (!p || p->kind != LGF_PLAN_RK) return -1;
+    return which == 0 ? p->rk->n_x : p->rk->n_soln;
+}
+
+lgf_status lgf_rk_blocks(const lgf_plan *p, int which, int32_t *coords, int n)
+{
+    clear_error();
+    LGF_CHECK_ARG(p && coords && p->kind == LGF_PLAN_RK, "lgf_rk_blocks: not an RK plan");
+    const int cnt = which == 0 ? p->rk->n_x : p->rk->n_soln;
+    LGF_CHECK_ARG(n >= cnt, "lgf_rk_blocks: need room for %d blocks", cnt);
+    std::copy(p->rk->xsoln.begin(), p->rk->xsoln.begin() + 3 * (size_t)cnt, coords);
+    return LGF_OK;
+}
+
+lgf_status lgf_op_apply(lgf_plan *p, int op, const float *in, float *out, double coef, const double uinf[3],
+                        void *stream)
+{
+    clear_error();
+    LGF_CHECK_ARG(p && in && out && in != out, "lgf_op_apply: NULL or aliasing argument");
+    LGF_CHECK_ARG(p->kind == LGF_PLAN_RK, "lgf_op_apply: needs a plan from lgf_rk_plan");
+    LGF_CHECK_ARG(op >= 0 && op <= 4, "lgf_op_apply: unknown operator %d", op);
+    RkPlan *r = p->rk;
+    return op_launch(op, r->B, r->n_x, r->d_nbr27, op == 4 ? r->d_soln_keep : nullptr, in, out, r->dx, coef, uinf,
+                     (cudaStream_t)stream);
+}
+
+static lgf_status project(RkPlan *r, const float *rv, float *gd, cudaStream_t s)
+{
+    // gd = G d^, d^ = -M^xsoln L^{-1} M^supp G^T M^xsoln r
+    float *sx = r->work + 8 * r->vec;  // G^T r on xsoln cells
+    float *ss = sx + r->scal_x;        // restricted to supp
+    const int B3 = r->B * r->B * r->B;
+    LGF_TRY(op_launch(2, r->B, r->n_x, r->d_nbr27, nullptr, rv, sx, r->dx, 1.0, nullptr, s));
+    LGF_TRY(gather_launch(sx, ss, r->d_supp_idx, r->n_soln, B3, s));
+    const float *srcs[1] = {ss};
+    float *dsts[1] = {sx};  // d^ overwrites G^T r on xsoln
+    LGF_TRY(lgf_conv_execute(r->poisson, srcs, dsts, s));
+    LGF_TRY(op_launch(3, r->B, r->n_x, r->d_nbr27, nullptr, sx, gd, r->dx, 1.0, nullptr, s));
+    return LGF_OK;
+}
+
+lgf_status lgf_rk_step(lgf_plan *p, const float *u_in, float *u_out, const double uinf[3], void *stream)
+{
+    clear_error();
+    LGF_CHECK_ARG(p && u_in && u_out && uinf && u_in != u_out, "lgf_rk_step: NULL or aliasing argument");
+    LGF_CHECK_ARG(p->kind == LGF_PLAN_RK, "lgf_rk_step: needs a plan from lgf_rk_plan");
+    RkPlan *r = p->rk;
+    cudaStream_t s = (cudaStream_t)stream;
+    const double dt = r->dt;
+    // shifted Scheme A coefficients (eq. herk_shift)
+    const double r3 = std::sqrt(3.0);
+    const double a11 = 0.5, a21 = r3 / 3.0, a22 = (3.0 - r3) / 3.0;
+    const double a31 = (3.0 + r3) / 6.0, a32 = -r3 / 3.0, a33 = (3.0 + r3) / 6.0;
+    const size_t V = r->vec;
+    float *g = r->work, *rv = g + V, *w11 = rv + V, *w22 = w11 + V, *t1 = w22 + V, *t2 = t1 + V, *u1 = t2 + V,
+          *u2 = u1 + V;
+    float *gd = t2;  // reused
+    const int B = r->B;
+    const float *u0 = u_in;
+    auto NL = [&](const float *u, double a) {
+        return op_launch(4, B, r->n_x, r->d_nbr27, r->d_soln_keep, u, g, r->dx, -a * dt, uinf, s);
+    };
+    auto H = [&](const float *x, float *y) { return ifactor_apply(r->ifp, x, y, s); };
+    auto LC = [&](float *o, const float *x0, double c0, const float *x1 = nullptr, double c1 = 0,
+                  const float *x2 = nullptr, double c2 = 0, const float *x3 = nullptr, double c3 = 0) {
+        return lincomb_launch(o, (int64_t)V, x0, c0, x1, c1, x2, c2, x3, c3, s);
+    };
+    // stage 1
+    LGF_TRY(NL(u0, a11));
+    LGF_TRY(LC(rv, u0, 1.0, g, 1.0));
+    LGF_TRY(project(r, rv, gd, s));
+    LGF_TRY(LC(t1, rv, 1.0, gd, -1.0));
+    LGF_TRY(H(t1, u1));
+    LGF_TRY(LC(w11, g, 1.0 / (a11 * dt), gd, -1.0 / (a11 * dt)));
+    // stage 2
+    LGF_TRY(NL(u1, a22));
+    LGF_TRY(LC(t1, u0, 1.0, w11, dt * a21));
+    LGF_TRY(H(t1, rv));
+    LGF_TRY(LC(rv, rv, 1.0, g, 1.0));
+    LGF_TRY(project(r, rv, gd, s));
+    LGF_TRY(LC(t1, rv, 1.0, gd, -1.0));
+    LGF_TRY(H(t1, u2));
+    LGF_TRY(LC(w22, g, 1.0 / (a22 * dt), gd, -1.0 / (a22 * dt)));
+    // stage 3 (H^3 = I)
+    LGF_TRY(NL(u2, a33));
+    LGF_TRY(LC(t1, u0, 1.0, w11, dt * a31));
+    LGF_TRY(H(t1, u1));  // u1 no longer needed: holds H(u0 + dt a31 w11)
+    LGF_TRY(LC(t1, u1, 1.0, w22, dt * a32));
+    LGF_TRY(H(t1, rv));
+    LGF_TRY(LC(rv, rv, 1.0, g, 1.0));
+    LGF_TRY(project(r, rv, gd, s));
+    LGF_TRY(LC(u_out, rv, 1.0, gd, -1.0));
+    return LGF_OK;
+}
+
+}  // extern "C"

@@ -48,6 +48,19 @@ class _SolveDesc(ctypes.Structure):
     ]
 
 
+class _RkDesc(ctypes.Structure):
+    _fields_ = [
+        ("B", ctypes.c_int),
+        ("n_soln", ctypes.c_int),
+        ("soln_blocks", ctypes.POINTER(ctypes.c_int32)),
+        ("dx", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("re", ctypes.c_double),
+        ("scheme", ctypes.c_int),
+        ("reserved", ctypes.c_int * 3),
+    ]
+
+
 class _PlanOpts(ctypes.Structure):
     _fields_ = [("use_graph", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
 
@@ -80,6 +93,13 @@ _SIGS = {
     "lgf_plan_kernel_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "lgf_plan_kernel_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
                                              ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
+    "lgf_rk_plan": (ctypes.c_int, [ctypes.POINTER(_RkDesc), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "lgf_rk_block_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "lgf_rk_blocks": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_int]),
+    "lgf_rk_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.c_void_p]),
+    "lgf_op_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                    ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "lgf_plan_destroy": (None, [ctypes.c_void_p]),
     "lgf_last_error": (ctypes.c_char_p, []),
     "lgf_version": (ctypes.c_char_p, []),
@@ -239,6 +259,52 @@ class Plan:
             _check(L.lgf_plan_kernel_times(self._h, i, ctypes.byref(nm), ctypes.byref(la), ctypes.byref(ms)))
             out[nm.value.decode()] = (la.value, ms.value)
         return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lgf_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+OP_CURL, OP_CURL_T, OP_DIV_T, OP_GRAD, OP_NONLINEAR = 0, 1, 2, 3, 4
+
+
+class RKPlan:
+    """One IF-HERK (Scheme A) step on a block set (lgf_rk_plan / lgf_rk_step)."""
+
+    def __init__(self, B: int, soln_blocks, dx: float, dt: float, re: float, stream=None):
+        L = load()
+        self._soln = np.ascontiguousarray(soln_blocks, dtype=np.int32).reshape(-1, 3)
+        d = _RkDesc()
+        d.B, d.n_soln = int(B), len(self._soln)
+        d.soln_blocks = self._soln.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        d.dx, d.dt, d.re, d.scheme = float(dx), float(dt), float(re), 0
+        h = ctypes.c_void_p()
+        _check(L.lgf_rk_plan(ctypes.byref(d), _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self.B = B
+
+    def blocks(self, which: int = 0) -> np.ndarray:
+        """Block coordinates of D_xsoln (which=0, field order) or D_soln (which=1)."""
+        L = load()
+        n = L.lgf_rk_block_count(self._h, which)
+        out = np.zeros((n, 3), dtype=np.int32)
+        _check(L.lgf_rk_blocks(self._h, which, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), n))
+        return out
+
+    def step(self, u_in, u_out, uinf=(0.0, 0.0, 0.0), stream=None):
+        ui = (ctypes.c_double * 3)(*[float(v) for v in uinf])
+        _check(load().lgf_rk_step(self._h, _ptr(u_in), _ptr(u_out), ui, _stream(stream)))
+
+    def op(self, op: int, inp, out, coef: float = 1.0, uinf=(0.0, 0.0, 0.0), stream=None):
+        ui = (ctypes.c_double * 3)(*[float(v) for v in uinf])
+        _check(load().lgf_op_apply(self._h, int(op), _ptr(inp), _ptr(out), float(coef), ui, _stream(stream)))
 
     def close(self):
         if getattr(self, "_h", None):

@@ -1,0 +1,48 @@
+"""Pins for the oracle's IF-HERK step (Sec. 3.2 algorithm with Scheme A, Sec. 3.3
+projection, Sec. 5 masks).
+
+* With the nonlinear term switched off and a divergence-free start whose support
+  stays far from the edge of D_xsoln, the three stages reduce to
+  H^2 H^1 u = E(alpha/2) E(alpha/2) u = E(alpha) u (c~ = (1/2, 1, 1), H^3 = I,
+  semigroup of Sec. 3.2): checked against one integrating factor of alpha.
+* With the nonlinear term on, the last stage is a projection (H^3 = I), so
+  G^T u_{k+1} vanishes on the D_supp cells (eq. proj_final with L_C = -G^T G).
+* The shifted tableau of Scheme A (eq. herk_shift): a~ rows and c~ = (1/2, 1, 1).
+"""
+import math
+
+import numpy as np
+
+import oracle as O
+from tests.rk_cases import small_case
+
+
+def test_shifted_tableau_scheme_a():
+    at, ct, s = O.shifted_tableau()
+    assert s == 3
+    assert ct[1] == 0.5 and ct[2] == 1.0 and ct[3] == 1.0 and ct[0] == 0.0
+    assert math.isclose(at[(1, 1)], 0.5)
+    assert math.isclose(at[(2, 1)], math.sqrt(3) / 3) and math.isclose(at[(2, 2)], (3 - math.sqrt(3)) / 3)
+    assert math.isclose(at[(3, 1)] + at[(3, 2)] + at[(3, 3)], 1.0)  # b sums to 1
+
+
+def test_linear_step_is_one_integrating_factor():
+    cs = small_case(B=8)
+    u0 = cs["u0"]
+    dt, re, dx = 0.5, 10.0, 1.0       # alpha = 0.05
+    cube = O.lgf_cube(64)
+    u1 = O.if_herk_step(u0, dt, re, dx, (0.0, 0.0, 0.0), cs["masks"], cube, nonlinear=False)
+    ref = O.ifactor_masked(O.ifactor_taps(dt / (re * dx * dx)), u0, cs["masks"]["xsoln"])
+    assert np.abs(u1 - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+def test_step_is_divergence_free_on_supp():
+    cs = small_case(B=8)
+    u0 = cs["u0"]
+    dt, re, dx = 0.5, 10.0, 1.0
+    cube = O.lgf_cube(64)
+    u1 = O.if_herk_step(u0, dt, re, dx, (0.05, -0.02, 0.1), cs["masks"], cube, nonlinear=True)
+    div = O.op_Gt(u1, dx)
+    supp = cs["masks"]["supp"]
+    assert np.abs(div[supp]).max() < 1e-11 * np.abs(u1).max() / dx
+    assert np.abs(u1 - u0).max() > 1e-4 * np.abs(u0).max()  # the step did something
