@@ -331,6 +331,155 @@ def bench_gpu(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# other workloads (not the headline metric): each prints one JSON line with its
+# own metric; device time with CUDA events, L2 flushed between steps.
+# ---------------------------------------------------------------------------
+def _dilate(blocks):
+    s = set(map(tuple, np.asarray(blocks).tolist()))
+    out = set()
+    for (x, y, z) in s:
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    out.add((x + dx, y + dy, z + dz))
+    return np.array(sorted(out), dtype=np.int32)
+
+
+def aux_workload(name, lgf, torch):
+    """Returns (step_fn, plans, points_per_step, config, graph_note)."""
+    from paper_1601_00035_gb300 import inputs
+    if name == "blobs32":
+        f = inputs.gaussian_blobs(32)
+        c = inputs.block_grid(f.shape, B)
+        t = lgf.Table(lgf.LAPLACE7, max_offset=lgf.required_max_offset(c, c, B))
+        p = lgf.Plan(t, [lgf.Solve(B, 1, c, c)])
+        src = torch.from_numpy(inputs.to_blocks(f, B, c)).cuda()
+        dst = torch.zeros_like(src)
+        return (lambda: p.execute([src], [dst])), [p], 32 ** 3, {
+            "workload": "scalar Poisson, 32^3 box, 3 Gaussian blobs, 16^3 blocks"}, [t]
+    if name == "if128":
+        u = inputs.two_ring_velocity()
+        c = inputs.block_grid(u.shape[1:], B)
+        x = torch.from_numpy(inputs.to_blocks(u, B, c)).cuda()
+        ys = [torch.zeros_like(x) for _ in range(3)]
+        tabs = [lgf.Table(lgf.IFACTOR, alpha=a) for a in (0.05, 0.2, 1.0)]
+        plans = [lgf.Plan(tb, [lgf.Solve(B, 3, c, None)]) for tb in tabs]
+        f = inputs.gaussian_blobs(32)
+        cb = inputs.block_grid(f.shape, B)
+        tp = lgf.Table(lgf.LAPLACE7, max_offset=lgf.required_max_offset(cb, cb, B))
+        pp = lgf.Plan(tp, [lgf.Solve(B, 1, cb, cb)])
+        fs = torch.from_numpy(inputs.to_blocks(f, B, cb)).cuda()
+        fd = torch.zeros_like(fs)
+
+        def step():
+            for pl, y in zip(plans, ys):
+                pl.ifactor(x, y)
+            pp.execute([fs], [fd])
+        return step, plans + [pp], 3 * x.numel() + 32 ** 3, {
+            "workload": "integrating factor on a 3 x 128^3 two-ring velocity, alpha in {0.05, 0.2, 1.0} "
+                        "(R = 7, 9, 15), plus the 32^3 Poisson solve, one captured graph per step"}, tabs + [tp]
+    if name == "rk256":
+        n, R0c, dcells = 256, 50.0, 10.0
+        dx = 1.0 / R0c                      # R0 = 1, Gamma = 1
+        dt, re = 0.01721, 500.0             # Sec. 6.4: dt Gamma/R0^2 = 0.01721, Re = 500
+        uinf = (0.0, 0.0, -0.18686)
+        axis = inputs.random_axis_tilted(inputs.rng_for(4))
+        w = inputs.vortex_ring_edges(n, R0c, dcells, axis) / dx ** 2   # physical vorticity
+        supp = inputs.active_blocks(w, B, 1e-6)
+        rk = lgf.RKPlan(B, supp, dx, dt, re)
+        xs = rk.blocks(0)
+        # initial velocity by the method itself: a = -L^-1 w (vector, D_supp -> D_xsoln), u = C^T a
+        K = lgf.required_max_offset(supp, xs, B)
+        t = lgf.Table(lgf.LAPLACE7, max_offset=K)
+        pv = lgf.Plan(t, [lgf.Solve(B, 3, supp, xs, dx=dx, scale=-1.0)])
+        ws = torch.from_numpy(inputs.to_blocks(w, B, supp)).cuda()
+        a = torch.zeros((len(xs), 3, B, B, B), device="cuda")
+        pv.execute([ws], [a])
+        u0 = torch.zeros_like(a)
+        rk.op(lgf.OP_CURL_T, a, u0)
+        u1 = torch.zeros_like(u0)
+        return (lambda: rk.step(u0, u1, uinf)), [rk], len(xs) * B ** 3, {
+            "workload": "one Scheme-A IF-HERK step, Re=500 ring (R0 = 50 dx, core 10 dx), 256^3 bounding box, "
+                        "D_supp = blocks with |w| > 1e-6 max, D_xsoln = one-block dilation",
+            "supp_blocks": int(len(supp)), "xsoln_blocks": int(len(xs)), "alpha": dt / (re * dx * dx),
+            "points": "D_xsoln points per step"}, [t, pv]
+    if name == "ragged64":
+        fs = inputs.ragged_ring_sources(nsolve=64)
+        solves, srcs, dsts, pts = [], [], [], 0
+        for f in fs:
+            sc = inputs.active_blocks(f, B, 1e-14)
+            dc = inputs.block_grid(f.shape, B)
+            solves.append(lgf.Solve(B, 1, sc, dc, scale=-1.0))
+            srcs.append(torch.from_numpy(inputs.to_blocks(f, B, sc)).cuda())
+            dsts.append(torch.zeros((len(dc), 1, B, B, B), device="cuda"))
+            pts += f.size
+        K = max(lgf.required_max_offset(s_.src_blocks, s_.dst_blocks, B) for s_ in solves)
+        t = lgf.Table(lgf.LAPLACE7, max_offset=K)
+        p = lgf.Plan(t, solves, use_graph=True)
+        return (lambda: p.execute(srcs, dsts)), [p], pts, {
+            "workload": "ragged batch of 64 scalar ring solves, edges 24..192 (log-uniform), one captured graph",
+            "points": "sum of e^3 over the batch"}, [t]
+    raise ValueError(name)
+
+
+def bench_aux(args):
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1601_00035_gb300 import build as libbuild
+    libbuild.build()
+    from paper_1601_00035_gb300 import lgf
+    step, plans, pts, cfg, keep = aux_workload(args.workload, lgf, torch)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        step()
+        flush.fill_(1.0)
+    torch.cuda.synchronize()
+    use_graph = args.workload == "if128"
+    graph = None
+    if use_graph:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        graph.replay()
+        torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        if graph is not None:
+            graph.replay()
+        else:
+            step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    dev_ms = sum(ms)
+    # per-kernel shares from a separate profiled pass (not in the timed region)
+    for p_ in plans:
+        p_.set_profiling(2)
+    for _ in range(min(args.steps, 20)):
+        step()
+    torch.cuda.synchronize()
+    kt = {}
+    for p_ in plans:
+        for k, v in p_.kernel_times().items():
+            a = kt.setdefault(k, [0, 0.0])
+            a[0] += v[0]
+            a[1] += v[1]
+        p_.set_profiling(0)
+    tot = sum(v[1] for v in kt.values()) or 1.0
+    line = {"metric": "Mpoints/s (%s)" % args.workload, "value": round(pts * args.steps / (dev_ms / 1e3) / 1e6, 1),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dev_ms / args.steps, 5), "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic", "config": cfg,
+            "kernels": {k: {"launches": v[0], "ms_per_launch": round(v[1] / max(v[0], 1), 5),
+                            "share": round(v[1] / tot, 4)} for k, v in kt.items()}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -339,11 +488,15 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="ring128", choices=["ring128", "blobs32", "if128", "rk256", "ragged64"],
+                    help="ring128 is the headline workload; the others print their own throughput")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return bench_reference(args)
+    if args.workload != "ring128":
+        return bench_aux(args)
     return bench_gpu(args)
 
 

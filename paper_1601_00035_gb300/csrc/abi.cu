@@ -742,6 +742,27 @@ lgf_status lgf_plan_set_profiling(lgf_plan *p, int enable)
     LGF_CHECK_ARG(p != nullptr && enable >= 0 && enable <= 2, "lgf_plan_set_profiling: bad argument");
     if (enable == 2) p->prof.clear();
     p->prof.on = enable != 0;
+    if (p->rk) {  // an RK plan also times the kernels of its Poisson and IF sub-plans
+        LGF_TRY(lgf_plan_set_profiling(p->rk->poisson, enable));
+        LGF_TRY(lgf_plan_set_profiling(p->rk->ifp, enable));
+    }
+    return LGF_OK;
+}
+
+// RK plans: fold the sub-plans' totals into the plan's own records
+static lgf_status merge_sub_profiles(lgf_plan *p)
+{
+    LGF_TRY(p->prof.collect());
+    if (!p->rk) return LGF_OK;
+    for (lgf_plan *sub : {p->rk->poisson, p->rk->ifp}) {
+        LGF_TRY(sub->prof.collect());
+        for (auto &r : sub->prof.recs) {
+            const int k = p->prof.rec_of(r.name.c_str());
+            p->prof.recs[k].launches += r.launches;
+            p->prof.recs[k].ms += r.ms;
+        }
+        sub->prof.recs.clear();
+    }
     return LGF_OK;
 }
 
@@ -749,7 +770,7 @@ lgf_status lgf_plan_kernel_count(lgf_plan *p, int *count)
 {
     clear_error();
     LGF_CHECK_ARG(p && count, "lgf_plan_kernel_count: NULL argument");
-    LGF_TRY(p->prof.collect());
+    LGF_TRY(merge_sub_profiles(p));
     *count = (int)p->prof.recs.size();
     return LGF_OK;
 }
@@ -758,7 +779,7 @@ lgf_status lgf_plan_kernel_times(lgf_plan *p, int i, const char **name, long lon
 {
     clear_error();
     LGF_CHECK_ARG(p != nullptr, "lgf_plan_kernel_times: NULL plan");
-    LGF_TRY(p->prof.collect());
+    LGF_TRY(merge_sub_profiles(p));
     LGF_CHECK_ARG(i >= 0 && i < (int)p->prof.recs.size(), "lgf_plan_kernel_times: index %d out of range", i);
     if (name) *name = p->prof.recs[i].name.c_str();
     if (launches) *launches = p->prof.recs[i].launches;

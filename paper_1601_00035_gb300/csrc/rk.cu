@@ -63,6 +63,31 @@ void free_rk(RkPlan *r)
     delete r;
 }
 
+// run a launch between two profiling events of the plan (when enabled)
+template <typename F>
+lgf_status timed(Profiler &pr, const char *name, cudaStream_t s, F &&f)
+{
+    if (pr.on) pr.begin(s);
+    lgf_status st = f();
+    if (pr.on && st == LGF_OK) pr.end(name, s);
+    return st;
+}
+
+lgf_status rk_project(RkPlan *r, Profiler &pr, const float *rv, float *gd, cudaStream_t s)
+{
+    // gd = G d^, d^ = -M^xsoln L^{-1} M^supp G^T M^xsoln r
+    float *sx = r->work + 8 * r->vec;  // G^T r on xsoln cells
+    float *ss = sx + r->scal_x;        // restricted to supp
+    const int B3 = r->B * r->B * r->B;
+    LGF_TRY(timed(pr, "op_div_t", s, [&] { return op_launch(2, r->B, r->n_x, r->d_nbr27, nullptr, rv, sx, r->dx, 1.0, nullptr, s); }));
+    LGF_TRY(timed(pr, "gather_supp", s, [&] { return gather_launch(sx, ss, r->d_supp_idx, r->n_soln, B3, s); }));
+    const float *srcs[1] = {ss};
+    float *dsts[1] = {sx};  // d^ overwrites G^T r on xsoln
+    LGF_TRY(lgf_conv_execute(r->poisson, srcs, dsts, s));
+    LGF_TRY(timed(pr, "op_grad", s, [&] { return op_launch(3, r->B, r->n_x, r->d_nbr27, nullptr, sx, gd, r->dx, 1.0, nullptr, s); }));
+    return LGF_OK;
+}
+
 }  // namespace lgf
 
 using namespace lgf;
@@ -241,21 +266,6 @@ lgf_status lgf_op_apply(lgf_plan *p, int op, const float *in, float *out, double
                      (cudaStream_t)stream);
 }
 
-static lgf_status project(RkPlan *r, const float *rv, float *gd, cudaStream_t s)
-{
-    // gd = G d^, d^ = -M^xsoln L^{-1} M^supp G^T M^xsoln r
-    float *sx = r->work + 8 * r->vec;  // G^T r on xsoln cells
-    float *ss = sx + r->scal_x;        // restricted to supp
-    const int B3 = r->B * r->B * r->B;
-    LGF_TRY(op_launch(2, r->B, r->n_x, r->d_nbr27, nullptr, rv, sx, r->dx, 1.0, nullptr, s));
-    LGF_TRY(gather_launch(sx, ss, r->d_supp_idx, r->n_soln, B3, s));
-    const float *srcs[1] = {ss};
-    float *dsts[1] = {sx};  // d^ overwrites G^T r on xsoln
-    LGF_TRY(lgf_conv_execute(r->poisson, srcs, dsts, s));
-    LGF_TRY(op_launch(3, r->B, r->n_x, r->d_nbr27, nullptr, sx, gd, r->dx, 1.0, nullptr, s));
-    return LGF_OK;
-}
-
 lgf_status lgf_rk_step(lgf_plan *p, const float *u_in, float *u_out, const double uinf[3], void *stream)
 {
     clear_error();
@@ -274,18 +284,21 @@ lgf_status lgf_rk_step(lgf_plan *p, const float *u_in, float *u_out, const doubl
     float *gd = t2;  // reused
     const int B = r->B;
     const float *u0 = u_in;
+    Profiler &pr = p->prof;
     auto NL = [&](const float *u, double a) {
-        return op_launch(4, B, r->n_x, r->d_nbr27, r->d_soln_keep, u, g, r->dx, -a * dt, uinf, s);
+        return timed(pr, "op_nonlinear", s,
+                     [&] { return op_launch(4, B, r->n_x, r->d_nbr27, r->d_soln_keep, u, g, r->dx, -a * dt, uinf, s); });
     };
     auto H = [&](const float *x, float *y) { return ifactor_apply(r->ifp, x, y, s); };
     auto LC = [&](float *o, const float *x0, double c0, const float *x1 = nullptr, double c1 = 0,
                   const float *x2 = nullptr, double c2 = 0, const float *x3 = nullptr, double c3 = 0) {
-        return lincomb_launch(o, (int64_t)V, x0, c0, x1, c1, x2, c2, x3, c3, s);
+        return timed(pr, "lincomb", s, [&] { return lincomb_launch(o, (int64_t)V, x0, c0, x1, c1, x2, c2, x3, c3, s); });
     };
+    auto project = [&](const float *rvv, float *gdd) { return rk_project(r, pr, rvv, gdd, s); };
     // stage 1
     LGF_TRY(NL(u0, a11));
     LGF_TRY(LC(rv, u0, 1.0, g, 1.0));
-    LGF_TRY(project(r, rv, gd, s));
+    LGF_TRY(project(rv, gd));
     LGF_TRY(LC(t1, rv, 1.0, gd, -1.0));
     LGF_TRY(H(t1, u1));
     LGF_TRY(LC(w11, g, 1.0 / (a11 * dt), gd, -1.0 / (a11 * dt)));
@@ -294,7 +307,7 @@ lgf_status lgf_rk_step(lgf_plan *p, const float *u_in, float *u_out, const doubl
     LGF_TRY(LC(t1, u0, 1.0, w11, dt * a21));
     LGF_TRY(H(t1, rv));
     LGF_TRY(LC(rv, rv, 1.0, g, 1.0));
-    LGF_TRY(project(r, rv, gd, s));
+    LGF_TRY(project(rv, gd));
     LGF_TRY(LC(t1, rv, 1.0, gd, -1.0));
     LGF_TRY(H(t1, u2));
     LGF_TRY(LC(w22, g, 1.0 / (a22 * dt), gd, -1.0 / (a22 * dt)));
@@ -305,7 +318,7 @@ lgf_status lgf_rk_step(lgf_plan *p, const float *u_in, float *u_out, const doubl
     LGF_TRY(LC(t1, u1, 1.0, w22, dt * a32));
     LGF_TRY(H(t1, rv));
     LGF_TRY(LC(rv, rv, 1.0, g, 1.0));
-    LGF_TRY(project(r, rv, gd, s));
+    LGF_TRY(project(rv, gd));
     LGF_TRY(LC(u_out, rv, 1.0, gd, -1.0));
     return LGF_OK;
 }

@@ -298,6 +298,11 @@ class RKPlan:
         _check(L.lgf_rk_blocks(self._h, which, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), n))
         return out
 
+    def set_profiling(self, enable: int):
+        _check(load().lgf_plan_set_profiling(self._h, int(enable)))
+
+    kernel_times = Plan.kernel_times
+
     def step(self, u_in, u_out, uinf=(0.0, 0.0, 0.0), stream=None):
         ui = (ctypes.c_double * 3)(*[float(v) for v in uinf])
         _check(load().lgf_rk_step(self._h, _ptr(u_in), _ptr(u_out), ui, _stream(stream)))
