@@ -81,7 +81,10 @@ typedef struct {
 
 typedef struct {
     int use_graph;   /* 1: capture the execute launch sequence in a CUDA graph on first use */
-    int reserved[7]; /* must be zero */
+    int precision;   /* 0: FP32 data and transforms (lgf_conv_execute);
+                        1: FP64 data and transforms, FP64 spectrum (lgf_conv_execute_f64 only;
+                           FFT lengths up to 512) */
+    int reserved[6]; /* must be zero */
 } lgf_plan_opts;
 
 /* ---------------------------------------------------------------------------
@@ -132,6 +135,10 @@ lgf_status lgf_plan_workspace_bytes(const lgf_plan *p, size_t *bytes);
  * overwritten on every target point) = scale * dx^2 * G * src[i] (device,
  * [n_src][ncomp][B^3] FP32).  Asynchronous on `stream`; no allocation. */
 lgf_status lgf_conv_execute(lgf_plan *p, const float *const *src, float *const *dst, void *stream);
+
+/* FP64 variant for plans built with opts->precision = 1: src[i], dst[i] are
+ * device FP64 arrays with the same layout.  Asynchronous; no allocation. */
+lgf_status lgf_conv_execute_f64(lgf_plan *p, const double *const *src, double *const *dst, void *stream);
 
 /* Same as lgf_conv_execute with HOST buffers: copies every src[i] to
  * plan-owned device staging, executes, copies the results to dst[i] and

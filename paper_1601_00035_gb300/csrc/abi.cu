@@ -92,6 +92,14 @@ void free_plan(lgf_plan *p)
     for (auto &sp : p->spectra) cudaFree(sp.d_Kh);
     cudaFree(p->d_wsA);
     cudaFree(p->d_wsB);
+    cudaFree(p->d_wsA64);
+    cudaFree(p->d_wsB64);
+    for (auto &sp : p->spectra) cudaFree(sp.d_Kh64);
+    for (auto w : p->lane_wsA) cudaFree(w);
+    for (auto w : p->lane_wsB) cudaFree(w);
+    for (auto st : p->lanes) cudaStreamDestroy(st);
+    for (auto e : p->lane_done) cudaEventDestroy(e);
+    if (p->fork) cudaEventDestroy(p->fork);
     cudaFree(p->d_acc);
     cudaFree(p->ifp.nbz);
     cudaFree(p->ifp.nby);
@@ -468,17 +476,62 @@ static lgf_status plan_poisson(lgf_plan *p, const lgf_table *t, const lgf_solve_
             Spectrum &spr = p->spectra.back();
             const size_t nK = (size_t)(g.N[0] / 2 + 1) * (g.N[1] / 2 + 1) * (g.N[2] / 2 + 1);
             LGF_TRY(dalloc(&spr.d_Kh, nK, p->bytes));
-            LGF_TRY(build_spectrum(t->d_vals, t->K, g.N, spr.d_Kh, s));
+            if (p->precision == 1) LGF_TRY(dalloc(&spr.d_Kh64, nK, p->bytes));
+            LGF_TRY(build_spectrum(t->d_vals, t->K, g.N, spr.d_Kh, spr.d_Kh64, s));
             it = spec_index.emplace(key, (int)p->spectra.size() - 1).first;
         }
         q.spec = it->second;
     }
-    for (auto &q : p->solves) q.g.Kh = p->spectra[q.spec].d_Kh;
-    LGF_TRY(dalloc(&p->d_wsA, maxA, p->bytes));
-    LGF_TRY(dalloc(&p->d_wsB, maxB, p->bytes));
+    for (auto &q : p->solves) {
+        q.g.Kh = p->spectra[q.spec].d_Kh;
+        q.g.Kh64 = p->spectra[q.spec].d_Kh64;
+        q.g.mul64 = q.scale * q.dx * q.dx / ((double)q.g.N[0] * q.g.N[1] * q.g.N[2]);
+    }
     LGF_TRY(dalloc(&p->d_acc, 2, p->bytes));
-    p->wsA = maxA;
-    p->wsB = maxB;
+    if (p->precision == 1) {
+        for (auto &q : p->solves)
+            LGF_CHECK_ARG(q.g.N[0] <= 512 && q.g.N[1] <= 512 && q.g.N[2] <= 512,
+                          "FP64 plans are limited to FFT lengths <= 512 (need %d x %d x %d)", q.g.N[0], q.g.N[1], q.g.N[2]);
+        LGF_TRY(dalloc(&p->d_wsA64, maxA, p->bytes));
+        LGF_TRY(dalloc(&p->d_wsB64, maxB, p->bytes));
+        return LGF_OK;
+    }
+    if (n_solves == 1) {
+        LGF_TRY(dalloc(&p->d_wsA, maxA, p->bytes));
+        LGF_TRY(dalloc(&p->d_wsB, maxB, p->bytes));
+        p->wsA = maxA;
+        p->wsB = maxB;
+        return LGF_OK;
+    }
+    // independent solves run on up to 8 worker streams; longest-first greedy
+    // assignment on the workspace size as the cost estimate
+    const int nl = std::min(8, n_solves);
+    std::vector<int> order(n_solves);
+    for (int i = 0; i < n_solves; i++) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+        return p->solves[a].elemsA + p->solves[a].elemsB > p->solves[b].elemsA + p->solves[b].elemsB;
+    });
+    std::vector<double> load(nl, 0.0);
+    std::vector<size_t> la(nl, 0), lb(nl, 0);
+    p->solve_lane.assign(n_solves, 0);
+    for (int i : order) {
+        const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        p->solve_lane[i] = k;
+        load[k] += (double)(p->solves[i].elemsA + p->solves[i].elemsB);
+        la[k] = std::max(la[k], p->solves[i].elemsA);
+        lb[k] = std::max(lb[k], p->solves[i].elemsB);
+    }
+    p->lanes.assign(nl, nullptr);
+    p->lane_done.assign(nl, nullptr);
+    p->lane_wsA.assign(nl, nullptr);
+    p->lane_wsB.assign(nl, nullptr);
+    LGF_CUDA_TRY(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming));
+    for (int k = 0; k < nl; k++) {
+        LGF_CUDA_TRY(cudaStreamCreateWithFlags(&p->lanes[k], cudaStreamNonBlocking));
+        LGF_CUDA_TRY(cudaEventCreateWithFlags(&p->lane_done[k], cudaEventDisableTiming));
+        LGF_TRY(dalloc(&p->lane_wsA[k], la[k], p->bytes));
+        LGF_TRY(dalloc(&p->lane_wsB[k], lb[k], p->bytes));
+    }
     return LGF_OK;
 }
 
@@ -577,7 +630,8 @@ lgf_status lgf_conv_plan(const lgf_table *t, const lgf_solve_desc *solves, int n
     *out = nullptr;
     LGF_CHECK_ARG(t != nullptr && solves != nullptr && n_solves >= 1, "lgf_conv_plan: bad table/solves/n_solves");
     if (opts) {
-        for (int i = 0; i < 7; i++) LGF_CHECK_ARG(opts->reserved[i] == 0, "lgf_conv_plan: reserved option fields must be zero");
+        for (int i = 0; i < 6; i++) LGF_CHECK_ARG(opts->reserved[i] == 0, "lgf_conv_plan: reserved option fields must be zero");
+        LGF_CHECK_ARG(opts->precision == 0 || opts->precision == 1, "lgf_conv_plan: precision must be 0 or 1");
     }
     const int dev = current_device();
     if (dev != t->device) {
@@ -595,6 +649,7 @@ lgf_status lgf_conv_plan(const lgf_table *t, const lgf_solve_desc *solves, int n
     p->device = dev;
     p->table = t;
     p->use_graph = opts ? opts->use_graph : 0;
+    p->precision = opts ? opts->precision : 0;
     lgf_status st = t->kind == LGF_KERNEL_LAPLACE7 ? plan_poisson(p, t, solves, n_solves, s)
                                                    : plan_ifactor(p, t, solves, n_solves, s);
     if (st != LGF_OK) {
@@ -616,8 +671,40 @@ lgf_status lgf_plan_workspace_bytes(const lgf_plan *p, size_t *bytes)
 static lgf_status run_poisson(lgf_plan *p, const float *const *src, float *const *dst, cudaStream_t s,
                               bool capturing = false)
 {
-    for (size_t i = 0; i < p->solves.size(); i++)
-        LGF_TRY(poisson_launch(p->solves[i].g, src[i], dst[i], p->d_wsA, p->d_wsB, s, capturing ? nullptr : &p->prof));
+    Profiler *prof = capturing ? nullptr : &p->prof;
+    if (p->lanes.empty()) {
+        for (size_t i = 0; i < p->solves.size(); i++)
+            LGF_TRY(poisson_launch(p->solves[i].g, src[i], dst[i], p->d_wsA, p->d_wsB, s, prof));
+        return LGF_OK;
+    }
+    // fork: every lane waits for the work queued so far on the caller's stream
+    LGF_CUDA_TRY(cudaEventRecord(p->fork, s));
+    for (size_t k = 0; k < p->lanes.size(); k++) LGF_CUDA_TRY(cudaStreamWaitEvent(p->lanes[k], p->fork, 0));
+    for (size_t i = 0; i < p->solves.size(); i++) {
+        const int k = p->solve_lane[i];
+        LGF_TRY(poisson_launch(p->solves[i].g, src[i], dst[i], p->lane_wsA[k], p->lane_wsB[k], p->lanes[k], prof));
+    }
+    // join: the caller's stream waits for every lane
+    for (size_t k = 0; k < p->lanes.size(); k++) {
+        LGF_CUDA_TRY(cudaEventRecord(p->lane_done[k], p->lanes[k]));
+        LGF_CUDA_TRY(cudaStreamWaitEvent(s, p->lane_done[k], 0));
+    }
+    return LGF_OK;
+}
+
+lgf_status lgf_conv_execute_f64(lgf_plan *p, const double *const *src, double *const *dst, void *stream)
+{
+    clear_error();
+    LGF_CHECK_ARG(p && src && dst, "lgf_conv_execute_f64: NULL argument");
+    if (p->kind != LGF_KERNEL_LAPLACE7 || p->precision != 1) {
+        set_error("lgf_conv_execute_f64: needs a Poisson plan built with precision = 1");
+        return LGF_ERR_STATE;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    for (size_t i = 0; i < p->solves.size(); i++) {
+        LGF_CHECK_ARG(src[i] && dst[i], "lgf_conv_execute_f64: NULL buffer for solve %zu", i);
+        LGF_TRY(poisson_launch64(p->solves[i].g, src[i], dst[i], p->d_wsA64, p->d_wsB64, s, &p->prof));
+    }
     return LGF_OK;
 }
 
@@ -627,6 +714,10 @@ lgf_status lgf_conv_execute(lgf_plan *p, const float *const *src, float *const *
     LGF_CHECK_ARG(p && src && dst, "lgf_conv_execute: NULL argument");
     if (p->kind != LGF_KERNEL_LAPLACE7) {
         set_error("lgf_conv_execute: plan is not a Poisson plan (use ifactor_apply)");
+        return LGF_ERR_STATE;
+    }
+    if (p->precision != 0) {
+        set_error("lgf_conv_execute: FP64 plan (use lgf_conv_execute_f64)");
         return LGF_ERR_STATE;
     }
     for (size_t i = 0; i < p->solves.size(); i++)
@@ -677,7 +768,7 @@ lgf_status lgf_conv_execute_host(lgf_plan *p, const float *const *src, float *co
 {
     clear_error();
     LGF_CHECK_ARG(p && src && dst, "lgf_conv_execute_host: NULL argument");
-    if (p->kind != LGF_KERNEL_LAPLACE7) {
+    if (p->kind != LGF_KERNEL_LAPLACE7 || p->precision != 0) {
         set_error("lgf_conv_execute_host: plan is not a Poisson plan");
         return LGF_ERR_STATE;
     }

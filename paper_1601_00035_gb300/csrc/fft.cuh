@@ -306,16 +306,25 @@ __host__ __device__ constexpr bool in_lower_half(int e)
     return (e % R) * (N / R) < N / 2;
 }
 
-// Load w_N^j (j < N) into shared memory from the 1024-entry global table.
+// Load w_N^j (j < N) into shared memory from the 1024-entry global table of
+// the same precision (float2 for T = float, double2 for T = double).
 template <int N, typename T>
 __device__ __forceinline__ void load_twiddles(cx<T> *tw_s, const void *tw_global)
 {
     static_assert(N <= TW_MAX, "N too large");
     constexpr int STRIDE = TW_MAX / N;
-    const float2 *g = (const float2 *)tw_global;
-    for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        float2 w = __ldg(g + j * STRIDE);
-        tw_s[j] = {(T)w.x, (T)w.y};
+    if constexpr (sizeof(T) == 8) {
+        const double2 *g = (const double2 *)tw_global;
+        for (int j = threadIdx.x; j < N; j += blockDim.x) {
+            double2 w = __ldg(g + j * STRIDE);
+            tw_s[j] = {w.x, w.y};
+        }
+    } else {
+        const float2 *g = (const float2 *)tw_global;
+        for (int j = threadIdx.x; j < N; j += blockDim.x) {
+            float2 w = __ldg(g + j * STRIDE);
+            tw_s[j] = {w.x, w.y};
+        }
     }
 }
 

@@ -22,6 +22,8 @@ struct Geom {
     const int *dst_lut;  // [nbT_z][nbT_y][nbT_x] -> target block index, -1 if none
     const float *Kh;     // real even spectrum octant [Nz/2+1][Ny/2+1][Nx/2+1]
     float mul;           // scale * dx^2 / (Nx Ny Nz)
+    const double *Kh64;  // FP64 copy (precision = FP64 plans only)
+    double mul64;
     int KX;              // Nx/2 + 1
 };
 
@@ -41,6 +43,7 @@ struct PoissonSolve {
 struct Spectrum {
     int N[3];
     float *d_Kh = nullptr;
+    double *d_Kh64 = nullptr;  // FP64 plans
 };
 
 // Optional per-kernel event timing (lgf_plan_set_profiling).
@@ -71,12 +74,15 @@ struct Profiler {
 // launchers (poisson.cu)
 lgf_status poisson_launch(const Geom &g, const float *src, float *dst, cx<float> *wsA, cx<float> *wsB,
                           cudaStream_t s, Profiler *prof = nullptr);
+lgf_status poisson_launch64(const Geom &g, const double *src, double *dst, cx<double> *wsA, cx<double> *wsB,
+                            cudaStream_t s, Profiler *prof = nullptr);
 bool poisson_supported_n(int n);
 lgf_status poisson_prepare();  // per-device constant tables; call outside stream capture
 int poisson_pick_n(int need);  // smallest supported FFT length >= need, 0 if none
 
 // spectrum construction (spectrum.cu): FP64 cosine transforms of the table samples
-lgf_status build_spectrum(const double *d_octant, int K, const int N[3], float *d_Kh, cudaStream_t s);
+lgf_status build_spectrum(const double *d_octant, int K, const int N[3], float *d_Kh, double *d_Kh64,
+                          cudaStream_t s);
 
 // tables (table.cu)
 lgf_status build_lgf_octant(int K, double *d_out, cudaStream_t s);
@@ -145,6 +151,15 @@ struct lgf_plan {
     std::vector<lgf::Spectrum> spectra;
     lgf::cx<float> *d_wsA = nullptr, *d_wsB = nullptr;
     size_t wsA = 0, wsB = 0;
+    int precision = 0;  // 0 FP32, 1 FP64
+    lgf::cx<double> *d_wsA64 = nullptr, *d_wsB64 = nullptr;
+    // several solves: worker streams ("lanes"), each with its own workspaces;
+    // execute forks them off the caller's stream with events and joins back
+    std::vector<cudaStream_t> lanes;
+    std::vector<cudaEvent_t> lane_done;
+    cudaEvent_t fork = nullptr;
+    std::vector<lgf::cx<float> *> lane_wsA, lane_wsB;
+    std::vector<int> solve_lane;
     double *d_acc = nullptr;  // residual accumulators
     // IF
     int B = 0, ncomp = 0, nblk = 0, R = 0;

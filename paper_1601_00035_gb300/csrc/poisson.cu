@@ -27,19 +27,31 @@ using fft::Plan;
 
 // Lines per block: y/z passes run LS consecutive kx lines (line-fast thread
 // mapping, coalesced rows of kx); x passes run whole rows (lane-fast mapping).
-template <int N>
+// (FP64 tiles are half as wide so that the static shared memory stays < 48 KB.)
+template <int N, typename T>
 struct TileY {
     static constexpr int G = Plan<N>::G;
-    static constexpr int LS = G == 1 ? 64 : (G >= 64 ? 8 : (G == 8 ? 32 : 16));
+    static constexpr int LS32 = G == 1 ? 64 : (G >= 64 ? 8 : (G == 8 ? 32 : 16));
+    static constexpr int LS = sizeof(T) == 8 ? (G >= 64 ? 2 : LS32 / 2) : LS32;
     static constexpr int LSP = LS + 1;
     static constexpr int threads = LS * G;
 };
-template <int N>
+template <int N, typename T>
 struct TileX {
     static constexpr int G = Plan<N>::G;
-    static constexpr int threads = G == 1 ? 64 : 256;
+    static constexpr int threads = G == 1 ? 64 : (sizeof(T) == 8 ? 128 : 256);
     static constexpr int LS = threads / G;
 };
+
+// spectrum pointer and factor of the requested precision
+template <typename T>
+__device__ __forceinline__ const T *kh_of(const Geom &g);
+template <>
+__device__ __forceinline__ const float *kh_of<float>(const Geom &g) { return g.Kh; }
+template <>
+__device__ __forceinline__ const double *kh_of<double>(const Geom &g) { return g.Kh64; }
+template <typename T>
+__device__ __forceinline__ T mul_of(const Geom &g) { return sizeof(T) == 8 ? (T)g.mul64 : (T)g.mul; }
 
 __device__ __forceinline__ int wrap_mod(int v, int n)
 {
@@ -49,16 +61,16 @@ __device__ __forceinline__ int wrap_mod(int v, int n)
 
 // ---------------------------------------------------------------------------
 // x forward: gather two source rows per complex line from the block list, R2C.
-template <int N>
-__global__ void __launch_bounds__(TileX<N>::threads) k_x_fwd(Geom g, const float *__restrict__ src,
-                                                              cx<float> *__restrict__ out, const float2 *tw_g)
+template <int N, typename T>
+__global__ void __launch_bounds__(TileX<N, T>::threads) k_x_fwd(Geom g, const T *__restrict__ src,
+                                                                 cx<T> *__restrict__ out, const void *tw_g)
 {
-    using TL = TileX<N>;
+    using TL = TileX<N, T>;
     constexpr int E = Plan<N>::E;
     using SM = fft::Smem<N, false>;
-    __shared__ cx<float> buf[TL::LS * SM::NP + 8];
-    __shared__ cx<float> tw[N];
-    fft::load_twiddles<N, float>(tw, tw_g);
+    __shared__ cx<T> buf[TL::LS * SM::NP + 8];
+    __shared__ cx<T> tw[N];
+    fft::load_twiddles<N, T>(tw, tw_g);
     const int c = blockIdx.y;
     const int j = threadIdx.x % TL::G, l = threadIdx.x / TL::G;
     const int nrows = g.Es[1] * g.Es[2];
@@ -68,16 +80,16 @@ __global__ void __launch_bounds__(TileX<N>::threads) k_x_fwd(Geom g, const float
     const int z = row_ok ? r0 / g.Es[1] : 0, y = row_ok ? r0 - z * g.Es[1] : 0;
     const int lut_row = ((z / B) * g.nbS[1] + y / B) * g.nbS[0];
     const size_t in_blk = (size_t)(z % B) * B * B + (size_t)(y % B) * B;
-    cx<float> v[E];
+    cx<T> v[E];
 #pragma unroll
     for (int e = 0; e < E; e++) {
-        v[e] = {0.f, 0.f};
+        v[e] = {(T)0, (T)0};
         if (fft::in_lower_half<N, false>(e)) {
             const int pos = fft::in_pos<N, false>(e, j);
             if (row_ok && pos < g.Es[0]) {
                 const int blk = __ldg(g.src_lut + lut_row + pos / B);
                 if (blk >= 0) {
-                    const float *p = src + (size_t)(blk * g.ncomp + c) * B * B * B + in_blk + (pos % B);
+                    const T *p = src + (size_t)(blk * g.ncomp + c) * B * B * B + in_blk + (pos % B);
                     v[e] = {__ldg(p), __ldg(p + B)};
                 }
             }
@@ -85,7 +97,7 @@ __global__ void __launch_bounds__(TileX<N>::threads) k_x_fwd(Geom g, const float
     }
     __syncthreads();  // twiddles
     SM sm{0};
-    fft::transform<N, false, false, float>(v, buf, tw, sm, l, j);
+    fft::transform<N, false, false, T>(v, buf, tw, sm, l, j);
 #pragma unroll
     for (int e = 0; e < E; e++) buf[sm.at(fft::out_pos<N, false>(e, j), l)] = v[e];
     __syncthreads();
@@ -95,11 +107,12 @@ __global__ void __launch_bounds__(TileX<N>::threads) k_x_fwd(Geom g, const float
         const int ll = idx / KX, k = idx - ll * KX;
         const int rr = 2 * (blockIdx.x * TL::LS + ll);
         if (rr >= nrows) continue;
-        const cx<float> zk = buf[sm.at(k, ll)];
-        const cx<float> zn = buf[sm.at((N - k) & (N - 1), ll)];
+        const cx<T> zk = buf[sm.at(k, ll)];
+        const cx<T> zn = buf[sm.at((N - k) & (N - 1), ll)];
         const size_t row = ((size_t)c * nrows + rr) * KX;
-        out[row + k] = {0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y)};
-        out[row + KX + k] = {0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x)};
+        const T h = (T)0.5;
+        out[row + k] = {h * (zk.x + zn.x), h * (zk.y - zn.y)};
+        out[row + KX + k] = {h * (zk.y + zn.y), -h * (zk.x - zn.x)};
     }
 }
 
@@ -108,16 +121,16 @@ __global__ void __launch_bounds__(TileX<N>::threads) k_x_fwd(Geom g, const float
 //   MODE 0: in [c][Es_z][Es_y][KX] -> out [c][Es_z][Ny][KX]
 //   MODE 1: in [c][Es_z][Ny][KX]   -> out [c][Et_z][Ny][KX]
 //   MODE 2: in [c][Et_z][Ny][KX]   -> out [c][Et_z][Et_y][KX]
-template <int N, int MODE>
-__global__ void __launch_bounds__(TileY<N>::threads) k_line(Geom g, const cx<float> *__restrict__ in,
-                                                             cx<float> *__restrict__ out, const float2 *tw_g)
+template <int N, int MODE, typename T>
+__global__ void __launch_bounds__(TileY<N, T>::threads) k_line(Geom g, const cx<T> *__restrict__ in,
+                                                                cx<T> *__restrict__ out, const void *tw_g)
 {
-    using TL = TileY<N>;
+    using TL = TileY<N, T>;
     constexpr int E = Plan<N>::E;
     using SM = fft::Smem<N, true>;
-    __shared__ cx<float> buf[N * TL::LSP];
-    __shared__ cx<float> tw[N];
-    fft::load_twiddles<N, float>(tw, tw_g);
+    __shared__ cx<T> buf[N * TL::LSP];
+    __shared__ cx<T> tw[N];
+    fft::load_twiddles<N, T>(tw, tw_g);
     const int KX = g.KX;
     const int l = threadIdx.x % TL::LS, j = threadIdx.x / TL::LS;
     const int kx = blockIdx.x * TL::LS + l;
@@ -126,11 +139,11 @@ __global__ void __launch_bounds__(TileY<N>::threads) k_line(Geom g, const cx<flo
     const int c = blockIdx.z;
     const int Ny = g.N[1];
     SM sm{TL::LSP};
-    cx<float> v[E];
+    cx<T> v[E];
     constexpr bool INV0 = MODE == 2;  // first transform direction
 #pragma unroll
     for (int e = 0; e < E; e++) {
-        v[e] = {0.f, 0.f};
+        v[e] = {(T)0, (T)0};
         const int pos = fft::in_pos<N, INV0>(e, j);
         if constexpr (MODE == 0) {
             if (fft::in_lower_half<N, false>(e) && ok && pos < g.Es[1])
@@ -144,25 +157,26 @@ __global__ void __launch_bounds__(TileY<N>::threads) k_line(Geom g, const cx<flo
     }
     __syncthreads();  // twiddles
     if constexpr (MODE == 0) {
-        fft::transform<N, false, true, float>(v, buf, tw, sm, l, j);
+        fft::transform<N, false, true, T>(v, buf, tw, sm, l, j);
         if (ok) {
 #pragma unroll
             for (int e = 0; e < E; e++)
                 out[(((size_t)c * g.Es[2] + p) * N + fft::out_pos<N, false>(e, j)) * KX + kx] = v[e];
         }
     } else if constexpr (MODE == 1) {
-        fft::transform<N, false, true, float>(v, buf, tw, sm, l, j);
+        fft::transform<N, false, true, T>(v, buf, tw, sm, l, j);
         const int kyf = p <= Ny / 2 ? p : Ny - p;
-        const float *krow = g.Kh + (size_t)kyf * KX + (ok ? kx : 0);
+        const T *krow = kh_of<T>(g) + (size_t)kyf * KX + (ok ? kx : 0);
         const size_t kstride = (size_t)(Ny / 2 + 1) * KX;
+        const T mul = mul_of<T>(g);
 #pragma unroll
         for (int e = 0; e < E; e++) {
             const int pos = fft::out_pos<N, false>(e, j);
             const int kzf = pos <= N / 2 ? pos : N - pos;
-            const float w = g.mul * __ldg(krow + kzf * kstride);
+            const T w = mul * __ldg(krow + kzf * kstride);
             v[e] = {v[e].x * w, v[e].y * w};
         }
-        fft::transform<N, true, true, float>(v, buf, tw, sm, l, j);
+        fft::transform<N, true, true, T>(v, buf, tw, sm, l, j);
         if (ok) {
             const int dz = g.T0[2] - g.S0[2];
 #pragma unroll
@@ -172,7 +186,7 @@ __global__ void __launch_bounds__(TileY<N>::threads) k_line(Geom g, const cx<flo
             }
         }
     } else {
-        fft::transform<N, true, true, float>(v, buf, tw, sm, l, j);
+        fft::transform<N, true, true, T>(v, buf, tw, sm, l, j);
         if (ok) {
             const int dy = g.T0[1] - g.S0[1];
 #pragma unroll
@@ -186,16 +200,16 @@ __global__ void __launch_bounds__(TileY<N>::threads) k_line(Geom g, const cx<flo
 
 // x inverse: two target rows per complex line (Z = A + i B with Hermitian
 // extension), C2R, scatter into the target block list.
-template <int N>
-__global__ void __launch_bounds__(TileX<N>::threads) k_x_inv(Geom g, const cx<float> *__restrict__ in,
-                                                              float *__restrict__ dst, const float2 *tw_g)
+template <int N, typename T>
+__global__ void __launch_bounds__(TileX<N, T>::threads) k_x_inv(Geom g, const cx<T> *__restrict__ in,
+                                                                 T *__restrict__ dst, const void *tw_g)
 {
-    using TL = TileX<N>;
+    using TL = TileX<N, T>;
     constexpr int E = Plan<N>::E;
     using SM = fft::Smem<N, false>;
-    __shared__ cx<float> buf[TL::LS * SM::NP + 8];
-    __shared__ cx<float> tw[N];
-    fft::load_twiddles<N, float>(tw, tw_g);
+    __shared__ cx<T> buf[TL::LS * SM::NP + 8];
+    __shared__ cx<T> tw[N];
+    fft::load_twiddles<N, T>(tw, tw_g);
     constexpr int KX = N / 2 + 1;
     const int c = blockIdx.y;
     const int j = threadIdx.x % TL::G, l = threadIdx.x / TL::G;
@@ -203,13 +217,13 @@ __global__ void __launch_bounds__(TileX<N>::threads) k_x_inv(Geom g, const cx<fl
     const int r0 = 2 * (blockIdx.x * TL::LS + l);
     const bool row_ok = r0 < nrows;
     const size_t row = ((size_t)c * nrows + (row_ok ? r0 : 0)) * KX;
-    cx<float> v[E];
+    cx<T> v[E];
 #pragma unroll
     for (int e = 0; e < E; e++) {
-        v[e] = {0.f, 0.f};
+        v[e] = {(T)0, (T)0};
         if (row_ok) {
             const int pos = fft::in_pos<N, true>(e, j);
-            cx<float> a, b;
+            cx<T> a, b;
             if (pos <= N / 2) {
                 a = in[row + pos];
                 b = in[row + KX + pos];
@@ -222,7 +236,7 @@ __global__ void __launch_bounds__(TileX<N>::threads) k_x_inv(Geom g, const cx<fl
     }
     __syncthreads();  // twiddles
     SM sm{0};
-    fft::transform<N, true, false, float>(v, buf, tw, sm, l, j);
+    fft::transform<N, true, false, T>(v, buf, tw, sm, l, j);
     if (!row_ok) return;
     const int B = g.B;
     const int zt = r0 / g.Et[1], yt = r0 - zt * g.Et[1];
@@ -235,7 +249,7 @@ __global__ void __launch_bounds__(TileX<N>::threads) k_x_inv(Geom g, const cx<fl
         if (xt < g.Et[0]) {
             const int blk = __ldg(g.dst_lut + lut_row + xt / B);
             if (blk >= 0) {
-                float *p = dst + (size_t)(blk * g.ncomp + c) * B * B * B + out_blk + (xt % B);
+                T *p = dst + (size_t)(blk * g.ncomp + c) * B * B * B + out_blk + (xt % B);
                 p[0] = v[e].x;
                 p[B] = v[e].y;
             }
@@ -243,48 +257,81 @@ __global__ void __launch_bounds__(TileX<N>::threads) k_x_inv(Geom g, const cx<fl
     }
 }
 
-template <int N>
-lgf_status launch_x_fwd(const Geom &g, const float *src, cx<float> *out, cudaStream_t s)
+template <typename T>
+const void *tw_table() { return sizeof(T) == 8 ? (const void *)twiddle_table_f64() : (const void *)twiddle_table_f32(); }
+
+template <int N, typename T>
+lgf_status launch_x_fwd(const Geom &g, const T *src, cx<T> *out, cudaStream_t s)
 {
-    using TL = TileX<N>;
+    using TL = TileX<N, T>;
     const int nrows = g.Es[1] * g.Es[2];
     dim3 grid(ceil_div(nrows / 2, TL::LS), g.ncomp);
-    k_x_fwd<N><<<grid, TL::threads, 0, s>>>(g, src, out, twiddle_table_f32());
+    k_x_fwd<N, T><<<grid, TL::threads, 0, s>>>(g, src, out, tw_table<T>());
     LGF_LAUNCH_CHECK("x_fwd");
     return LGF_OK;
 }
-template <int N, int MODE>
-lgf_status launch_line(const Geom &g, const cx<float> *in, cx<float> *out, cudaStream_t s)
+template <int N, int MODE, typename T>
+lgf_status launch_line(const Geom &g, const cx<T> *in, cx<T> *out, cudaStream_t s)
 {
-    using TL = TileY<N>;
+    using TL = TileY<N, T>;
     int planes = MODE == 0 ? g.Es[2] : (MODE == 1 ? g.N[1] : g.Et[2]);
     dim3 grid(ceil_div(g.KX, TL::LS), planes, g.ncomp);
-    k_line<N, MODE><<<grid, TL::threads, 0, s>>>(g, in, out, twiddle_table_f32());
+    k_line<N, MODE, T><<<grid, TL::threads, 0, s>>>(g, in, out, tw_table<T>());
     LGF_LAUNCH_CHECK(MODE == 0 ? "y_fwd" : (MODE == 1 ? "z_mid" : "y_inv"));
     return LGF_OK;
 }
-template <int N>
-lgf_status launch_x_inv(const Geom &g, const cx<float> *in, float *dst, cudaStream_t s)
+template <int N, typename T>
+lgf_status launch_x_inv(const Geom &g, const cx<T> *in, T *dst, cudaStream_t s)
 {
-    using TL = TileX<N>;
+    using TL = TileX<N, T>;
     const int nrows = g.Et[1] * g.Et[2];
     dim3 grid(ceil_div(nrows / 2, TL::LS), g.ncomp);
-    k_x_inv<N><<<grid, TL::threads, 0, s>>>(g, in, dst, twiddle_table_f32());
+    k_x_inv<N, T><<<grid, TL::threads, 0, s>>>(g, in, dst, tw_table<T>());
     LGF_LAUNCH_CHECK("x_inv");
     return LGF_OK;
 }
 
-#define LGF_DISPATCH_N(n, CALL)            \
-    switch (n) {                           \
-        case 16: { constexpr int NN = 16; CALL; } break;     \
-        case 32: { constexpr int NN = 32; CALL; } break;     \
-        case 64: { constexpr int NN = 64; CALL; } break;     \
-        case 128: { constexpr int NN = 128; CALL; } break;   \
-        case 256: { constexpr int NN = 256; CALL; } break;   \
-        case 512: { constexpr int NN = 512; CALL; } break;   \
-        case 1024: { constexpr int NN = 1024; CALL; } break; \
-        default: set_error("unsupported FFT length %d", n); return LGF_ERR_ARG; \
+// N-dispatch; FP64 transforms stop at N = 512 (shared-memory budget).
+#define LGF_DISPATCH_N(T, n, CALL)                                                          \
+    switch (n) {                                                                            \
+        case 16: { constexpr int NN = 16; CALL; } break;                                    \
+        case 32: { constexpr int NN = 32; CALL; } break;                                    \
+        case 64: { constexpr int NN = 64; CALL; } break;                                    \
+        case 128: { constexpr int NN = 128; CALL; } break;                                  \
+        case 256: { constexpr int NN = 256; CALL; } break;                                  \
+        case 512: { constexpr int NN = 512; CALL; } break;                                  \
+        case 1024:                                                                          \
+            if constexpr (sizeof(T) == 4) { constexpr int NN = 1024; CALL; }                \
+            else { set_error("FP64 transforms are limited to N <= 512"); return LGF_ERR_ARG; } \
+            break;                                                                          \
+        default: set_error("unsupported FFT length %d", n); return LGF_ERR_ARG;             \
     }
+
+template <typename T>
+lgf_status launch_all(const Geom &g, const T *src, T *dst, cx<T> *wsA, cx<T> *wsB, cudaStream_t s, Profiler *prof)
+{
+    if (fft::upload_tw64() != cudaSuccess) {
+        set_error("twiddle upload failed");
+        return LGF_ERR_CUDA;
+    }
+    const bool P = prof && prof->on;
+    if (P) prof->begin(s);
+    LGF_DISPATCH_N(T, g.N[0], LGF_TRY((launch_x_fwd<NN, T>(g, src, wsA, s))));
+    if (P) prof->end("x_fwd_gather_r2c", s);
+    if (P) prof->begin(s);
+    LGF_DISPATCH_N(T, g.N[1], LGF_TRY((launch_line<NN, 0, T>(g, wsA, wsB, s))));
+    if (P) prof->end("y_fwd", s);
+    if (P) prof->begin(s);
+    LGF_DISPATCH_N(T, g.N[2], LGF_TRY((launch_line<NN, 1, T>(g, wsB, wsA, s))));
+    if (P) prof->end("z_fwd_mul_inv", s);
+    if (P) prof->begin(s);
+    LGF_DISPATCH_N(T, g.N[1], LGF_TRY((launch_line<NN, 2, T>(g, wsA, wsB, s))));
+    if (P) prof->end("y_inv", s);
+    if (P) prof->begin(s);
+    LGF_DISPATCH_N(T, g.N[0], LGF_TRY((launch_x_inv<NN, T>(g, wsB, dst, s))));
+    if (P) prof->end("x_inv_c2r_scatter", s);
+    return LGF_OK;
+}
 
 }  // namespace
 
@@ -312,27 +359,13 @@ int poisson_pick_n(int need)
 lgf_status poisson_launch(const Geom &g, const float *src, float *dst, cx<float> *wsA, cx<float> *wsB,
                           cudaStream_t s, Profiler *prof)
 {
-    if (fft::upload_tw64() != cudaSuccess) {
-        set_error("twiddle upload failed");
-        return LGF_ERR_CUDA;
-    }
-    const bool P = prof && prof->on;
-    if (P) prof->begin(s);
-    LGF_DISPATCH_N(g.N[0], LGF_TRY((launch_x_fwd<NN>(g, src, wsA, s))));
-    if (P) prof->end("x_fwd_gather_r2c", s);
-    if (P) prof->begin(s);
-    LGF_DISPATCH_N(g.N[1], LGF_TRY((launch_line<NN, 0>(g, wsA, wsB, s))));
-    if (P) prof->end("y_fwd", s);
-    if (P) prof->begin(s);
-    LGF_DISPATCH_N(g.N[2], LGF_TRY((launch_line<NN, 1>(g, wsB, wsA, s))));
-    if (P) prof->end("z_fwd_mul_inv", s);
-    if (P) prof->begin(s);
-    LGF_DISPATCH_N(g.N[1], LGF_TRY((launch_line<NN, 2>(g, wsA, wsB, s))));
-    if (P) prof->end("y_inv", s);
-    if (P) prof->begin(s);
-    LGF_DISPATCH_N(g.N[0], LGF_TRY((launch_x_inv<NN>(g, wsB, dst, s))));
-    if (P) prof->end("x_inv_c2r_scatter", s);
-    return LGF_OK;
+    return launch_all<float>(g, src, dst, wsA, wsB, s, prof);
+}
+
+lgf_status poisson_launch64(const Geom &g, const double *src, double *dst, cx<double> *wsA, cx<double> *wsB,
+                            cudaStream_t s, Profiler *prof)
+{
+    return launch_all<double>(g, src, dst, wsA, wsB, s, prof);
 }
 
 }  // namespace lgf

@@ -77,7 +77,8 @@ __global__ void k_to_f32(const double *__restrict__ in, float *__restrict__ out,
 
 }  // namespace
 
-lgf_status build_spectrum(const double *d_octant, int K, const int N[3], float *d_Kh, cudaStream_t s)
+lgf_status build_spectrum(const double *d_octant, int K, const int N[3], float *d_Kh, double *d_Kh64,
+                          cudaStream_t s)
 {
     const int hx = N[0] / 2, hy = N[1] / 2, hz = N[2] / 2;
     if (hx - 1 > K || hy - 1 > K || hz - 1 > K) {
@@ -115,6 +116,11 @@ lgf_status build_spectrum(const double *d_octant, int K, const int N[3], float *
             k_cos_axis<<<blocks, threads, 0, s>>>(cur, nxt, nx, ny, nz, axis, Na, ct);
             if (cudaGetLastError() != cudaSuccess) { set_error("k_cos_axis launch failed"); st = LGF_ERR_CUDA; goto done; }
             double *tmp = cur; cur = nxt; nxt = tmp;
+        }
+        if (d_Kh64 && cudaMemcpyAsync(d_Kh64, cur, total * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+            set_error("FP64 spectrum copy failed");
+            st = LGF_ERR_CUDA;
+            goto done;
         }
         k_to_f32<<<blocks, threads, 0, s>>>(cur, d_Kh, total);
         if (cudaGetLastError() != cudaSuccess) { set_error("k_to_f32 launch failed"); st = LGF_ERR_CUDA; goto done; }

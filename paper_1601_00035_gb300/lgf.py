@@ -62,7 +62,7 @@ class _RkDesc(ctypes.Structure):
 
 
 class _PlanOpts(ctypes.Structure):
-    _fields_ = [("use_graph", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+    _fields_ = [("use_graph", ctypes.c_int), ("precision", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
 _lib = None
@@ -81,6 +81,8 @@ _SIGS = {
     "lgf_plan_workspace_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     "lgf_conv_execute": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
                                         ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
+    "lgf_conv_execute_f64": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                                            ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
     "lgf_conv_execute_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
                                              ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
     "ifactor_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -189,7 +191,8 @@ class Solve:
 class Plan:
     """lgf_conv_plan over one or more solves."""
 
-    def __init__(self, table: Table, solves: Sequence[Solve], use_graph: bool = False, stream=None):
+    def __init__(self, table: Table, solves: Sequence[Solve], use_graph: bool = False, stream=None,
+                 precision: int = 0):
         L = load()
         self.table = table  # keep alive
         self.solves = list(solves)
@@ -205,6 +208,7 @@ class Plan:
             d.dx, d.scale = float(s.dx), float(s.scale)
         opts = _PlanOpts()
         opts.use_graph = 1 if use_graph else 0
+        opts.precision = int(precision)
         h = ctypes.c_void_p()
         _check(L.lgf_conv_plan(table._h, descs, len(self.solves), ctypes.byref(opts), _stream(stream), ctypes.byref(h)))
         self._h = h
@@ -220,6 +224,19 @@ class Plan:
         a = (ctypes.c_void_p * n)(*[_ptr(t) for t in src])
         b = (ctypes.c_void_p * n)(*[_ptr(t) for t in dst])
         _check(load().lgf_conv_execute(self._h, a, b, _stream(stream)))
+
+    def execute_f64(self, src, dst, stream=None):
+        """FP64 plans (precision=1): float64 device tensors."""
+        import torch
+
+        def p64(t):
+            if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+                raise TypeError("expected a contiguous float64 CUDA tensor")
+            return t.data_ptr()
+        n = len(self.solves)
+        a = (ctypes.c_void_p * n)(*[p64(t) for t in src])
+        b = (ctypes.c_void_p * n)(*[p64(t) for t in dst])
+        _check(load().lgf_conv_execute_f64(self._h, a, b, _stream(stream)))
 
     def execute_host(self, src: Sequence[np.ndarray], dst: Sequence[np.ndarray], stream=None):
         """Poisson with host float32 arrays (pinned for full bandwidth); synchronous."""
