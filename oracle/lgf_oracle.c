@@ -207,6 +207,51 @@ int oracle_lgf_octant(int K, double t_lo, double T, double panel, int ngl, doubl
     return 0;
 }
 
+/* G at an explicit list of offsets (a_i, b_i, c_i) (any signs), same
+ * quadrature and tail as oracle_lgf_octant; for offsets too large for a
+ * dense table.  nmax must be >= every |offset|. */
+int oracle_lgf_points(int64_t n, const int32_t *abc, int nmax, double t_lo, double T, double panel, int ngl,
+                      double *out)
+{
+    if (nmax < 0 || ngl < 2 || ngl > 64 || !(panel > 0.0) || !(T > t_lo) || !(t_lo > 0.0)) return -1;
+    double xg[64], wg[64];
+    oracle_gauss_legendre(ngl, xg, wg);
+    const double s0 = log(t_lo), s1 = log(T);
+    const int npan = (int)ceil((s1 - s0) / panel);
+    const double h = (s1 - s0) / npan;
+    const long nq = (long)npan * ngl;
+    double *wt = (double *)malloc(sizeof(double) * nq);
+    double *bes = (double *)malloc(sizeof(double) * nq * (nmax + 1));
+    if (!wt || !bes) { free(wt); free(bes); return -2; }
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 4) reduction(| : bad)
+    for (long q = 0; q < nq; q++) {
+        const int p = (int)(q / ngl), g = (int)(q % ngl);
+        const double t = exp(s0 + h * (p + 0.5 * (xg[g] + 1.0)));
+        wt[q] = 0.5 * h * wg[g] * t;
+        bad |= oracle_bessel_scaled(t, nmax, bes + q * (nmax + 1)) != 0;
+    }
+    const double c4pi = pow(4.0 * M_PI, -1.5);
+#pragma omp parallel for schedule(static) reduction(| : bad)
+    for (int64_t i = 0; i < n; i++) {
+        const int a = abs(abc[3 * i]), b = abs(abc[3 * i + 1]), c = abs(abc[3 * i + 2]);
+        if (a > nmax || b > nmax || c > nmax) { bad = 1; continue; }
+        double sum = 0.0, comp = 0.0;
+        for (long q = 0; q < nq; q++) {
+            const double *bq = bes + q * (nmax + 1);
+            double yk = wt[q] * bq[a] * bq[b] * bq[c] - comp;
+            double tk = sum + yk;
+            comp = (tk - sum) - yk;
+            sum = tk;
+        }
+        const double c1 = ((4.0 * a * a - 1.0) + (4.0 * b * b - 1.0) + (4.0 * c * c - 1.0)) / 16.0;
+        out[i] = -(sum + c4pi * (2.0 / sqrt(T) - (2.0 / 3.0) * c1 * pow(T, -1.5)));
+    }
+    free(wt);
+    free(bes);
+    return bad ? -3 : 0;
+}
+
 /* Expand an octant table into the dense cube D[z][y][x] = G(x, y, z),
  * 0 <= x, y, z <= K (the LGF is even in each coordinate and symmetric under
  * permutations, App. B). */

@@ -29,7 +29,7 @@ __all__ = [
     "octant_size", "asymptotic_G", "ifactor_taps", "ifactor_radius", "direct_conv",
     "direct_conv_box", "ifactor_direct", "shift", "op_G", "op_Gt", "op_C", "op_Ct", "op_D",
     "op_Dbar", "op_L", "op_N", "residual_L", "WATSON_W", "num_threads", "SCHEME_A", "shifted_tableau",
-    "block_mask", "ifactor_masked", "poisson_masked", "if_herk_step",
+    "block_mask", "ifactor_masked", "poisson_masked", "if_herk_step", "lgf_points",
 ]
 
 # Watson's integral for the simple cubic lattice, closed form (Watson 1939):
@@ -52,6 +52,8 @@ def lib() -> ctypes.CDLL:
     L.oracle_lgf_octant.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_int, _dp]
     L.oracle_octant_to_cube.argtypes = [ctypes.c_int, _dp, _dp]
+    L.oracle_lgf_points.argtypes = [ctypes.c_int64, _ip, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_int, _dp]
     L.oracle_direct_conv.argtypes = [ctypes.c_int, _dp, ctypes.c_int64, _ip, _dp,
                                      ctypes.c_int64, _ip, _dp]
     L.oracle_ifactor_direct.argtypes = [ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int,
@@ -116,6 +118,18 @@ def lgf_cube(K: int) -> np.ndarray:
     lib().oracle_octant_to_cube(int(K), _d(oct_), _d(cube))
     cube.setflags(write=False)
     return cube
+
+
+def lgf_points(offsets) -> np.ndarray:
+    """G at explicit integer offsets [n, 3] (App. B Bessel form, same quadrature as the table)."""
+    o = np.ascontiguousarray(offsets, dtype=np.int32).reshape(-1, 3)
+    nmax = int(np.abs(o).max()) if len(o) else 0
+    out = np.zeros(len(o))
+    q = QUAD_DEFAULT
+    rc = lib().oracle_lgf_points(len(o), _i(o), nmax, q["t_lo"], q["T"], q["panel"], int(q["ngl"]), _d(out))
+    if rc != 0:
+        raise RuntimeError("oracle_lgf_points failed (%d)" % rc)
+    return out
 
 
 def lgf_value(n, K: int | None = None) -> float:

@@ -31,7 +31,7 @@ using fft::Plan;
 template <int N, typename T>
 struct TileY {
     static constexpr int G = Plan<N>::G;
-    static constexpr int LS32 = G == 1 ? 64 : (G >= 64 ? 8 : (G == 8 ? 32 : 16));
+    static constexpr int LS32 = G == 1 ? 64 : (G >= 64 ? (N >= 1024 ? 4 : 8) : (G == 8 ? 32 : 16));
     static constexpr int LS = sizeof(T) == 8 ? (G >= 64 ? 2 : LS32 / 2) : LS32;
     static constexpr int LSP = LS + 1;
     static constexpr int threads = LS * G;

@@ -1,0 +1,89 @@
+"""Edge cases of the Poisson path: every FFT length class, single blocks,
+far-apart source and target sets (FFT length 1024), and argument errors.
+
+Lengths 16 and 32 run one thread per line; 64..256 two-stage transforms;
+512 and 1024 three-stage transforms.  Far offsets use the oracle's per-point
+LGF evaluation (same Bessel-integral quadrature as its tables)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1601_00035_gb300 import inputs
+from tests.helpers import built, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _solve(lgf, B, src_c, dst_c, f, ncomp=1):
+    K = lgf.required_max_offset(src_c, dst_c, B)
+    table = lgf.Table(lgf.LAPLACE7, max_offset=K)
+    plan = lgf.Plan(table, [lgf.Solve(B, ncomp, src_c, dst_c)])
+    d_src = torch.from_numpy(np.ascontiguousarray(f, dtype=np.float32)).cuda()
+    d_dst = torch.zeros((len(dst_c), ncomp, B, B, B), device="cuda")
+    plan.execute([d_src], [d_dst])
+    return d_dst.cpu().numpy()
+
+
+def _reference(f, src_c, dst_c, B, pts):
+    """Direct sum at sample points with G evaluated per offset."""
+    sp = inputs.block_points(src_c, B)
+    v = f[:, 0].reshape(-1).astype(np.float64)
+    offs = (np.asarray(pts)[:, None, :] - sp[None, :, :]).reshape(-1, 3)
+    g = O.lgf_points(offs).reshape(len(pts), len(sp))
+    return g @ v
+
+
+@pytest.mark.parametrize("dst", [[[0, 0, 0]], [[0, 0, 0], [1, 0, 0]], [[-1, 0, 0], [0, 1, 0], [1, 1, 1]]])
+def test_small_lengths(dst):
+    """Single source block B=8: FFT lengths 16 (same block) and 32/64 (neighbours)."""
+    lgf = built()
+    B = 8
+    rng = np.random.default_rng(len(dst))
+    src_c = np.array([[0, 0, 0]], dtype=np.int32)
+    dst_c = np.array(dst, dtype=np.int32)
+    f = rng.standard_normal((1, 1, B, B, B))
+    out = _solve(lgf, B, src_c, dst_c, f)
+    pts = inputs.block_points(dst_c, B)
+    K = lgf.required_max_offset(src_c, dst_c, B)
+    ref = O.direct_conv(O.lgf_cube(K), inputs.block_points(src_c, B), f.reshape(-1), pts)
+    assert rel_l2(out.reshape(-1), ref) < 1e-6
+
+
+@pytest.mark.parametrize("dst", [[[30, 0, 0]], [[0, 30, 30]]])
+def test_far_target_length_1024(dst):
+    """Target block 30 blocks (480 cells) from the source: FFT length 1024 on the far axes."""
+    lgf = built()
+    B = 16
+    rng = np.random.default_rng(7)
+    src_c = np.array([[0, 0, 0]], dtype=np.int32)
+    dst_c = np.array(dst, dtype=np.int32)
+    f = rng.standard_normal((1, 1, B, B, B))
+    out = _solve(lgf, B, src_c, dst_c, f)
+    pts = inputs.block_points(dst_c, B)
+    sel = rng.choice(len(pts), 48, replace=False)
+    ref = _reference(f, src_c, dst_c, B, pts[sel])
+    # Targets that see only the far field: the FP32 transforms round at the scale
+    # of the near field (|G(0)| rms(f) ~ 0.25 here), ~70x the far values (~0.01),
+    # so the FP32 bound 1e-6 relative to the near-field scale becomes 1e-6 * 0.25 / 0.01.
+    near = abs(O.lgf_value((0, 0, 0))) * np.sqrt(np.mean(f ** 2))
+    tol = 1e-6 * max(1.0, near / np.sqrt(np.mean(ref ** 2)))
+    assert rel_l2(out.reshape(-1)[sel], ref) < tol
+
+
+def test_argument_errors():
+    lgf = built()
+    t = lgf.Table(lgf.LAPLACE7, max_offset=31)
+    one = np.array([[0, 0, 0]], dtype=np.int32)
+    with pytest.raises(lgf.LGFError) as e:
+        lgf.Plan(t, [lgf.Solve(8, 1, np.zeros((0, 3), np.int32), one)])
+    assert e.value.status == lgf.LGF_ERR_ARG
+    with pytest.raises(lgf.LGFError):
+        lgf.Plan(t, [lgf.Solve(8, 4, one, one)])          # ncomp out of range
+    with pytest.raises(lgf.LGFError):
+        lgf.Plan(t, [lgf.Solve(8, 1, one, one, dx=0.0)])  # dx must be positive
+    p = lgf.Plan(t, [lgf.Solve(8, 1, one, one)])
+    x = torch.zeros((1, 1, 8, 8, 8), device="cuda")
+    with pytest.raises(lgf.LGFError) as e:
+        p.ifactor(x, torch.zeros_like(x))                   # wrong kind of plan
+    assert e.value.status == lgf.LGF_ERR_STATE

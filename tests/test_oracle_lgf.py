@@ -82,3 +82,14 @@ def test_monotone_and_negative():
     cube = O.lgf_cube(30)
     axis = cube[0, 0, :]
     assert np.all(axis < 0) and np.all(np.diff(axis) > 0)
+
+
+def test_points_equal_table():
+    rng = np.random.default_rng(1)
+    o = rng.integers(-40, 41, size=(200, 3))
+    cube = O.lgf_cube(40)
+    a = np.abs(o)
+    ref = cube[a[:, 2], a[:, 1], a[:, 0]]
+    # same quadrature; the Miller start index follows the largest requested offset,
+    # so agreement is to the last bits rather than bitwise
+    assert np.max(np.abs(O.lgf_points(o) - ref) / np.abs(ref)) < 2e-15
