@@ -139,7 +139,7 @@ def geometry(src_c, dst_c, ncomp):
         T0, T1 = t[:, a].min() * B, (t[:, a].max() + 1) * B - 1
         m = max(abs(T0 - S1), abs(T1 - S0))
         n = 16
-        while n < 2 * m + 2:
+        while n < max(2 * m + 2, 2 * (S1 - S0 + 1)):
             n *= 2
         N.append(n)
     return {"Es": Es, "Et": Et, "N": N, "ncomp": ncomp, "nsrc": len(s), "ndst": len(t)}

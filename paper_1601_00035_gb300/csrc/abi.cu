@@ -417,7 +417,11 @@ static lgf_status plan_poisson(lgf_plan *p, const lgf_table *t, const lgf_solve_
             const long lo = (long)g.T0[a] - (long)(g.S0[a] + g.Es[a] - 1);
             const long hi = (long)(g.T0[a] + g.Et[a] - 1) - (long)g.S0[a];
             const long maxabs = std::max(std::labs(lo), std::labs(hi));
-            const int n = poisson_pick_n((int)std::min<long>(2 * maxabs + 2, 1 << 20));
+            // exact embedding: N >= 2 maxabs + 2 (no two offsets share a wrapped
+            // index); N >= 2 Es keeps every source sample in the lower half of
+            // the line, which the forward transforms take as their zero pattern
+            const long need = std::max<long>(2 * maxabs + 2, 2L * g.Es[a]);
+            const int n = poisson_pick_n((int)std::min<long>(need, 1 << 20));
             LGF_CHECK_ARG(n > 0, "solve %d: source/target extent %ld along axis %d needs an FFT longer than 1024", i,
                           maxabs, a);
             g.N[a] = n;

@@ -126,22 +126,34 @@ __device__ __forceinline__ void level(cx<T> *a)
     }
 }
 
-template <int R, bool INV, typename T, int OFF, int LEN = 2>
+// First level when the upper half of the DFT input is zero: after the
+// bit-reversal each pair holds (x_m, x_{m+R/2} = 0), so both outputs are x_m.
+template <int R, typename T, int OFF, int I = 0>
+__device__ __forceinline__ void level_half(cx<T> *a)
+{
+    if constexpr (I < R) {
+        a[OFF + I + 1] = a[OFF + I];
+        level_half<R, T, OFF, I + 2>(a);
+    }
+}
+
+template <int R, bool INV, typename T, int OFF, bool HALF, int LEN = 2>
 __device__ __forceinline__ void levels(cx<T> *a)
 {
     if constexpr (LEN <= R) {
-        level<R, INV, T, OFF, LEN>(a);
-        levels<R, INV, T, OFF, LEN * 2>(a);
+        if constexpr (HALF && LEN == 2) level_half<R, T, OFF>(a);
+        else level<R, INV, T, OFF, LEN>(a);
+        levels<R, INV, T, OFF, HALF, LEN * 2>(a);
     }
 }
 
 // In-register DFT of length R on a[OFF .. OFF+R), natural order in and out
-// (radix-2 decimation in time).
-template <int R, bool INV, typename T, int OFF>
+// (radix-2 decimation in time).  HALF: inputs R/2 .. R-1 are known to be zero.
+template <int R, bool INV, typename T, int OFF, bool HALF = false>
 __device__ __forceinline__ void dft_reg(cx<T> *a)
 {
     bitrev_perm<R, T, OFF>(a);
-    levels<R, INV, T, OFF>(a);
+    levels<R, INV, T, OFF, HALF>(a);
 }
 
 // G lanes per line, E = N / G elements per lane, radices (forward order).
@@ -212,20 +224,23 @@ struct Smem {
     }
 };
 
-template <int N, bool INV, int s, typename T, int b = 0>
+template <int N, bool INV, int s, typename T, bool HALF, int b = 0>
 __device__ __forceinline__ void dft_all(cx<T> (&v)[Plan<N>::E])
 {
     constexpr int R = radix<N, INV>(s);
     if constexpr (b < Plan<N>::E / R) {
-        dft_reg<R, INV, T, b * R>(v);
-        dft_all<N, INV, s, T, b + 1>(v);
+        dft_reg<R, INV, T, b * R, HALF>(v);
+        dft_all<N, INV, s, T, HALF, b + 1>(v);
     }
 }
 
-// Stage s: twiddles (s > 0) and the DFTs, all in registers.
-template <int N, bool INV, int s, typename T>
+// Stage s: twiddles (s > 0) and the DFTs, all in registers.  HALF (stage 0
+// only): the input positions >= N/2 are zero, i.e. elements m >= R/2 of every
+// stage-0 butterfly (see in_lower_half).
+template <int N, bool INV, int s, typename T, bool HALF = false>
 __device__ __forceinline__ void stage_compute(cx<T> (&v)[Plan<N>::E], const cx<T> *tw, int j)
 {
+    static_assert(!HALF || s == 0, "zero upper half only holds for the first stage");
     constexpr int R = radix<N, INV>(s);
     constexpr int L = span<N, INV>(s);
     constexpr int STEP = N / (R * L);
@@ -241,7 +256,7 @@ __device__ __forceinline__ void stage_compute(cx<T> (&v)[Plan<N>::E], const cx<T
             }
         }
     }
-    dft_all<N, INV, s, T>(v);
+    dft_all<N, INV, s, T, HALF>(v);
 }
 
 // Move from the output layout of stage s to the input layout of stage s+1.
@@ -272,14 +287,15 @@ __device__ __forceinline__ void exchange(cx<T> (&v)[Plan<N>::E], cx<T> *buf, Sme
 
 // The whole transform: registers in (input layout of stage 0), registers out
 // (output layout of the last stage).  Every thread of the block must call it.
-template <int N, bool INV, bool LINE_FAST, typename T, int s = 0>
+// HALF: the caller left every element with in_lower_half(e) == false at zero.
+template <int N, bool INV, bool LINE_FAST, typename T, bool HALF = false, int s = 0>
 __device__ __forceinline__ void transform(cx<T> (&v)[Plan<N>::E], cx<T> *buf, const cx<T> *tw,
                                           Smem<N, LINE_FAST> sm, int l, int j)
 {
     if constexpr (s < Plan<N>::S) {
-        stage_compute<N, INV, s, T>(v, tw, j);
+        stage_compute<N, INV, s, T, HALF && s == 0>(v, tw, j);
         if constexpr (s + 1 < Plan<N>::S) exchange<N, INV, s, LINE_FAST, T>(v, buf, sm, l, j);
-        transform<N, INV, LINE_FAST, T, s + 1>(v, buf, tw, sm, l, j);
+        transform<N, INV, LINE_FAST, T, HALF, s + 1>(v, buf, tw, sm, l, j);
     }
 }
 

@@ -35,6 +35,13 @@ struct TileY {
     static constexpr int LS = sizeof(T) == 8 ? (G >= 64 ? 2 : LS32 / 2) : LS32;
     static constexpr int LSP = LS + 1;
     static constexpr int threads = LS * G;
+    // resident blocks per SM asked of the compiler (a register cap per thread:
+    // 48 / 64 for the single / double transform passes in FP32, twice that in FP64)
+    static constexpr int cap(int mode)
+    {
+        return (G == 1 || Plan<N>::E > 16 ? 128 : (mode == 1 ? 64 : 48) + (N >= 1024 ? 8 : 0)) * (sizeof(T) == 8 ? 2 : 1);
+    }
+    static constexpr int minb(int mode) { return 65536 / (threads * cap(mode)) > 0 ? 65536 / (threads * cap(mode)) : 1; }
 };
 template <int N, typename T>
 struct TileX {
@@ -97,7 +104,7 @@ __global__ void __launch_bounds__(TileX<N, T>::threads) k_x_fwd(Geom g, const T 
     }
     __syncthreads();  // twiddles
     SM sm{0};
-    fft::transform<N, false, false, T>(v, buf, tw, sm, l, j);
+    fft::transform<N, false, false, T, true>(v, buf, tw, sm, l, j);
 #pragma unroll
     for (int e = 0; e < E; e++) buf[sm.at(fft::out_pos<N, false>(e, j), l)] = v[e];
     __syncthreads();
@@ -117,13 +124,26 @@ __global__ void __launch_bounds__(TileX<N, T>::threads) k_x_fwd(Geom g, const T 
 }
 
 // y forward (MODE 0), z forward + spectral multiply + z inverse (MODE 1),
-// y inverse (MODE 2) over [c][plane][line][kx] arrays, LS consecutive kx per block.
+// y inverse (MODE 2) over [c][plane][line][kx] arrays.
 //   MODE 0: in [c][Es_z][Es_y][KX] -> out [c][Es_z][Ny][KX]
 //   MODE 1: in [c][Es_z][Ny][KX]   -> out [c][Et_z][Ny][KX]
 //   MODE 2: in [c][Et_z][Ny][KX]   -> out [c][Et_z][Et_y][KX]
+// Block tiling: the KX * planes lines of a component are numbered kx-fastest
+// (line i = p * KX + kx) and block b takes lines b LS .. b LS + LS - 1.
+// Consecutive lines are consecutive kx of one plane, so a block's rows are
+// coalesced (at most two contiguous segments, at a plane boundary), and only
+// the last block of a component holds padding lines.  KX = Nx/2 + 1 is the x
+// extent of the spectrum, independent of this pass's line length N.  (In the
+// z pass the [plane][line] offset of line i is i itself.)
+template <int MODE>
+__host__ __device__ __forceinline__ int line_planes(const Geom &g)
+{
+    return MODE == 0 ? g.Es[2] : (MODE == 1 ? g.N[1] : g.Et[2]);
+}
+
 template <int N, int MODE, typename T>
-__global__ void __launch_bounds__(TileY<N, T>::threads) k_line(Geom g, const cx<T> *__restrict__ in,
-                                                                cx<T> *__restrict__ out, const void *tw_g)
+__global__ void __launch_bounds__(TileY<N, T>::threads, TileY<N, T>::minb(MODE))
+    k_line(Geom g, const cx<T> *__restrict__ in, cx<T> *__restrict__ out, const void *tw_g)
 {
     using TL = TileY<N, T>;
     constexpr int E = Plan<N>::E;
@@ -133,66 +153,81 @@ __global__ void __launch_bounds__(TileY<N, T>::threads) k_line(Geom g, const cx<
     fft::load_twiddles<N, T>(tw, tw_g);
     const int KX = g.KX;
     const int l = threadIdx.x % TL::LS, j = threadIdx.x / TL::LS;
-    const int kx = blockIdx.x * TL::LS + l;
-    const bool ok = kx < KX;
-    const int p = blockIdx.y;
-    const int c = blockIdx.z;
+    const int i = blockIdx.x * TL::LS + l;  // line p * KX + kx
+    const bool ok = i < KX * line_planes<MODE>(g);
+    const int c = blockIdx.y;
     const int Ny = g.N[1];
+    const int Es1 = g.Es[1], Es2 = g.Es[2], Et1 = g.Et[1], Et2 = g.Et[2];
     SM sm{TL::LSP};
     cx<T> v[E];
-    constexpr bool INV0 = MODE == 2;  // first transform direction
-#pragma unroll
-    for (int e = 0; e < E; e++) {
-        v[e] = {(T)0, (T)0};
-        const int pos = fft::in_pos<N, INV0>(e, j);
-        if constexpr (MODE == 0) {
-            if (fft::in_lower_half<N, false>(e) && ok && pos < g.Es[1])
-                v[e] = in[(((size_t)c * g.Es[2] + p) * g.Es[1] + pos) * KX + kx];
-        } else if constexpr (MODE == 1) {
-            if (fft::in_lower_half<N, false>(e) && ok && pos < g.Es[2])
-                v[e] = in[(((size_t)c * g.Es[2] + pos) * Ny + p) * KX + kx];
+    {
+        // element pos of the line sits at ibase[pos * istride]
+        const cx<T> *ibase;
+        int istride;
+        if constexpr (MODE == 1) {
+            ibase = in + (size_t)c * Es2 * Ny * KX + i;
+            istride = Ny * KX;
         } else {
-            if (ok) v[e] = in[(((size_t)c * g.Et[2] + p) * Ny + pos) * KX + kx];
+            const int p = i / KX, kx = i - p * KX;
+            ibase = in + ((size_t)c * (MODE == 0 ? Es2 : Et2) + p) * (MODE == 0 ? Es1 : Ny) * KX + kx;
+            istride = KX;
+        }
+        constexpr bool INV0 = MODE == 2;  // first transform direction
+        const int ilim = MODE == 0 ? Es1 : (MODE == 1 ? Es2 : N);
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+            v[e] = {(T)0, (T)0};
+            const int pos = fft::in_pos<N, INV0>(e, j);
+            const bool live = MODE == 2 || fft::in_lower_half<N, false>(e);
+            if (live && ok && pos < ilim) v[e] = ibase[pos * istride];
         }
     }
     __syncthreads();  // twiddles
     if constexpr (MODE == 0) {
-        fft::transform<N, false, true, T>(v, buf, tw, sm, l, j);
+        fft::transform<N, false, true, T, true>(v, buf, tw, sm, l, j);
         if (ok) {
+            const int p = i / KX, kx = i - p * KX;
+            cx<T> *obase = out + (((size_t)c * Es2 + p) * N) * KX + kx;
 #pragma unroll
-            for (int e = 0; e < E; e++)
-                out[(((size_t)c * g.Es[2] + p) * N + fft::out_pos<N, false>(e, j)) * KX + kx] = v[e];
+            for (int e = 0; e < E; e++) obase[fft::out_pos<N, false>(e, j) * KX] = v[e];
         }
     } else if constexpr (MODE == 1) {
-        fft::transform<N, false, true, T>(v, buf, tw, sm, l, j);
-        const int kyf = p <= Ny / 2 ? p : Ny - p;
-        const T *krow = kh_of<T>(g) + (size_t)kyf * KX + (ok ? kx : 0);
-        const size_t kstride = (size_t)(Ny / 2 + 1) * KX;
-        const T mul = mul_of<T>(g);
+        fft::transform<N, false, true, T, true>(v, buf, tw, sm, l, j);
+        {
+            const int p = ok ? i / KX : 0, kx = ok ? i - p * KX : 0;
+            const int kyf = p <= Ny / 2 ? p : Ny - p;
+            const T *krow = kh_of<T>(g) + kyf * KX + kx;
+            const int kstride = (Ny / 2 + 1) * KX;
+            const T mul = mul_of<T>(g);
 #pragma unroll
-        for (int e = 0; e < E; e++) {
-            const int pos = fft::out_pos<N, false>(e, j);
-            const int kzf = pos <= N / 2 ? pos : N - pos;
-            const T w = mul * __ldg(krow + kzf * kstride);
-            v[e] = {v[e].x * w, v[e].y * w};
+            for (int e = 0; e < E; e++) {
+                const int pos = fft::out_pos<N, false>(e, j);
+                const int kzf = pos <= N / 2 ? pos : N - pos;
+                const T w = mul * __ldg(krow + kzf * kstride);
+                v[e] = {v[e].x * w, v[e].y * w};
+            }
         }
         fft::transform<N, true, true, T>(v, buf, tw, sm, l, j);
         if (ok) {
             const int dz = g.T0[2] - g.S0[2];
+            cx<T> *obase = out + (size_t)c * Et2 * Ny * KX + i;
+            const int ostride = Ny * KX;
 #pragma unroll
             for (int e = 0; e < E; e++) {
                 const int zt = wrap_mod(fft::out_pos<N, true>(e, j) - dz, N);
-                if (zt < g.Et[2]) out[(((size_t)c * g.Et[2] + zt) * Ny + p) * KX + kx] = v[e];
+                if (zt < Et2) obase[zt * ostride] = v[e];
             }
         }
     } else {
         fft::transform<N, true, true, T>(v, buf, tw, sm, l, j);
         if (ok) {
+            const int p = i / KX, kx = i - p * KX;
             const int dy = g.T0[1] - g.S0[1];
+            cx<T> *obase = out + (((size_t)c * Et2 + p) * Et1) * KX + kx;
 #pragma unroll
             for (int e = 0; e < E; e++) {
                 const int yt = wrap_mod(fft::out_pos<N, true>(e, j) - dy, N);
-                if (yt < g.Et[1]) out[(((size_t)c * g.Et[2] + p) * g.Et[1] + yt) * KX + kx] = v[e];
+                if (yt < Et1) obase[yt * KX] = v[e];
             }
         }
     }
@@ -274,8 +309,8 @@ template <int N, int MODE, typename T>
 lgf_status launch_line(const Geom &g, const cx<T> *in, cx<T> *out, cudaStream_t s)
 {
     using TL = TileY<N, T>;
-    int planes = MODE == 0 ? g.Es[2] : (MODE == 1 ? g.N[1] : g.Et[2]);
-    dim3 grid(ceil_div(g.KX, TL::LS), planes, g.ncomp);
+    const int planes = MODE == 0 ? g.Es[2] : (MODE == 1 ? g.N[1] : g.Et[2]);
+    dim3 grid(ceil_div(g.KX * planes, TL::LS), g.ncomp);
     k_line<N, MODE, T><<<grid, TL::threads, 0, s>>>(g, in, out, tw_table<T>());
     LGF_LAUNCH_CHECK(MODE == 0 ? "y_fwd" : (MODE == 1 ? "z_mid" : "y_inv"));
     return LGF_OK;

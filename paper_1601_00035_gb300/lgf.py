@@ -364,7 +364,7 @@ def required_max_offset(src_blocks: np.ndarray, dst_blocks: np.ndarray, B: int) 
         T0, T1 = t[:, a].min() * B, (t[:, a].max() + 1) * B - 1
         m = max(abs(T0 - S1), abs(T1 - S0))
         n = 16
-        while n < 2 * m + 2:
+        while n < max(2 * m + 2, 2 * (S1 - S0 + 1)):
             n *= 2
         need = max(need, n // 2 - 1)
     return int(need)

@@ -40,3 +40,10 @@ def test_required_max_offset():
     from paper_1601_00035_gb300 import lgf
     b = np.array([[0, 0, 0], [7, 7, 7]])
     assert lgf.required_max_offset(b, b, 16) == 127
+    # a target inside a long source: the offsets alone allow length 128, the
+    # source extent (96 points) needs 256 so that it fills at most half a line
+    s = np.array([[i, 0, 0] for i in range(6)])
+    t = np.array([[3, 0, 0]])
+    assert lgf.required_max_offset(s, t, 16) == 127
+    # far target: the offsets decide
+    assert lgf.required_max_offset(np.array([[0, 0, 0]]), np.array([[30, 0, 0]]), 16) == 511

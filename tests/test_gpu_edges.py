@@ -71,6 +71,26 @@ def test_far_target_length_1024(dst):
     assert rel_l2(out.reshape(-1)[sel], ref) < tol
 
 
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_wide_source_narrow_target(axis):
+    """Source six blocks long on one axis, target one block inside it: the
+    largest offset (63) alone would allow length 128, but the source extent (96)
+    must stay in the lower half of the line, so the plan takes 256 there."""
+    lgf = built()
+    B = 16
+    rng = np.random.default_rng(11 + axis)
+    src_c = np.zeros((6, 3), dtype=np.int32)
+    src_c[:, axis] = np.arange(6)
+    dst_c = np.zeros((1, 3), dtype=np.int32)
+    dst_c[0, axis] = 3
+    f = rng.standard_normal((6, 1, B, B, B))
+    out = _solve(lgf, B, src_c, dst_c, f)
+    K = lgf.required_max_offset(src_c, dst_c, B)
+    assert K == 127
+    ref = O.direct_conv(O.lgf_cube(K), inputs.block_points(src_c, B), f.reshape(-1), inputs.block_points(dst_c, B))
+    assert rel_l2(out.reshape(-1), ref) < 1e-6
+
+
 def test_argument_errors():
     lgf = built()
     t = lgf.Table(lgf.LAPLACE7, max_offset=31)
