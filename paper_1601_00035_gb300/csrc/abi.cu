@@ -385,6 +385,7 @@ static lgf_status plan_poisson(lgf_plan *p, const lgf_table *t, const lgf_solve_
         Geom &g = ps.g;
         std::memset(&g, 0, sizeof(g));
         g.B = d.B;
+        g.lB = d.B == 8 ? 3 : (d.B == 16 ? 4 : 5);
         g.ncomp = d.ncomp;
         ps.nsrc = d.n_src;
         ps.ndst = d.n_dst;

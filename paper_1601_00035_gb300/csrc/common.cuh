@@ -80,4 +80,30 @@ const double2 *twiddle_table_f64();  // device pointer, current device
 lgf_status ensure_twiddles();
 constexpr int TW_MAX = 1024;
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched by
+// launch_pdl may begin while its predecessor on the stream is still draining:
+// pdl_wait() blocks until that predecessor has completed and its writes are
+// visible, so every read of a predecessor's output and every global write
+// comes after it; pdl_trigger() lets the successor begin launching once every
+// block of this grid has started.  Without a programmatic dependency both
+// return at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 }  // namespace lgf

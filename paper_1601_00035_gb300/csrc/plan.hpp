@@ -14,6 +14,7 @@
 namespace lgf {
 struct Geom {
     int B, ncomp;
+    int lB;            // log2(B)
     int S0[3], Es[3];  // source bounding box: origin, extent (multiples of B)
     int T0[3], Et[3];  // target bounding box
     int N[3];          // zero-padded FFT length per axis

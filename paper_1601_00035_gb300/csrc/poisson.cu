@@ -48,6 +48,9 @@ struct TileX {
     static constexpr int G = Plan<N>::G;
     static constexpr int threads = G == 1 ? 64 : (sizeof(T) == 8 ? 128 : 256);
     static constexpr int LS = threads / G;
+    static constexpr int cap = (G == 1 || Plan<N>::E > 16 ? 128 : (N >= 1024 ? 80 : (N == 128 ? 64 : 48))) *
+                               (sizeof(T) == 8 ? 2 : 1);
+    static constexpr int minb = 65536 / (threads * cap) > 0 ? 65536 / (threads * cap) : 1;
 };
 
 // spectrum pointer and factor of the requested precision
@@ -60,16 +63,18 @@ __device__ __forceinline__ const double *kh_of<double>(const Geom &g) { return g
 template <typename T>
 __device__ __forceinline__ T mul_of(const Geom &g) { return sizeof(T) == 8 ? (T)g.mul64 : (T)g.mul; }
 
-__device__ __forceinline__ int wrap_mod(int v, int n)
+// v mod N in [0, N) for any int v (two's complement, N a power of two)
+template <int N>
+__device__ __forceinline__ int wrap_mod(int v)
 {
-    int r = v % n;
-    return r < 0 ? r + n : r;
+    static_assert((N & (N - 1)) == 0, "power of two");
+    return v & (N - 1);
 }
 
 // ---------------------------------------------------------------------------
 // x forward: gather two source rows per complex line from the block list, R2C.
 template <int N, typename T>
-__global__ void __launch_bounds__(TileX<N, T>::threads) k_x_fwd(Geom g, const T *__restrict__ src,
+__global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_fwd(Geom g, const T *__restrict__ src,
                                                                  cx<T> *__restrict__ out, const void *tw_g)
 {
     using TL = TileX<N, T>;
@@ -78,6 +83,8 @@ __global__ void __launch_bounds__(TileX<N, T>::threads) k_x_fwd(Geom g, const T 
     __shared__ cx<T> buf[TL::LS * SM::NP + 8];
     __shared__ cx<T> tw[N];
     fft::load_twiddles<N, T>(tw, tw_g);
+    pdl_trigger();
+    pdl_wait();  // the previous pass (or the producer of src) is complete
     const int c = blockIdx.y;
     const int j = threadIdx.x % TL::G, l = threadIdx.x / TL::G;
     const int nrows = g.Es[1] * g.Es[2];
@@ -85,8 +92,9 @@ __global__ void __launch_bounds__(TileX<N, T>::threads) k_x_fwd(Geom g, const T 
     const int B = g.B;
     const bool row_ok = r0 < nrows;
     const int z = row_ok ? r0 / g.Es[1] : 0, y = row_ok ? r0 - z * g.Es[1] : 0;
-    const int lut_row = ((z / B) * g.nbS[1] + y / B) * g.nbS[0];
-    const size_t in_blk = (size_t)(z % B) * B * B + (size_t)(y % B) * B;
+    const int lB = g.lB, mB = B - 1;
+    const int lut_row = ((z >> lB) * g.nbS[1] + (y >> lB)) * g.nbS[0];
+    const int in_blk = (((z & mB) << lB) + (y & mB)) << lB;
     cx<T> v[E];
 #pragma unroll
     for (int e = 0; e < E; e++) {
@@ -94,9 +102,9 @@ __global__ void __launch_bounds__(TileX<N, T>::threads) k_x_fwd(Geom g, const T 
         if (fft::in_lower_half<N, false>(e)) {
             const int pos = fft::in_pos<N, false>(e, j);
             if (row_ok && pos < g.Es[0]) {
-                const int blk = __ldg(g.src_lut + lut_row + pos / B);
+                const int blk = __ldg(g.src_lut + lut_row + (pos >> lB));
                 if (blk >= 0) {
-                    const T *p = src + (size_t)(blk * g.ncomp + c) * B * B * B + in_blk + (pos % B);
+                    const T *p = src + ((size_t)(blk * g.ncomp + c) << (3 * lB)) + in_blk + (pos & mB);
                     v[e] = {__ldg(p), __ldg(p + B)};
                 }
             }
@@ -151,6 +159,8 @@ __global__ void __launch_bounds__(TileY<N, T>::threads, TileY<N, T>::minb(MODE))
     __shared__ cx<T> buf[N * TL::LSP];
     __shared__ cx<T> tw[N];
     fft::load_twiddles<N, T>(tw, tw_g);
+    pdl_trigger();
+    pdl_wait();  // the previous pass (or the producer of src) is complete
     const int KX = g.KX;
     const int l = threadIdx.x % TL::LS, j = threadIdx.x / TL::LS;
     const int i = blockIdx.x * TL::LS + l;  // line p * KX + kx
@@ -214,7 +224,7 @@ __global__ void __launch_bounds__(TileY<N, T>::threads, TileY<N, T>::minb(MODE))
             const int ostride = Ny * KX;
 #pragma unroll
             for (int e = 0; e < E; e++) {
-                const int zt = wrap_mod(fft::out_pos<N, true>(e, j) - dz, N);
+                const int zt = wrap_mod<N>(fft::out_pos<N, true>(e, j) - dz);
                 if (zt < Et2) obase[zt * ostride] = v[e];
             }
         }
@@ -226,7 +236,7 @@ __global__ void __launch_bounds__(TileY<N, T>::threads, TileY<N, T>::minb(MODE))
             cx<T> *obase = out + (((size_t)c * Et2 + p) * Et1) * KX + kx;
 #pragma unroll
             for (int e = 0; e < E; e++) {
-                const int yt = wrap_mod(fft::out_pos<N, true>(e, j) - dy, N);
+                const int yt = wrap_mod<N>(fft::out_pos<N, true>(e, j) - dy);
                 if (yt < Et1) obase[yt * KX] = v[e];
             }
         }
@@ -236,7 +246,7 @@ __global__ void __launch_bounds__(TileY<N, T>::threads, TileY<N, T>::minb(MODE))
 // x inverse: two target rows per complex line (Z = A + i B with Hermitian
 // extension), C2R, scatter into the target block list.
 template <int N, typename T>
-__global__ void __launch_bounds__(TileX<N, T>::threads) k_x_inv(Geom g, const cx<T> *__restrict__ in,
+__global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_inv(Geom g, const cx<T> *__restrict__ in,
                                                                  T *__restrict__ dst, const void *tw_g)
 {
     using TL = TileX<N, T>;
@@ -245,6 +255,8 @@ __global__ void __launch_bounds__(TileX<N, T>::threads) k_x_inv(Geom g, const cx
     __shared__ cx<T> buf[TL::LS * SM::NP + 8];
     __shared__ cx<T> tw[N];
     fft::load_twiddles<N, T>(tw, tw_g);
+    pdl_trigger();
+    pdl_wait();  // the previous pass (or the producer of src) is complete
     constexpr int KX = N / 2 + 1;
     const int c = blockIdx.y;
     const int j = threadIdx.x % TL::G, l = threadIdx.x / TL::G;
@@ -275,16 +287,17 @@ __global__ void __launch_bounds__(TileX<N, T>::threads) k_x_inv(Geom g, const cx
     if (!row_ok) return;
     const int B = g.B;
     const int zt = r0 / g.Et[1], yt = r0 - zt * g.Et[1];
-    const int lut_row = ((zt / B) * g.nbT[1] + yt / B) * g.nbT[0];
-    const size_t out_blk = (size_t)(zt % B) * B * B + (size_t)(yt % B) * B;
+    const int lB = g.lB, mB = B - 1;
+    const int lut_row = ((zt >> lB) * g.nbT[1] + (yt >> lB)) * g.nbT[0];
+    const int out_blk = (((zt & mB) << lB) + (yt & mB)) << lB;
     const int dx0 = g.T0[0] - g.S0[0];
 #pragma unroll
     for (int e = 0; e < E; e++) {
-        const int xt = wrap_mod(fft::out_pos<N, true>(e, j) - dx0, N);
+        const int xt = wrap_mod<N>(fft::out_pos<N, true>(e, j) - dx0);
         if (xt < g.Et[0]) {
-            const int blk = __ldg(g.dst_lut + lut_row + xt / B);
+            const int blk = __ldg(g.dst_lut + lut_row + (xt >> lB));
             if (blk >= 0) {
-                T *p = dst + (size_t)(blk * g.ncomp + c) * B * B * B + out_blk + (xt % B);
+                T *p = dst + ((size_t)(blk * g.ncomp + c) << (3 * lB)) + out_blk + (xt & mB);
                 p[0] = v[e].x;
                 p[B] = v[e].y;
             }
@@ -301,8 +314,7 @@ lgf_status launch_x_fwd(const Geom &g, const T *src, cx<T> *out, cudaStream_t s)
     using TL = TileX<N, T>;
     const int nrows = g.Es[1] * g.Es[2];
     dim3 grid(ceil_div(nrows / 2, TL::LS), g.ncomp);
-    k_x_fwd<N, T><<<grid, TL::threads, 0, s>>>(g, src, out, tw_table<T>());
-    LGF_LAUNCH_CHECK("x_fwd");
+    LGF_CUDA_TRY(launch_pdl(k_x_fwd<N, T>, grid, dim3(TL::threads), s, g, src, out, tw_table<T>()));
     return LGF_OK;
 }
 template <int N, int MODE, typename T>
@@ -311,8 +323,7 @@ lgf_status launch_line(const Geom &g, const cx<T> *in, cx<T> *out, cudaStream_t 
     using TL = TileY<N, T>;
     const int planes = MODE == 0 ? g.Es[2] : (MODE == 1 ? g.N[1] : g.Et[2]);
     dim3 grid(ceil_div(g.KX * planes, TL::LS), g.ncomp);
-    k_line<N, MODE, T><<<grid, TL::threads, 0, s>>>(g, in, out, tw_table<T>());
-    LGF_LAUNCH_CHECK(MODE == 0 ? "y_fwd" : (MODE == 1 ? "z_mid" : "y_inv"));
+    LGF_CUDA_TRY(launch_pdl(k_line<N, MODE, T>, grid, dim3(TL::threads), s, g, in, out, tw_table<T>()));
     return LGF_OK;
 }
 template <int N, typename T>
@@ -321,8 +332,7 @@ lgf_status launch_x_inv(const Geom &g, const cx<T> *in, T *dst, cudaStream_t s)
     using TL = TileX<N, T>;
     const int nrows = g.Et[1] * g.Et[2];
     dim3 grid(ceil_div(nrows / 2, TL::LS), g.ncomp);
-    k_x_inv<N, T><<<grid, TL::threads, 0, s>>>(g, in, dst, tw_table<T>());
-    LGF_LAUNCH_CHECK("x_inv");
+    LGF_CUDA_TRY(launch_pdl(k_x_inv<N, T>, grid, dim3(TL::threads), s, g, in, dst, tw_table<T>()));
     return LGF_OK;
 }
 
