@@ -109,16 +109,49 @@ __device__ __forceinline__ void bitrev_perm(cx<T> *a)
     }
 }
 
+// One butterfly (u, v) -> (u + w v, u - w v) with w = w_len^k (conjugated for
+// the inverse), k and len compile-time.  Where w is not a power of -i the
+// multiply is folded into fused multiply-adds: with t the rotated v, u + h t
+// and u - h t are two FMAs (w = w_8 type), and for a general w the sum is
+// two chained FMAs per component and the difference 2 u - sum is one more.
+template <bool INV, typename T>
+__device__ __forceinline__ void butterfly(cx<T> &u, cx<T> &v, int k, int len)
+{
+    if (k == 0 || 4 * k == len) {
+        const cx<T> wv = twiddle_len<INV>(v, k, len);
+        const cx<T> a = u + wv, b = u - wv;
+        u = a;
+        v = b;
+        return;
+    }
+    if (8 * k == len || 8 * k == 3 * len) {
+        const T h = (T)0.70710678118654752440;
+        const T sg = (8 * k == len) ? (T)1 : (T)-1;
+        // w v = h t
+        const cx<T> t = INV ? cx<T>{sg * v.x - v.y, sg * v.y + v.x} : cx<T>{sg * v.x + v.y, sg * v.y - v.x};
+        const cx<T> a = {fma(h, t.x, u.x), fma(h, t.y, u.y)};
+        const cx<T> b = {fma(-h, t.x, u.x), fma(-h, t.y, u.y)};
+        u = a;
+        v = b;
+        return;
+    }
+    const cx<T> w = tw64<T>(k * (64 / len));
+    const T ws = INV ? -w.y : w.y;  // imaginary part of the applied twiddle
+    cx<T> a;
+    a.x = fma(-v.y, ws, fma(v.x, w.x, u.x));
+    a.y = fma(v.y, w.x, fma(v.x, ws, u.y));
+    const cx<T> b = {fma((T)2, u.x, -a.x), fma((T)2, u.y, -a.y)};
+    u = a;
+    v = b;
+}
+
 // Butterflies of one radix-2 level (span LEN) by template recursion over (I, K).
 template <int R, bool INV, typename T, int OFF, int LEN, int I = 0, int K = 0>
 __device__ __forceinline__ void level(cx<T> *a)
 {
     if constexpr (I < R) {
         if constexpr (K < LEN / 2) {
-            const cx<T> u = a[OFF + I + K];
-            const cx<T> v = twiddle_len<INV>(a[OFF + I + K + LEN / 2], K, LEN);
-            a[OFF + I + K] = u + v;
-            a[OFF + I + K + LEN / 2] = u - v;
+            butterfly<INV>(a[OFF + I + K], a[OFF + I + K + LEN / 2], K, LEN);
             level<R, INV, T, OFF, LEN, I, K + 1>(a);
         } else {
             level<R, INV, T, OFF, LEN, I + LEN, 0>(a);
@@ -210,6 +243,42 @@ __host__ __device__ constexpr int span(int s)
     return L;
 }
 
+// Twiddles of the stages s >= 1 in shared memory.  N <= 512: stage-major
+// tables; for direction INV, stage s (radix R, span L, STEP = N / (R L))
+// holds w_N^(m k STEP) at off(s) + m L + k (k < L, m < R), so a butterfly
+// finds its R twiddles at fixed offsets from its k, and lanes with
+// consecutive k read consecutive words.  Plans whose radices are not a
+// palindrome keep the inverse direction's table behind the forward one.
+// N = 1024: the N powers w_N^q (q < N), indexed m k STEP (shared-memory budget).
+template <int N>
+__host__ __device__ constexpr bool tw_stage_tables() { return N <= 512; }
+template <int N, bool INV>
+__host__ __device__ constexpr int tw_stage_off(int s)
+{
+    int off = 0;
+    for (int i = 1; i < s; i++) off += span<N, INV>(i) * radix<N, INV>(i);
+    return off;
+}
+template <int N, bool INV>
+__host__ __device__ constexpr int tw_dir_size() { return tw_stage_off<N, INV>(Plan<N>::S); }
+template <int N>
+__host__ __device__ constexpr bool tw_palindrome()
+{
+    for (int s = 0; s < Plan<N>::S; s++)
+        if (radix<N, false>(s) != radix<N, true>(s)) return false;
+    return true;
+}
+template <int N>
+__host__ __device__ constexpr int tw_base(bool inv) { return inv && !tw_palindrome<N>() ? tw_dir_size<N, false>() : 0; }
+// entries of the shared twiddle array
+template <int N>
+__host__ __device__ constexpr int tw_size()
+{
+    if (!tw_stage_tables<N>()) return N;
+    const int n = tw_dir_size<N, false>() + (tw_palindrome<N>() ? 0 : tw_dir_size<N, true>());
+    return n > 0 ? n : 1;
+}
+
 // Shared-memory addressing of element `pos` of line `l`:
 //   LINE_FAST (threads of a warp run across lines):  pos * LSP + l
 //   lane-fast (threads of a warp run along a line):   l * NP + pos + pos / 32
@@ -245,14 +314,25 @@ __device__ __forceinline__ void stage_compute(cx<T> (&v)[Plan<N>::E], const cx<T
     constexpr int L = span<N, INV>(s);
     constexpr int STEP = N / (R * L);
     constexpr int G = Plan<N>::G;
+    static_assert(G % L == 0 || L % G == 0, "lane/span layout");
     if constexpr (L > 1) {
 #pragma unroll
         for (int b = 0; b < Plan<N>::E / R; b++) {
-            const int k = (j + b * G) % L;
+            // k = (j + b G) mod L, with j < G
+            const int k = G % L == 0 ? j % L : j + (b * G) % L;
+            if constexpr (tw_stage_tables<N>()) {
+                const cx<T> *col = tw + tw_base<N>(INV) + tw_stage_off<N, INV>(s) + k;
 #pragma unroll
-            for (int m = 1; m < R; m++) {
-                const cx<T> w = tw[m * k * STEP];
-                v[b * R + m] = INV ? cmulc(v[b * R + m], w) : cmul(v[b * R + m], w);
+                for (int m = 1; m < R; m++) {
+                    const cx<T> w = col[m * L];
+                    v[b * R + m] = INV ? cmulc(v[b * R + m], w) : cmul(v[b * R + m], w);
+                }
+            } else {
+#pragma unroll
+                for (int m = 1; m < R; m++) {
+                    const cx<T> w = tw[m * k * STEP];
+                    v[b * R + m] = INV ? cmulc(v[b * R + m], w) : cmul(v[b * R + m], w);
+                }
             }
         }
     }
@@ -322,25 +402,42 @@ __host__ __device__ constexpr bool in_lower_half(int e)
     return (e % R) * (N / R) < N / 2;
 }
 
-// Load w_N^j (j < N) into shared memory from the 1024-entry global table of
-// the same precision (float2 for T = float, double2 for T = double).
+// Fill the shared twiddle array (tw_size<N>() entries) from the 1024-entry
+// global table of the same precision (float2 for T = float, double2 for double).
+template <typename T>
+__device__ __forceinline__ cx<T> tw_global_at(const void *tw_global, int idx)
+{
+    if constexpr (sizeof(T) == 8) {
+        const double2 w = __ldg((const double2 *)tw_global + idx);
+        return {w.x, w.y};
+    } else {
+        const float2 w = __ldg((const float2 *)tw_global + idx);
+        return {w.x, w.y};
+    }
+}
+template <int N, bool INV, typename T, int s = 1>
+__device__ __forceinline__ void load_dir(cx<T> *tw_s, const void *tw_global)
+{
+    if constexpr (s < Plan<N>::S) {
+        constexpr int SC = TW_MAX / N;
+        constexpr int R = radix<N, INV>(s), L = span<N, INV>(s), STEP = N / (R * L);
+        cx<T> *ts = tw_s + tw_base<N>(INV) + tw_stage_off<N, INV>(s);
+        for (int q = threadIdx.x; q < L * R; q += blockDim.x) {
+            const int m = q / L, k = q - m * L;
+            ts[q] = tw_global_at<T>(tw_global, (m * k * STEP * SC) & (TW_MAX - 1));
+        }
+        load_dir<N, INV, T, s + 1>(tw_s, tw_global);
+    }
+}
 template <int N, typename T>
 __device__ __forceinline__ void load_twiddles(cx<T> *tw_s, const void *tw_global)
 {
     static_assert(N <= TW_MAX, "N too large");
-    constexpr int STRIDE = TW_MAX / N;
-    if constexpr (sizeof(T) == 8) {
-        const double2 *g = (const double2 *)tw_global;
-        for (int j = threadIdx.x; j < N; j += blockDim.x) {
-            double2 w = __ldg(g + j * STRIDE);
-            tw_s[j] = {w.x, w.y};
-        }
+    if constexpr (tw_stage_tables<N>()) {
+        load_dir<N, false, T>(tw_s, tw_global);
+        if constexpr (!tw_palindrome<N>()) load_dir<N, true, T>(tw_s, tw_global);
     } else {
-        const float2 *g = (const float2 *)tw_global;
-        for (int j = threadIdx.x; j < N; j += blockDim.x) {
-            float2 w = __ldg(g + j * STRIDE);
-            tw_s[j] = {w.x, w.y};
-        }
+        for (int q = threadIdx.x; q < N; q += blockDim.x) tw_s[q] = tw_global_at<T>(tw_global, q * (TW_MAX / N));
     }
 }
 

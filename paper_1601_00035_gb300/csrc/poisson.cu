@@ -42,6 +42,10 @@ struct TileY {
         return (G == 1 || Plan<N>::E > 16 ? 128 : (mode == 1 ? 64 : 48) + (N >= 1024 ? 8 : 0)) * (sizeof(T) == 8 ? 2 : 1);
     }
     static constexpr int minb(int mode) { return 65536 / (threads * cap(mode)) > 0 ? 65536 / (threads * cap(mode)) : 1; }
+    // the z pass's spectrum columns fit beside the exchange buffer and twiddles
+    // in the 48 KB of static shared memory
+    static constexpr bool slab_fits = (size_t)N * LSP * sizeof(cx<T>) + fft::tw_size<N>() * sizeof(cx<T>) +
+                                          (size_t)(N / 2 + 1) * LS * sizeof(T) <= 48 * 1024;
 };
 template <int N, typename T>
 struct TileX {
@@ -80,21 +84,37 @@ __global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_f
     using TL = TileX<N, T>;
     constexpr int E = Plan<N>::E;
     using SM = fft::Smem<N, false>;
+    // block-list lookups of the lines' rows: the source extent is <= N/2 and
+    // B >= 8, so a row meets at most N/16 blocks
+    constexpr int NBX = N / 16;
     __shared__ cx<T> buf[TL::LS * SM::NP + 8];
-    __shared__ cx<T> tw[N];
+    __shared__ cx<T> tw[fft::tw_size<N>()];
+    __shared__ int lut_s[TL::LS * NBX];
     fft::load_twiddles<N, T>(tw, tw_g);
-    pdl_trigger();
-    pdl_wait();  // the previous pass (or the producer of src) is complete
     const int c = blockIdx.y;
     const int j = threadIdx.x % TL::G, l = threadIdx.x / TL::G;
     const int nrows = g.Es[1] * g.Es[2];
-    const int r0 = 2 * (blockIdx.x * TL::LS + l);
     const int B = g.B;
+    const int lB = g.lB, mB = B - 1;
+    // the lookup table is fixed at plan time: read it before waiting
+    for (int q = threadIdx.x; q < TL::LS * NBX; q += TL::threads) {
+        const int ll = q / NBX, xb = q - ll * NBX;
+        const int rr = 2 * (blockIdx.x * TL::LS + ll);
+        int b = -1;
+        if (rr < nrows && xb < g.nbS[0]) {
+            const int zz = rr / g.Es[1], yy = rr - zz * g.Es[1];
+            b = __ldg(g.src_lut + ((zz >> lB) * g.nbS[1] + (yy >> lB)) * g.nbS[0] + xb);
+        }
+        lut_s[q] = b;
+    }
+    pdl_trigger();
+    pdl_wait();  // the previous pass (or the producer of src) is complete
+    __syncthreads();  // twiddles, lookups
+    const int r0 = 2 * (blockIdx.x * TL::LS + l);
     const bool row_ok = r0 < nrows;
     const int z = row_ok ? r0 / g.Es[1] : 0, y = row_ok ? r0 - z * g.Es[1] : 0;
-    const int lB = g.lB, mB = B - 1;
-    const int lut_row = ((z >> lB) * g.nbS[1] + (y >> lB)) * g.nbS[0];
     const int in_blk = (((z & mB) << lB) + (y & mB)) << lB;
+    const int *lut = lut_s + l * NBX;
     cx<T> v[E];
 #pragma unroll
     for (int e = 0; e < E; e++) {
@@ -102,7 +122,7 @@ __global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_f
         if (fft::in_lower_half<N, false>(e)) {
             const int pos = fft::in_pos<N, false>(e, j);
             if (row_ok && pos < g.Es[0]) {
-                const int blk = __ldg(g.src_lut + lut_row + (pos >> lB));
+                const int blk = lut[pos >> lB];
                 if (blk >= 0) {
                     const T *p = src + ((size_t)(blk * g.ncomp + c) << (3 * lB)) + in_blk + (pos & mB);
                     v[e] = {__ldg(p), __ldg(p + B)};
@@ -110,7 +130,6 @@ __global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_f
             }
         }
     }
-    __syncthreads();  // twiddles
     SM sm{0};
     fft::transform<N, false, false, T, true>(v, buf, tw, sm, l, j);
 #pragma unroll
@@ -155,18 +174,37 @@ __global__ void __launch_bounds__(TileY<N, T>::threads, TileY<N, T>::minb(MODE))
 {
     using TL = TileY<N, T>;
     constexpr int E = Plan<N>::E;
+    constexpr int G = Plan<N>::G;
     using SM = fft::Smem<N, true>;
     __shared__ cx<T> buf[N * TL::LSP];
-    __shared__ cx<T> tw[N];
+    __shared__ cx<T> tw[fft::tw_size<N>()];
+    // z pass: this block's kernel-spectrum columns ks[kz][l] (kz <= N/2), scaled
+    constexpr int KZ = N / 2 + 1;
+    constexpr bool SLAB = MODE == 1 && TileY<N, T>::slab_fits;
+    __shared__ T ks[SLAB ? KZ * TL::LS : 1];
     fft::load_twiddles<N, T>(tw, tw_g);
-    pdl_trigger();
-    pdl_wait();  // the previous pass (or the producer of src) is complete
     const int KX = g.KX;
     const int l = threadIdx.x % TL::LS, j = threadIdx.x / TL::LS;
     const int i = blockIdx.x * TL::LS + l;  // line p * KX + kx
     const bool ok = i < KX * line_planes<MODE>(g);
     const int c = blockIdx.y;
     const int Ny = g.N[1];
+    pdl_trigger();
+    if constexpr (SLAB) {
+        // the spectrum is fixed at plan time, so it is read before waiting on
+        // the previous pass; thread (l, j) fetches kz = j, j + G, ... of line l
+        if (ok) {
+            const int p = i / KX, kx = i - p * KX;
+            const int kyf = p <= Ny / 2 ? p : Ny - p;
+            const int kstride = (Ny / 2 + 1) * KX;
+            const T *kcol = kh_of<T>(g) + kyf * KX + kx + j * kstride;
+            const T mul = mul_of<T>(g);
+#pragma unroll
+            for (int kz = j, q = 0; q < (KZ + G - 1) / G; q++, kz += G)
+                if (kz < KZ) ks[kz * TL::LS + l] = mul * __ldg(kcol + q * G * kstride);
+        }
+    }
+    pdl_wait();  // the previous pass (or the producer of src) is complete
     const int Es1 = g.Es[1], Es2 = g.Es[2], Et1 = g.Et[1], Et2 = g.Et[2];
     SM sm{TL::LSP};
     cx<T> v[E];
@@ -203,7 +241,18 @@ __global__ void __launch_bounds__(TileY<N, T>::threads, TileY<N, T>::minb(MODE))
         }
     } else if constexpr (MODE == 1) {
         fft::transform<N, false, true, T, true>(v, buf, tw, sm, l, j);
-        {
+        if constexpr (SLAB) {
+            // element e sits at kz position C + j, C = out_pos(e, 0) a multiple
+            // of G; its folded index is C + j below N/2 and N - C - j from N/2 on
+            const T *k_lo = ks + j * TL::LS + l;
+            const T *k_hi = ks + l - j * TL::LS;
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                const int C = fft::out_pos<N, false>(e, 0);
+                const T w = C < N / 2 ? k_lo[C * TL::LS] : k_hi[(N - C) * TL::LS];
+                v[e] = {v[e].x * w, v[e].y * w};
+            }
+        } else {
             const int p = ok ? i / KX : 0, kx = ok ? i - p * KX : 0;
             const int kyf = p <= Ny / 2 ? p : Ny - p;
             const T *krow = kh_of<T>(g) + kyf * KX + kx;
@@ -252,15 +301,31 @@ __global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_i
     using TL = TileX<N, T>;
     constexpr int E = Plan<N>::E;
     using SM = fft::Smem<N, false>;
+    // block-list lookups of the lines' rows: the target extent is < N and
+    // B >= 8, so a row meets at most N/8 blocks
+    constexpr int NBX = N / 8;
     __shared__ cx<T> buf[TL::LS * SM::NP + 8];
-    __shared__ cx<T> tw[N];
+    __shared__ cx<T> tw[fft::tw_size<N>()];
+    __shared__ int lut_d[TL::LS * NBX];
     fft::load_twiddles<N, T>(tw, tw_g);
-    pdl_trigger();
-    pdl_wait();  // the previous pass (or the producer of src) is complete
     constexpr int KX = N / 2 + 1;
     const int c = blockIdx.y;
     const int j = threadIdx.x % TL::G, l = threadIdx.x / TL::G;
     const int nrows = g.Et[1] * g.Et[2];
+    const int lB = g.lB;
+    // the lookup table is fixed at plan time: read it before waiting
+    for (int q = threadIdx.x; q < TL::LS * NBX; q += TL::threads) {
+        const int ll = q / NBX, xb = q - ll * NBX;
+        const int rr = 2 * (blockIdx.x * TL::LS + ll);
+        int b = -1;
+        if (rr < nrows && xb < g.nbT[0]) {
+            const int zz = rr / g.Et[1], yy = rr - zz * g.Et[1];
+            b = __ldg(g.dst_lut + ((zz >> lB) * g.nbT[1] + (yy >> lB)) * g.nbT[0] + xb);
+        }
+        lut_d[q] = b;
+    }
+    pdl_trigger();
+    pdl_wait();  // the previous pass (or the producer of src) is complete
     const int r0 = 2 * (blockIdx.x * TL::LS + l);
     const bool row_ok = r0 < nrows;
     const size_t row = ((size_t)c * nrows + (row_ok ? r0 : 0)) * KX;
@@ -287,15 +352,15 @@ __global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_i
     if (!row_ok) return;
     const int B = g.B;
     const int zt = r0 / g.Et[1], yt = r0 - zt * g.Et[1];
-    const int lB = g.lB, mB = B - 1;
-    const int lut_row = ((zt >> lB) * g.nbT[1] + (yt >> lB)) * g.nbT[0];
+    const int mB = B - 1;
+    const int *lut = lut_d + l * NBX;
     const int out_blk = (((zt & mB) << lB) + (yt & mB)) << lB;
     const int dx0 = g.T0[0] - g.S0[0];
 #pragma unroll
     for (int e = 0; e < E; e++) {
         const int xt = wrap_mod<N>(fft::out_pos<N, true>(e, j) - dx0);
         if (xt < g.Et[0]) {
-            const int blk = __ldg(g.dst_lut + lut_row + (xt >> lB));
+            const int blk = lut[xt >> lB];
             if (blk >= 0) {
                 T *p = dst + ((size_t)(blk * g.ncomp + c) << (3 * lB)) + out_blk + (xt & mB);
                 p[0] = v[e].x;
