@@ -142,6 +142,92 @@ __global__ void __launch_bounds__(B *B) k_op(const float *__restrict__ in, float
     }
 }
 
+// N~(f) with shared-memory planes (replaces the per-point neighbour fetches of
+// k_op<B, 4>): thread (x, y) walks z; plane z' of f = M(u + u_inf) with a
+// one-cell halo in x and y lives in a ring of three slots, and plane z' of
+// e = C f at in-plane positions -1 .. B-1 in a ring of two, so every stencil
+// value is one shared-memory read.  Same arithmetic as eq. opr_def_nonlin.
+template <int B>
+__global__ void __launch_bounds__(B *B) k_nonlinear(const float *__restrict__ in, float *__restrict__ out,
+                                                    const int *__restrict__ nbr27,
+                                                    const unsigned char *__restrict__ out_keep, float inv_dx,
+                                                    float coef, float u0, float u1, float u2)
+{
+    constexpr int H = B + 2;  // f plane edge (halo -1 .. B)
+    constexpr int HE = B + 1; // e plane edge (-1 .. B-1)
+    __shared__ int nb[27];
+    __shared__ float Fs[3][3][H * H];   // [slot][component][(y+1) H + (x+1)]
+    __shared__ float Es[2][3][HE * HE]; // [slot][component][(y+1) HE + (x+1)]
+    const int blk = blockIdx.x;
+    const int x = threadIdx.x % B, y = threadIdx.x / B;
+    const bool keep = out_keep == nullptr || out_keep[blk];
+    if (!keep) {
+        for (int z = 0; z < B; z++)
+#pragma unroll
+            for (int q = 0; q < 3; q++) out[((size_t)(blk * 3 + q) * B + z) * B * B + y * B + x] = 0.f;
+        return;
+    }
+    if (threadIdx.x < 27) nb[threadIdx.x] = nbr27[blk * 27 + threadIdx.x];
+    __syncthreads();
+    const float uinf[3] = {u0, u1, u2};
+    // f plane zp (-1 .. B) into its slot
+    auto load_f = [&](int zp) {
+        const int dz = zp < 0 ? -1 : (zp >= B ? 1 : 0);
+        const int lz = zp - dz * B;
+        float *dst = &Fs[(zp + 1) % 3][0][0];
+        for (int idx = threadIdx.x; idx < H * H; idx += B * B) {
+            const int hx = idx % H - 1, hy = idx / H - 1;
+            const int dx = hx < 0 ? -1 : (hx >= B ? 1 : 0);
+            const int dy = hy < 0 ? -1 : (hy >= B ? 1 : 0);
+            const int n = nb[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)];
+            const size_t base = n >= 0 ? ((size_t)n * 3 * B + lz) * B * B + (hy - dy * B) * B + (hx - dx * B) : 0;
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                dst[c * H * H + idx] = n >= 0 ? __ldg(in + base + (size_t)c * B * B * B) + uinf[c] : 0.f;
+        }
+    };
+    auto F = [&](int c, int px, int py, int pz) -> float { return Fs[(pz + 1) % 3][c][(py + 1) * H + (px + 1)]; };
+    // e plane zp (-1 .. B-1): e^c(p) = f^r(p) - f^r(p + e_s) + f^s(p + e_r) - f^s(p), (c, r, s) cyclic
+    auto make_e = [&](int zp) {
+        float *dst = &Es[(zp + 1) % 2][0][0];
+        for (int idx = threadIdx.x; idx < HE * HE; idx += B * B) {
+            const int px = idx % HE - 1, py = idx / HE - 1;
+            const float f0 = F(0, px, py, zp), f1 = F(1, px, py, zp), f2 = F(2, px, py, zp);
+            // c = 0 (r = y, s = z); c = 1 (r = z, s = x); c = 2 (r = x, s = y)
+            dst[0 * HE * HE + idx] = (f1 - F(1, px, py, zp + 1) + F(2, px, py + 1, zp) - f2) * inv_dx;
+            dst[1 * HE * HE + idx] = (f2 - F(2, px + 1, py, zp) + F(0, px, py, zp + 1) - f0) * inv_dx;
+            dst[2 * HE * HE + idx] = (f0 - F(0, px, py + 1, zp) + F(1, px + 1, py, zp) - f1) * inv_dx;
+        }
+    };
+    auto Ev = [&](int c, int px, int py, int pz) -> float { return Es[(pz + 1) % 2][c][(py + 1) * HE + (px + 1)]; };
+    load_f(-1);
+    load_f(0);
+    load_f(1);
+    __syncthreads();
+    make_e(-1);
+    for (int z = 0; z < B; z++) {
+        make_e(z);  // reads f planes z, z + 1
+        __syncthreads();
+        const int o[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};  // unit offsets e_q
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            const int r = (q + 1) % 3, s2 = (q + 2) % 3;
+            float v = 0.f;
+#pragma unroll
+            for (int m = -1; m <= 0; m++) {
+                const int ax = x + m * o[s2][0], ay = y + m * o[s2][1], az = z + m * o[s2][2];
+                v += Ev(r, ax, ay, az) * (F(s2, ax, ay, az) + F(s2, ax + o[q][0], ay + o[q][1], az + o[q][2]));
+                const int bx = x + m * o[r][0], by = y + m * o[r][1], bz = z + m * o[r][2];
+                v -= Ev(s2, bx, by, bz) * (F(r, bx, by, bz) + F(r, bx + o[q][0], by + o[q][1], bz + o[q][2]));
+            }
+            out[((size_t)(blk * 3 + q) * B + z) * B * B + y * B + x] = v * 0.25f * coef;
+        }
+        __syncthreads();  // plane z - 1 of f and of e are no longer read
+        if (z + 2 <= B) load_f(z + 2);
+        __syncthreads();
+    }
+}
+
 // out = sum_t c_t x_t over n floats (up to 4 terms; null x_t skipped).  out may
 // alias an input (each element is read and written by the same thread), so no
 // __restrict__ and no read-only-cache loads here.
@@ -186,7 +272,10 @@ lgf_status op_launch(int op, int B, int nblk, const int *d_nbr27, const unsigned
     const float u0 = uinf ? (float)uinf[0] : 0.f, u1 = uinf ? (float)uinf[1] : 0.f, u2 = uinf ? (float)uinf[2] : 0.f;
     const float cf = (float)coef;
 #define LGF_OPCASE(BB, OPV)                                                                                     \
-    k_op<BB, OPV><<<nblk, BB * BB, 0, s>>>(in, out, d_nbr27, d_keep, inv_dx, cf, u0, u1, u2);
+    if constexpr (OPV == 4)                                                                                     \
+        k_nonlinear<BB><<<nblk, BB * BB, 0, s>>>(in, out, d_nbr27, d_keep, inv_dx, cf, u0, u1, u2);          \
+    else                                                                                                        \
+        k_op<BB, OPV><<<nblk, BB * BB, 0, s>>>(in, out, d_nbr27, d_keep, inv_dx, cf, u0, u1, u2);
 #define LGF_OPSWITCH(BB)                                                                                        \
     switch (op) {                                                                                               \
         case 0: LGF_OPCASE(BB, 0) break;                                                                        \
