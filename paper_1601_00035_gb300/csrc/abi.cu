@@ -800,6 +800,22 @@ lgf_status lgf_conv_execute_host(lgf_plan *p, const float *const *src, float *co
     return LGF_OK;
 }
 
+}  // extern "C"
+
+namespace lgf {
+lgf_status ifactor_apply_io(lgf_plan *p, const IfIO &io, float *y, cudaStream_t s)
+{
+    if (!p || p->kind != LGF_KERNEL_IFACTOR) {
+        set_error("integrating factor: plan was not built from an integrating-factor table");
+        return LGF_ERR_STATE;
+    }
+    LGF_CHECK_ARG(io.x0 && y && io.x0 != y && io.x1 != y, "integrating factor: NULL or aliasing argument");
+    return ifactor_launch_ex(p->ifp, p->ncomp, p->table->h_taps32.data(), io, y, s, &p->prof);
+}
+}  // namespace lgf
+
+extern "C" {
+
 lgf_status ifactor_apply(lgf_plan *p, const float *x, float *y, void *stream)
 {
     clear_error();

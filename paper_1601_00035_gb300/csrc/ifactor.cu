@@ -32,9 +32,13 @@ struct Taps {
 
 // AXIS 2: z pass (thread per (x, y)), AXIS 1: y pass (thread per (x, z)),
 // AXIS 0: x pass (thread per (y, z), rows read as aligned float4 groups).
-template <int B, int RM, int AXIS>
+// EXTRA (optional linear combinations folded into the first and last pass):
+// the z pass reads ca in + cb in2 instead of in, the x pass writes r + add.
+template <int B, int RM, int AXIS, bool EXTRA>
 __global__ void __launch_bounds__(B *B) k_if_pass(const float *__restrict__ in, float *__restrict__ out,
-                                                  const int *__restrict__ nbr3, int ncomp, Taps<RM> t)
+                                                  const int *__restrict__ nbr3, int ncomp, Taps<RM> t,
+                                                  const float *__restrict__ in2, float ca, float cb,
+                                                  const float *__restrict__ add)
 {
     const int ob = blockIdx.x;  // output block
     const int c = blockIdx.y;
@@ -72,9 +76,15 @@ __global__ void __launch_bounds__(B *B) k_if_pass(const float *__restrict__ in, 
         }
     } else {
         const size_t cs = (size_t)B * B * B;
-        const float *pm = in + (size_t)(n_mid >= 0 ? n_mid : 0) * ncomp * cs + (size_t)c * cs;
-        const float *pl = in + (size_t)(n_lo >= 0 ? n_lo : 0) * ncomp * cs + (size_t)c * cs;
-        const float *ph = in + (size_t)(n_hi >= 0 ? n_hi : 0) * ncomp * cs + (size_t)c * cs;
+        const size_t om = (size_t)(n_mid >= 0 ? n_mid : 0) * ncomp * cs + (size_t)c * cs;
+        const size_t ol = (size_t)(n_lo >= 0 ? n_lo : 0) * ncomp * cs + (size_t)c * cs;
+        const size_t oh = (size_t)(n_hi >= 0 ? n_hi : 0) * ncomp * cs + (size_t)c * cs;
+        const float *pm = in + om, *pl = in + ol, *ph = in + oh;
+        // value at element offset q of the block at offset o: in, or ca in + cb in2
+        auto val_at = [&](const float *p, size_t o, int q) -> float {
+            if constexpr (EXTRA && AXIS == 2) return ca * __ldg(p + q) + cb * __ldg(in2 + o + q);
+            else return __ldg(p + q);
+        };
         // element (line index j along the axis) of this thread's line
         auto off = [&](int j) -> int {
             if constexpr (AXIS == 2) return j * B * B + b * B + a;  // (x=a, y=b, z=j)
@@ -85,11 +95,11 @@ __global__ void __launch_bounds__(B *B) k_if_pass(const float *__restrict__ in, 
             const int j = k - RM;
             float val = 0.f;
             if (j < 0) {
-                if (n_lo >= 0) val = __ldg(pl + off(j + B));
+                if (n_lo >= 0) val = val_at(pl, ol, off(j + B));
             } else if (j < B) {
-                if (n_mid >= 0) val = __ldg(pm + off(j));
+                if (n_mid >= 0) val = val_at(pm, om, off(j));
             } else {
-                if (n_hi >= 0) val = __ldg(ph + off(j - B));
+                if (n_hi >= 0) val = val_at(ph, oh, off(j - B));
             }
             v[k] = val;
         }
@@ -104,7 +114,19 @@ __global__ void __launch_bounds__(B *B) k_if_pass(const float *__restrict__ in, 
     }
     float *o = out + (size_t)(ob * ncomp + c) * B * B * B;
     if constexpr (AXIS == 0) {
-        float4 *p = reinterpret_cast<float4 *>(o + (size_t)b * B * B + a * B);
+        const size_t ro = (size_t)(ob * ncomp + c) * B * B * B + (size_t)b * B * B + a * B;
+        float4 *p = reinterpret_cast<float4 *>(out + ro);
+        if constexpr (EXTRA) {
+            const float4 *ad = reinterpret_cast<const float4 *>(add + ro);
+#pragma unroll
+            for (int q = 0; q < B / 4; q++) {
+                const float4 w = __ldg(ad + q);
+                r[4 * q] += w.x;
+                r[4 * q + 1] += w.y;
+                r[4 * q + 2] += w.z;
+                r[4 * q + 3] += w.w;
+            }
+        }
 #pragma unroll
         for (int q = 0; q < B / 4; q++) p[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
     } else {
@@ -117,22 +139,36 @@ __global__ void __launch_bounds__(B *B) k_if_pass(const float *__restrict__ in, 
 }
 
 template <int B, int RM>
-lgf_status launch3(const IfPlan &ip, int ncomp, const float *taps, const float *x, float *y, cudaStream_t s,
+lgf_status launch3(const IfPlan &ip, int ncomp, const float *taps, const IfIO &io, float *y, cudaStream_t s,
                    Profiler *prof)
 {
     Taps<RM> t;
     for (int i = 0; i <= RM; i++) t.g[i] = i <= ip.R ? taps[i] : 0.f;
     const bool P = prof && prof->on;
+    const bool lin = io.x1 != nullptr || io.c0 != 1.0;
+    const float ca = (float)io.c0, cb = (float)io.c1;
     if (P) prof->begin(s);
-    k_if_pass<B, RM, 2><<<dim3(ip.n1, ncomp), B * B, 0, s>>>(x, ip.y1, ip.nbz, ncomp, t);
+    if (lin)
+        k_if_pass<B, RM, 2, true><<<dim3(ip.n1, ncomp), B * B, 0, s>>>(io.x0, ip.y1, ip.nbz, ncomp, t,
+                                                                       io.x1 ? io.x1 : io.x0, ca, io.x1 ? cb : 0.f,
+                                                                       nullptr);
+    else
+        k_if_pass<B, RM, 2, false><<<dim3(ip.n1, ncomp), B * B, 0, s>>>(io.x0, ip.y1, ip.nbz, ncomp, t, nullptr, 1.f,
+                                                                        0.f, nullptr);
     LGF_LAUNCH_CHECK("if_z_pass");
     if (P) prof->end("if_z_pass", s);
     if (P) prof->begin(s);
-    k_if_pass<B, RM, 1><<<dim3(ip.n2, ncomp), B * B, 0, s>>>(ip.y1, ip.y2, ip.nby, ncomp, t);
+    k_if_pass<B, RM, 1, false><<<dim3(ip.n2, ncomp), B * B, 0, s>>>(ip.y1, ip.y2, ip.nby, ncomp, t, nullptr, 1.f, 0.f,
+                                                                    nullptr);
     LGF_LAUNCH_CHECK("if_y_pass");
     if (P) prof->end("if_y_pass", s);
     if (P) prof->begin(s);
-    k_if_pass<B, RM, 0><<<dim3(ip.n0, ncomp), B * B, 0, s>>>(ip.y2, y, ip.nbx, ncomp, t);
+    if (io.add)
+        k_if_pass<B, RM, 0, true><<<dim3(ip.n0, ncomp), B * B, 0, s>>>(ip.y2, y, ip.nbx, ncomp, t, nullptr, 1.f, 0.f,
+                                                                       io.add);
+    else
+        k_if_pass<B, RM, 0, false><<<dim3(ip.n0, ncomp), B * B, 0, s>>>(ip.y2, y, ip.nbx, ncomp, t, nullptr, 1.f, 0.f,
+                                                                        nullptr);
     LGF_LAUNCH_CHECK("if_x_pass");
     if (P) prof->end("if_x_pass", s);
     return LGF_OK;
@@ -142,6 +178,14 @@ lgf_status launch3(const IfPlan &ip, int ncomp, const float *taps, const float *
 
 lgf_status ifactor_launch(const IfPlan &ip, int ncomp, const float *h_taps, const float *x, float *y, cudaStream_t s,
                           Profiler *prof)
+{
+    IfIO io;
+    io.x0 = x;
+    return ifactor_launch_ex(ip, ncomp, h_taps, io, y, s, prof);
+}
+
+lgf_status ifactor_launch_ex(const IfPlan &ip, int ncomp, const float *h_taps, const IfIO &x, float *y, cudaStream_t s,
+                             Profiler *prof)
 {
     const int B = ip.B, R = ip.R;
     if (R > B || R > 16) {

@@ -228,6 +228,37 @@ __global__ void __launch_bounds__(B *B) k_nonlinear(const float *__restrict__ in
     }
 }
 
+// Projection tail fused with the gradient: gd_q(n) = (dhat(n + e_q) - dhat(n)) / dx
+// on faces (App. A, G), then out1 = rv - gd and optionally out2 = c2 (g - gd);
+// gd itself is never stored.  One block per block of the set, thread (x, y)
+// walks z with the scalar dhat plane and its +x/+y neighbours in registers
+// from neighbour-table reads.
+template <int B>
+__global__ void __launch_bounds__(B *B) k_grad_combine(const float *__restrict__ dhat, const float *__restrict__ rv,
+                                                       const float *__restrict__ g, float *__restrict__ out1,
+                                                       float *__restrict__ out2, const int *__restrict__ nbr27,
+                                                       float inv_dx, float c2)
+{
+    const int blk = blockIdx.x;
+    __shared__ int nb[27];
+    if (threadIdx.x < 27) nb[threadIdx.x] = nbr27[blk * 27 + threadIdx.x];
+    __syncthreads();
+    const int x = threadIdx.x % B, y = threadIdx.x / B;
+    Fetch<B> D{dhat, 1, nb};
+    float d0 = D(0, x, y, 0);
+    for (int z = 0; z < B; z++) {
+        const float dpx = D(0, x + 1, y, z), dpy = D(0, x, y + 1, z), dpz = D(0, x, y, z + 1);
+        const float gq[3] = {(dpx - d0) * inv_dx, (dpy - d0) * inv_dx, (dpz - d0) * inv_dx};
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            const size_t o = ((size_t)(blk * 3 + q) * B + z) * B * B + y * B + x;
+            out1[o] = __ldg(rv + o) - gq[q];
+            if (out2) out2[o] = c2 * (__ldg(g + o) - gq[q]);
+        }
+        d0 = dpz;
+    }
+}
+
 // out = sum_t c_t x_t over n floats (up to 4 terms; null x_t skipped).  out may
 // alias an input (each element is read and written by the same thread), so no
 // __restrict__ and no read-only-cache loads here.
@@ -310,6 +341,22 @@ lgf_status lincomb_launch(float *out, int64_t n, const float *x0, double c0, con
     const int blocks = (int)std::min<int64_t>((n / 4 + threads - 1) / threads, 152 * 16);
     k_lincomb<<<blocks, threads, 0, s>>>(out, n, x0, (float)c0, x1, (float)c1, x2, (float)c2, x3, (float)c3);
     LGF_LAUNCH_CHECK("lincomb");
+    return LGF_OK;
+}
+
+lgf_status grad_combine_launch(int B, int nblk, const int *d_nbr27, const float *dhat, const float *rv, const float *g,
+                               float *out1, float *out2, double c2, double dx, cudaStream_t s)
+{
+    const float inv_dx = (float)(1.0 / dx);
+    if (B == 8)
+        k_grad_combine<8><<<nblk, 64, 0, s>>>(dhat, rv, g, out1, out2, d_nbr27, inv_dx, (float)c2);
+    else if (B == 16)
+        k_grad_combine<16><<<nblk, 256, 0, s>>>(dhat, rv, g, out1, out2, d_nbr27, inv_dx, (float)c2);
+    else {
+        set_error("operators support B in {8, 16} (got %d)", B);
+        return LGF_ERR_ARG;
+    }
+    LGF_LAUNCH_CHECK("grad_combine");
     return LGF_OK;
 }
 

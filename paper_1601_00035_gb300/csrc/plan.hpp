@@ -100,6 +100,22 @@ struct IfPlan {
 };
 lgf_status ifactor_launch(const IfPlan &ip, int ncomp, const float *h_taps, const float *x, float *y, cudaStream_t s,
                           Profiler *prof = nullptr);
+// y = H(c0 x0 + c1 x1) + add (x1, add optional; c0 x0 alone when x1 is null):
+// the linear combination is read by the first pass, add joins in the last
+struct IfIO {
+    const float *x0 = nullptr;
+    double c0 = 1.0;
+    const float *x1 = nullptr;
+    double c1 = 0.0;
+    const float *add = nullptr;
+};
+lgf_status ifactor_launch_ex(const IfPlan &ip, int ncomp, const float *h_taps, const IfIO &x, float *y, cudaStream_t s,
+                             Profiler *prof = nullptr);
+}  // namespace lgf
+struct lgf_plan;
+namespace lgf {
+// y = H(c0 x0 + c1 x1) + add on an integrating-factor plan (abi.cu)
+lgf_status ifactor_apply_io(lgf_plan *p, const IfIO &io, float *y, cudaStream_t s);
 
 // local operators (ops.cu): op 0 curl, 1 curl^T, 2 G^T, 3 G, 4 nonlinear
 lgf_status op_launch(int op, int B, int nblk, const int *d_nbr27, const unsigned char *d_keep, const float *in,
@@ -107,6 +123,10 @@ lgf_status op_launch(int op, int B, int nblk, const int *d_nbr27, const unsigned
 lgf_status lincomb_launch(float *out, int64_t n, const float *x0, double c0, const float *x1, double c1,
                           const float *x2, double c2, const float *x3, double c3, cudaStream_t s);
 lgf_status gather_launch(const float *in, float *out, const int *d_idx, int n, int block_floats, cudaStream_t s);
+// projection tail of a stage: with gd = G dhat (cells -> faces),
+// out1 = rv - gd and, when out2 != nullptr, out2 = c2 (g - gd)
+lgf_status grad_combine_launch(int B, int nblk, const int *d_nbr27, const float *dhat, const float *rv, const float *g,
+                               float *out1, float *out2, double c2, double dx, cudaStream_t s);
 
 // one IF-HERK step on a block set (rk.cu)
 struct RkPlan {

@@ -73,9 +73,11 @@ lgf_status timed(Profiler &pr, const char *name, cudaStream_t s, F &&f)
     return st;
 }
 
-lgf_status rk_project(RkPlan *r, Profiler &pr, const float *rv, float *gd, cudaStream_t s)
+// Projection of a stage: with gd = G d^, d^ = -M^xsoln L^{-1} M^supp G^T M^xsoln r,
+// writes out1 = r - gd and (out2 != nullptr) out2 = c2 (g - gd).
+lgf_status rk_project(RkPlan *r, Profiler &pr, const float *rv, const float *g, float *out1, float *out2, double c2,
+                      cudaStream_t s)
 {
-    // gd = G d^, d^ = -M^xsoln L^{-1} M^supp G^T M^xsoln r
     float *sx = r->work + 8 * r->vec;  // G^T r on xsoln cells
     float *ss = sx + r->scal_x;        // restricted to supp
     const int B3 = r->B * r->B * r->B;
@@ -84,7 +86,9 @@ lgf_status rk_project(RkPlan *r, Profiler &pr, const float *rv, float *gd, cudaS
     const float *srcs[1] = {ss};
     float *dsts[1] = {sx};  // d^ overwrites G^T r on xsoln
     LGF_TRY(lgf_conv_execute(r->poisson, srcs, dsts, s));
-    LGF_TRY(timed(pr, "op_grad", s, [&] { return op_launch(3, r->B, r->n_x, r->d_nbr27, nullptr, sx, gd, r->dx, 1.0, nullptr, s); }));
+    LGF_TRY(timed(pr, "grad_combine", s, [&] {
+        return grad_combine_launch(r->B, r->n_x, r->d_nbr27, sx, rv, g, out1, out2, c2, r->dx, s);
+    }));
     return LGF_OK;
 }
 
@@ -187,7 +191,9 @@ lgf_status lgf_rk_plan(const lgf_rk_desc *d, void *stream, lgf_plan **out)
         for (int a = 0; a < 3; a++) {
             const long m = std::max(std::labs((long)tlo[a] * B - ((long)shi[a] * B + B - 1)),
                                     std::labs(((long)thi[a] * B + B - 1) - (long)slo[a] * B));
-            const int n = poisson_pick_n((int)std::min<long>(2 * m + 2, 1 << 20));
+            // the Poisson plan's length rule: max(2 m + 2, 2 E_s)
+            const long len = std::max<long>(2 * m + 2, 2L * (shi[a] - slo[a] + 1) * B);
+            const int n = poisson_pick_n((int)std::min<long>(len, 1 << 20));
             need = std::max(need, n / 2 - 1);
         }
         return need;
@@ -279,9 +285,8 @@ lgf_status lgf_rk_step(lgf_plan *p, const float *u_in, float *u_out, const doubl
     const double a11 = 0.5, a21 = r3 / 3.0, a22 = (3.0 - r3) / 3.0;
     const double a31 = (3.0 + r3) / 6.0, a32 = -r3 / 3.0, a33 = (3.0 + r3) / 6.0;
     const size_t V = r->vec;
-    float *g = r->work, *rv = g + V, *w11 = rv + V, *w22 = w11 + V, *t1 = w22 + V, *t2 = t1 + V, *u1 = t2 + V,
+    float *g = r->work, *rv = g + V, *w11 = rv + V, *w22 = w11 + V, *t1 = w22 + V, *u1 = t1 + 2 * V,
           *u2 = u1 + V;
-    float *gd = t2;  // reused
     const int B = r->B;
     const float *u0 = u_in;
     Profiler &pr = p->prof;
@@ -289,37 +294,36 @@ lgf_status lgf_rk_step(lgf_plan *p, const float *u_in, float *u_out, const doubl
         return timed(pr, "op_nonlinear", s,
                      [&] { return op_launch(4, B, r->n_x, r->d_nbr27, r->d_soln_keep, u, g, r->dx, -a * dt, uinf, s); });
     };
-    auto H = [&](const float *x, float *y) { return ifactor_apply(r->ifp, x, y, s); };
+    // y = H(x0 + c1 x1) + add, the combinations folded into the integrating factor's passes
+    auto H = [&](const float *x, float *y, const float *x1 = nullptr, double c1 = 0.0, const float *add = nullptr) {
+        IfIO io;
+        io.x0 = x;
+        io.x1 = x1;
+        io.c1 = c1;
+        io.add = add;
+        return ifactor_apply_io(r->ifp, io, y, s);
+    };
     auto LC = [&](float *o, const float *x0, double c0, const float *x1 = nullptr, double c1 = 0,
                   const float *x2 = nullptr, double c2 = 0, const float *x3 = nullptr, double c3 = 0) {
         return timed(pr, "lincomb", s, [&] { return lincomb_launch(o, (int64_t)V, x0, c0, x1, c1, x2, c2, x3, c3, s); });
     };
-    auto project = [&](const float *rvv, float *gdd) { return rk_project(r, pr, rvv, gdd, s); };
+    // project(r, w, c): t = r - G d^ (the projected stage value) and w = c (g - G d^)
+    auto project = [&](const float *rvv, float *t, float *w, double c) { return rk_project(r, pr, rvv, g, t, w, c, s); };
     // stage 1
     LGF_TRY(NL(u0, a11));
     LGF_TRY(LC(rv, u0, 1.0, g, 1.0));
-    LGF_TRY(project(rv, gd));
-    LGF_TRY(LC(t1, rv, 1.0, gd, -1.0));
+    LGF_TRY(project(rv, t1, w11, 1.0 / (a11 * dt)));
     LGF_TRY(H(t1, u1));
-    LGF_TRY(LC(w11, g, 1.0 / (a11 * dt), gd, -1.0 / (a11 * dt)));
-    // stage 2
+    // stage 2: rv = H(u0 + dt a21 w11) + g
     LGF_TRY(NL(u1, a22));
-    LGF_TRY(LC(t1, u0, 1.0, w11, dt * a21));
-    LGF_TRY(H(t1, rv));
-    LGF_TRY(LC(rv, rv, 1.0, g, 1.0));
-    LGF_TRY(project(rv, gd));
-    LGF_TRY(LC(t1, rv, 1.0, gd, -1.0));
+    LGF_TRY(H(u0, rv, w11, dt * a21, g));
+    LGF_TRY(project(rv, t1, w22, 1.0 / (a22 * dt)));
     LGF_TRY(H(t1, u2));
-    LGF_TRY(LC(w22, g, 1.0 / (a22 * dt), gd, -1.0 / (a22 * dt)));
-    // stage 3 (H^3 = I)
+    // stage 3 (H^3 = I): rv = H(H(u0 + dt a31 w11) + dt a32 w22) + g
     LGF_TRY(NL(u2, a33));
-    LGF_TRY(LC(t1, u0, 1.0, w11, dt * a31));
-    LGF_TRY(H(t1, u1));  // u1 no longer needed: holds H(u0 + dt a31 w11)
-    LGF_TRY(LC(t1, u1, 1.0, w22, dt * a32));
-    LGF_TRY(H(t1, rv));
-    LGF_TRY(LC(rv, rv, 1.0, g, 1.0));
-    LGF_TRY(project(rv, gd));
-    LGF_TRY(LC(u_out, rv, 1.0, gd, -1.0));
+    LGF_TRY(H(u0, u1, w11, dt * a31));  // u1 no longer needed
+    LGF_TRY(H(u1, rv, w22, dt * a32, g));
+    LGF_TRY(project(rv, u_out, nullptr, 0.0));
     return LGF_OK;
 }
 
