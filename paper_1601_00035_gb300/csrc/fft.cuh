@@ -219,8 +219,8 @@ struct Plan<256> {
 };
 template <>
 struct Plan<512> {
-    static constexpr int G = 64, E = 8, S = 3;
-    static constexpr int R[3] = {8, 8, 8};
+    static constexpr int G = 16, E = 32, S = 2;
+    static constexpr int R[2] = {16, 32};
 };
 template <>
 struct Plan<1024> {

@@ -28,11 +28,19 @@ using fft::Plan;
 // Lines per block: y/z passes run LS consecutive kx lines (line-fast thread
 // mapping, coalesced rows of kx); x passes run whole rows (lane-fast mapping).
 // (FP64 tiles are half as wide so that the static shared memory stays < 48 KB.)
+// largest power-of-two line count <= want whose exchange buffer and twiddles fit in 44 KB
+template <int N, typename T>
+constexpr int lines_fit(int want, int pad)
+{
+    int ls = want;
+    while (ls > 1 && (size_t)N * (ls + pad) * sizeof(cx<T>) + fft::tw_size<N>() * sizeof(cx<T>) > 44 * 1024) ls /= 2;
+    return ls;
+}
 template <int N, typename T>
 struct TileY {
     static constexpr int G = Plan<N>::G;
     static constexpr int LS32 = G == 1 ? 64 : (G >= 64 ? (N >= 1024 ? 4 : 8) : (G == 8 ? 32 : 16));
-    static constexpr int LS = sizeof(T) == 8 ? (G >= 64 ? 2 : LS32 / 2) : LS32;
+    static constexpr int LS = lines_fit<N, T>(sizeof(T) == 8 ? (G >= 64 ? 2 : LS32 / 2) : LS32, 1);
     static constexpr int LSP = LS + 1;
     static constexpr int threads = LS * G;
     // resident blocks per SM asked of the compiler (a register cap per thread:
@@ -50,8 +58,8 @@ struct TileY {
 template <int N, typename T>
 struct TileX {
     static constexpr int G = Plan<N>::G;
-    static constexpr int threads = G == 1 ? 64 : (sizeof(T) == 8 ? 128 : 256);
-    static constexpr int LS = threads / G;
+    static constexpr int LS = G == 1 ? 64 : lines_fit<N, T>((sizeof(T) == 8 ? 128 : 256) / G, 0);
+    static constexpr int threads = LS * G;
     static constexpr int cap = (G == 1 || Plan<N>::E > 16 ? 128 : (N >= 1024 ? 80 : (N == 128 ? 64 : 48))) *
                                (sizeof(T) == 8 ? 2 : 1);
     static constexpr int minb = 65536 / (threads * cap) > 0 ? 65536 / (threads * cap) : 1;

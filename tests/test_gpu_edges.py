@@ -1,8 +1,8 @@
 """Edge cases of the Poisson path: every FFT length class, single blocks,
 far-apart source and target sets (FFT length 1024), and argument errors.
 
-Lengths 16 and 32 run one thread per line; 64..256 two-stage transforms;
-512 and 1024 three-stage transforms.  Far offsets use the oracle's per-point
+Lengths 16 and 32 run one thread per line; 64..512 two-stage transforms
+(512 with 32 elements per lane); 1024 a three-stage transform.  Far offsets use the oracle's per-point
 LGF evaluation (same Bessel-integral quadrature as its tables)."""
 import numpy as np
 import pytest
@@ -89,6 +89,33 @@ def test_wide_source_narrow_target(axis):
     assert K == 127
     ref = O.direct_conv(O.lgf_cube(K), inputs.block_points(src_c, B), f.reshape(-1), inputs.block_points(dst_c, B))
     assert rel_l2(out.reshape(-1), ref) < 1e-6
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_length_512(precision):
+    """Targets 15 blocks away along x (FFT length 512) and 7 along y (256), in
+    FP32 and FP64; sampled against the per-point direct sum."""
+    lgf = built()
+    B = 16
+    rng = np.random.default_rng(21)
+    src_c = np.array([[0, 0, 0]], dtype=np.int32)
+    dst_c = np.array([[15, 0, 0], [0, 7, 0], [1, 1, 0]], dtype=np.int32)
+    f = rng.standard_normal((1, 1, B, B, B))
+    K = lgf.required_max_offset(src_c, dst_c, B)
+    assert K == 255
+    table = lgf.Table(lgf.LAPLACE7, max_offset=K)
+    plan = lgf.Plan(table, [lgf.Solve(B, 1, src_c, dst_c)], precision=precision)
+    dt = torch.float64 if precision else torch.float32
+    d_src = torch.from_numpy(f).to(dt).cuda()
+    d_dst = torch.zeros((len(dst_c), 1, B, B, B), dtype=dt, device="cuda")
+    (plan.execute_f64 if precision else plan.execute)([d_src], [d_dst])
+    out = d_dst.cpu().numpy().reshape(-1)
+    pts = inputs.block_points(dst_c, B)
+    sel = rng.choice(len(pts), 96, replace=False)
+    ref = _reference(f, src_c, dst_c, B, pts[sel])
+    near = abs(O.lgf_value((0, 0, 0))) * np.sqrt(np.mean(f ** 2))
+    scale = max(1.0, near / np.sqrt(np.mean(ref ** 2)))
+    assert rel_l2(out[sel], ref) < (1e-12 if precision else 1e-6) * scale
 
 
 def test_argument_errors():
