@@ -58,6 +58,25 @@ def workload():
     return f, src_c, dst_c, cfg
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value of x over the ranks of the default process group (x itself
+    without one); the whole-job time is the slowest rank's."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank_step: float, steps: int, world: int, seconds: float) -> float:
+    """Whole-job throughput in millions of units per second: every rank
+    processes the same per-step work (replicas, weak scaling) and the job ends
+    with the slowest rank."""
+    return units_per_rank_step * steps * world / seconds / 1e6
+
+
 def rank_info():
     r = int(os.environ.get("RANK", "0"))
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -272,9 +291,7 @@ def bench_gpu(args):
     plan.set_profiling(0)
     kt = plan.kernel_times()
     if dist:
-        t = torch.tensor([dev_ms], device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        dev_ms = float(t.item())
+        dev_ms = max_over_ranks(dev_ms, device="cuda")
         tdist.barrier()
     torch.cuda.synchronize()
     clocks = clock_summary(sampler) if r == 0 else None
@@ -290,17 +307,15 @@ def bench_gpu(args):
         plan.execute_host([h_src], [h_dst])
     e2e_s = time.perf_counter() - t0
     if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, device="cuda")
 
     if r != 0:
         if dist:
             tdist.destroy_process_group()
         return 0
 
-    value = pts_per_step * args.steps * ws / (dev_ms / 1e3) / 1e6
-    e2e_value = pts_per_step * e2e_steps * ws / e2e_s / 1e6
+    value = job_rate(pts_per_step, args.steps, ws, dev_ms / 1e3)
+    e2e_value = job_rate(pts_per_step, e2e_steps, ws, e2e_s)
     # roofline of the dominant kernel
     pb = pass_bytes(geom)
     dom = max(kt, key=lambda k: kt[k][1])
