@@ -85,6 +85,26 @@ def test_sparse_ragged_blocks(seed):
         assert rel_linf(got, ref) < TOL_LINF, c
 
 
+def test_block_edge_32():
+    """B = 32: four sparse source blocks, eight target blocks (one shared), two
+    components; sampled outputs against the direct sum."""
+    lgf = built()
+    rng = np.random.default_rng(32)
+    B = 32
+    src_c = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 1], [-1, 0, 1]], dtype=np.int32)
+    dst_c = np.array([[x, y, z] for z in range(0, 2) for y in range(0, 2) for x in range(-1, 1)], dtype=np.int32)
+    f = rng.standard_normal((len(src_c), 2, B, B, B))
+    _, _, _, out = _run(lgf, [lgf.Solve(B, 2, src_c, dst_c, dx=2.0, scale=0.5)], [f])
+    pts_all = inputs.block_points(dst_c, B)
+    sel = rng.choice(len(pts_all), 4096, replace=False)
+    K = lgf.required_max_offset(src_c, dst_c, B)
+    for c in range(2):
+        ref = oracle_poisson_blocks(f, src_c, B, pts_all[sel], K, comp=c, scale=0.5, dx=2.0)
+        got = out[0][:, c].reshape(-1)[sel]
+        assert rel_l2(got, ref) < TOL_L2, c
+        assert rel_linf(got, ref) < TOL_LINF, c
+
+
 def test_multi_solve_and_graph_bitwise():
     """Several solves in one plan; the graph path and the host-buffer path give
     bitwise the same result as the plain launch sequence."""
