@@ -208,12 +208,15 @@ typedef struct {
     int n_soln;                  /* number of D_soln (= D_supp) blocks */
     const int32_t *soln_blocks;  /* [n_soln][3] block coordinates (host) */
     double dx, dt, re;           /* grid spacing, time step, Reynolds number: alpha = dt / (dx^2 re) */
-    int scheme;                  /* 0 = Scheme A */
+    int scheme;                  /* tableau of eq. ifherk_schemes: 0 = Scheme A, 1 = Scheme B, 2 = Scheme C */
     int reserved[3];             /* must be zero */
 } lgf_rk_desc;
 
-/* Builds the LGF and integrating-factor tables, a scalar Poisson plan
- * D_supp -> D_xsoln and an E(alpha/2) plan on D_xsoln, and all workspaces.
+/* Builds the LGF table, a scalar Poisson plan D_supp -> D_xsoln, the
+ * integrating-factor plans H^i = E((c~_i - c~_{i-1}) alpha) on D_xsoln of the
+ * scheme's shifted nodes (Sec. 3.2; c~_0 = c_1: A: E(a/2), E(a/2), I;
+ * B: E(a/3), E(2a/3), I; C: E(8a/15), E(2a/15), E(a/3)), and all workspaces.
+ * LGF_ERR_ARG if an integrating-factor radius exceeds min(B, 16).
  * Synchronises `stream`.  The result is used only with the lgf_rk_* and
  * lgf_op_apply calls (and destroyed with lgf_plan_destroy). */
 lgf_status lgf_rk_plan(const lgf_rk_desc *d, void *stream, lgf_plan **out);
@@ -223,7 +226,8 @@ int lgf_rk_block_count(const lgf_plan *p, int which);
 lgf_status lgf_rk_blocks(const lgf_plan *p, int which, int32_t *coords, int n);
 /* u_out = IF-HERK(u_in) over one step, freestream uinf (host, 3 doubles, constant over the step);
  * u_in and u_out device buffers [n_xsoln][3][B^3], must not alias.  Three scalar Poisson solves,
- * five integrating-factor applications, three nonlinear terms.  Asynchronous; no allocation. */
+ * five integrating-factor applications (six for Scheme C, whose H^3 is not the identity), three
+ * nonlinear terms.  Asynchronous; no allocation. */
 lgf_status lgf_rk_step(lgf_plan *p, const float *u_in, float *u_out, const double uinf[3], void *stream);
 /* One App. A operator on the D_xsoln block set (zero outside it):
  *   op 0: e = C f (faces -> edges)      op 1: f = C^T e (edges -> faces)

@@ -28,7 +28,8 @@ __all__ = [
     "lib", "gauss_legendre", "bessel_scaled", "lgf_octant", "lgf_cube", "lgf_value",
     "octant_size", "asymptotic_G", "ifactor_taps", "ifactor_radius", "direct_conv",
     "direct_conv_box", "ifactor_direct", "shift", "op_G", "op_Gt", "op_C", "op_Ct", "op_D",
-    "op_Dbar", "op_L", "op_N", "residual_L", "WATSON_W", "num_threads", "SCHEME_A", "shifted_tableau",
+    "op_Dbar", "op_L", "op_N", "residual_L", "WATSON_W", "num_threads", "SCHEME_A", "SCHEME_B", "SCHEME_C",
+    "SCHEMES", "shifted_tableau",
     "block_mask", "ifactor_masked", "poisson_masked", "if_herk_step", "lgf_points",
 ]
 
@@ -304,6 +305,22 @@ SCHEME_A = {
     "b": np.array([(3 + math.sqrt(3)) / 6, -math.sqrt(3) / 3, (3 + math.sqrt(3)) / 6]),
     "c": np.array([0.0, 0.5, 1.0]),
 }
+# Schemes B and C of eq. ifherk_schemes (Sec. 3.2)
+SCHEME_B = {
+    "A": np.array([[0.0, 0.0, 0.0],
+                   [1.0 / 3.0, 0.0, 0.0],
+                   [-1.0, 2.0, 0.0]]),
+    "b": np.array([0.0, 0.75, 0.25]),
+    "c": np.array([0.0, 1.0 / 3.0, 1.0]),
+}
+SCHEME_C = {
+    "A": np.array([[0.0, 0.0, 0.0],
+                   [8.0 / 15.0, 0.0, 0.0],
+                   [0.25, 5.0 / 12.0, 0.0]]),
+    "b": np.array([0.25, 0.0, 0.75]),
+    "c": np.array([0.0, 8.0 / 15.0, 2.0 / 3.0]),
+}
+SCHEMES = {"A": SCHEME_A, "B": SCHEME_B, "C": SCHEME_C}
 
 
 def shifted_tableau(tab=SCHEME_A):

@@ -856,7 +856,8 @@ lgf_status lgf_plan_set_profiling(lgf_plan *p, int enable)
     p->prof.on = enable != 0;
     if (p->rk) {  // an RK plan also times the kernels of its Poisson and IF sub-plans
         LGF_TRY(lgf_plan_set_profiling(p->rk->poisson, enable));
-        LGF_TRY(lgf_plan_set_profiling(p->rk->ifp, enable));
+        for (int i = 0; i < 3; i++)
+            if (p->rk->if_owned[i]) LGF_TRY(lgf_plan_set_profiling(p->rk->ifp[i], enable));
     }
     return LGF_OK;
 }
@@ -866,7 +867,10 @@ static lgf_status merge_sub_profiles(lgf_plan *p)
 {
     LGF_TRY(p->prof.collect());
     if (!p->rk) return LGF_OK;
-    for (lgf_plan *sub : {p->rk->poisson, p->rk->ifp}) {
+    std::vector<lgf_plan *> subs = {p->rk->poisson};
+    for (int i = 0; i < 3; i++)
+        if (p->rk->if_owned[i]) subs.push_back(p->rk->ifp[i]);
+    for (lgf_plan *sub : subs) {
         LGF_TRY(sub->prof.collect());
         for (auto &r : sub->prof.recs) {
             const int k = p->prof.rec_of(r.name.c_str());

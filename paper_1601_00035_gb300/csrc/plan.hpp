@@ -133,8 +133,16 @@ struct RkPlan {
     int B = 0, n_soln = 0, n_x = 0;
     double dx = 0, dt = 0, re = 0, alpha = 0;
     std::vector<int32_t> xsoln;  // [n_x][3]; the first n_soln blocks are D_soln = D_supp
-    lgf_table *lgf_table = nullptr, *if_table = nullptr;
-    lgf_plan *poisson = nullptr, *ifp = nullptr;
+    lgf_table *lgf_table = nullptr;
+    // H^i = E((c~_i - c~_{i-1}) alpha), i = 1..3: tables and plans (nullptr where the
+    // exponent is zero, H^i = identity; a stage whose exponent equals an earlier one
+    // shares that plan and owns nothing)
+    struct lgf_table *if_table[3] = {nullptr, nullptr, nullptr};
+    lgf_plan *ifp[3] = {nullptr, nullptr, nullptr};
+    bool if_owned[3] = {false, false, false};
+    int scheme = 0;
+    double at[4][4] = {};  // shifted tableau a~_{i,j}, 1-based
+    lgf_plan *poisson = nullptr;
     int *d_nbr27 = nullptr;
     unsigned char *d_soln_keep = nullptr;
     int *d_supp_idx = nullptr;

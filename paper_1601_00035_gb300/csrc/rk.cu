@@ -1,23 +1,26 @@
 // One step of the IF-HERK scheme on the finite block set (Sec. 3.2 algorithm,
-// Sec. 3.3 eq. proj_final, Sec. 5 xIF-HERK), Scheme A of eq. ifherk_schemes.
+// Sec. 3.3 eq. proj_final, Sec. 5 xIF-HERK) with Scheme A, B or C of
+// eq. ifherk_schemes.
 //
 // Domains (Sec. 4.2): D_soln = D_supp (Sec. 6) = the caller's block list,
 // D_xsoln = D_soln dilated by N_b = 1 block (eq. def_xsoln).  Fields live on
 // D_xsoln: face velocity u [n_x][3][B^3]; the pressure-like d^ on cells [n_x][1][B^3].
 //
-// Scheme A has c~ = (1/2, 1, 1) with c~_0 = c_1 = 0, so H^1 = H^2 = E(alpha/2),
-// H^3 = I, alpha = dt / (dx^2 Re).  Carrying the q and w recursions through
-// the integrating factors (E(a) E(b) = E(a + b) and the linearity of E) gives
-// the same step with five integrating-factor applications:
+// Shifted tableau (eq. herk_shift): a~_{i,j} = a_{i+1,j} (i < 3), b_j (i = 3);
+// c~_i = c_{i+1} (i < 3), c~_3 = 1, and c~_0 = c_1 = 0 (the first stage starts at
+// t_k).  H^i = E((c~_i - c~_{i-1}) alpha), alpha = dt / (dx^2 Re): Scheme A
+// E(a/2), E(a/2), I; Scheme B E(a/3), E(2a/3), I; Scheme C E(8a/15), E(2a/15), E(a/3).
+// Carrying the q and w recursions through the integrating factors (linearity of
+// E) gives the step with at most six integrating-factor applications:
 //   stage 1:  g1 = -a~11 dt M^soln N~(M(u0 + u_inf));  r1 = u0 + g1
-//             gd1 = G d^1, d^1 = -L^{-1} M^supp G^T r1;  u1 = H(r1 - gd1)
+//             gd1 = G d^1, d^1 = -L^{-1} M^supp G^T r1;  u1 = H1(r1 - gd1)
 //             w11 = (g1 - gd1) / (a~11 dt)
-//   stage 2:  g2 = -a~22 dt M^soln N~(M(u1 + u_inf));  r2 = H(u0 + dt a~21 w11) + g2
-//             gd2 = G d^2;  u2 = H(r2 - gd2);  w22 = (g2 - gd2) / (a~22 dt)
+//   stage 2:  g2 = -a~22 dt M^soln N~(M(u1 + u_inf));  r2 = H1(u0 + dt a~21 w11) + g2
+//             gd2 = G d^2;  u2 = H2(r2 - gd2);  w22 = (g2 - gd2) / (a~22 dt)
 //   stage 3:  g3 = -a~33 dt M^soln N~(M(u2 + u_inf))
-//             r3 = H(H(u0 + dt a~31 w11) + dt a~32 w22) + g3
-//             gd3 = G d^3;  u_{k+1} = r3 - gd3
-// (H = M^xsoln E(alpha/2) M^xsoln).  The sign of g follows eq. ifherk_g.
+//             r3 = H2(H1(u0 + dt a~31 w11) + dt a~32 w22) + g3
+//             gd3 = G d^3;  u_{k+1} = H3(r3 - gd3)
+// (Hi = M^xsoln H^i M^xsoln).  The sign of g follows eq. ifherk_g.
 // The oracle runs the paper's form (explicit q and w recursions) instead, so
 // the parity test also checks this rearrangement.
 #include <algorithm>
@@ -53,9 +56,12 @@ void free_rk(RkPlan *r)
 {
     if (!r) return;
     lgf_plan_destroy(r->poisson);
-    lgf_plan_destroy(r->ifp);
+    for (int i = 0; i < 3; i++)
+        if (r->if_owned[i]) {
+            lgf_plan_destroy(r->ifp[i]);
+            lgf_table_destroy(r->if_table[i]);
+        }
     lgf_table_destroy(r->lgf_table);
-    lgf_table_destroy(r->if_table);
     cudaFree(r->d_nbr27);
     cudaFree(r->d_soln_keep);
     cudaFree(r->d_supp_idx);
@@ -106,7 +112,8 @@ lgf_status lgf_rk_plan(const lgf_rk_desc *d, void *stream, lgf_plan **out)
     LGF_CHECK_ARG(d->B == 8 || d->B == 16, "lgf_rk_plan: B=%d not in {8,16}", d->B);
     LGF_CHECK_ARG(d->n_soln >= 1 && d->soln_blocks, "lgf_rk_plan: empty soln block list");
     LGF_CHECK_ARG(d->dx > 0 && d->dt > 0 && d->re > 0, "lgf_rk_plan: dx, dt, re must be positive");
-    LGF_CHECK_ARG(d->scheme == 0, "lgf_rk_plan: only Scheme A (0) is implemented");
+    LGF_CHECK_ARG(d->scheme >= 0 && d->scheme <= 2, "lgf_rk_plan: scheme %d not in {0 (A), 1 (B), 2 (C)}",
+                  d->scheme);
     for (int i = 0; i < 3; i++) LGF_CHECK_ARG(d->reserved[i] == 0, "lgf_rk_plan: reserved fields must be zero");
     cudaStream_t s = (cudaStream_t)stream;
     const int B = d->B;
@@ -210,15 +217,61 @@ lgf_status lgf_rk_plan(const lgf_rk_desc *d, void *stream, lgf_plan **out)
     pd.dx = d->dx;
     pd.scale = -1.0;
     if ((st = lgf_conv_plan(r->lgf_table, &pd, 1, nullptr, stream, &r->poisson)) != LGF_OK) return fail(st);
-    // integrating factor E(alpha/2) on D_xsoln, three components
-    if ((st = lgf_table_build(LGF_KERNEL_IFACTOR, 0.5 * r->alpha, 0, stream, &r->if_table)) != LGF_OK) return fail(st);
-    lgf_solve_desc id = pd;
-    id.ncomp = 3;
-    id.n_src = nx;
-    id.src_blocks = xs.data();
-    id.n_dst = 0;
-    id.dst_blocks = nullptr;
-    if ((st = lgf_conv_plan(r->if_table, &id, 1, nullptr, stream, &r->ifp)) != LGF_OK) return fail(st);
+    // shifted tableau of the scheme (eq. ifherk_schemes, eq. herk_shift)
+    {
+        const double r3 = std::sqrt(3.0);
+        double A[3][3] = {}, b[3] = {}, c[3] = {};
+        if (d->scheme == 0) {
+            A[1][0] = 0.5;
+            A[2][0] = r3 / 3.0;
+            A[2][1] = (3.0 - r3) / 3.0;
+            b[0] = (3.0 + r3) / 6.0;
+            b[1] = -r3 / 3.0;
+            b[2] = (3.0 + r3) / 6.0;
+        } else if (d->scheme == 1) {
+            A[1][0] = 1.0 / 3.0;
+            A[2][0] = -1.0;
+            A[2][1] = 2.0;
+            b[1] = 0.75;
+            b[2] = 0.25;
+        } else {
+            A[1][0] = 8.0 / 15.0;
+            A[2][0] = 0.25;
+            A[2][1] = 5.0 / 12.0;
+            b[0] = 0.25;
+            b[2] = 0.75;
+        }
+        for (int i = 0; i < 3; i++) c[i] = A[i][0] + A[i][1] + A[i][2];
+        r->scheme = d->scheme;
+        for (int i = 1; i <= 3; i++)
+            for (int j = 1; j <= i; j++) r->at[i][j] = i < 3 ? A[i][j - 1] : b[j - 1];
+        const double ct[4] = {c[0], c[1], c[2], 1.0};  // c~_0 = c_1, c~_i = c_{i+1}, c~_3 = 1
+        // integrating factors on D_xsoln, three components
+        lgf_solve_desc id = pd;
+        id.ncomp = 3;
+        id.n_src = nx;
+        id.src_blocks = xs.data();
+        id.n_dst = 0;
+        id.dst_blocks = nullptr;
+        double expo[3];
+        for (int i = 0; i < 3; i++) {
+            expo[i] = (ct[i + 1] - ct[i]) * r->alpha;
+            if (expo[i] <= 0.0) continue;  // identity
+            bool shared = false;
+            for (int k = 0; k < i; k++)
+                if (r->ifp[k] && std::fabs(expo[k] - expo[i]) <= 1e-15 * expo[i]) {
+                    r->ifp[i] = r->ifp[k];
+                    r->if_table[i] = r->if_table[k];
+                    shared = true;
+                    break;
+                }
+            if (shared) continue;
+            r->if_owned[i] = true;
+            if ((st = lgf_table_build(LGF_KERNEL_IFACTOR, expo[i], 0, stream, &r->if_table[i])) != LGF_OK)
+                return fail(st);
+            if ((st = lgf_conv_plan(r->if_table[i], &id, 1, nullptr, stream, &r->ifp[i])) != LGF_OK) return fail(st);
+        }
+    }
     // workspaces: vector fields g, r, w11, w22, t1, t2, u1, u2 ; scalars s_supp, dhat
     const size_t B3 = (size_t)B * B * B;
     r->vec = (size_t)nx * 3 * B3;
@@ -280,10 +333,8 @@ lgf_status lgf_rk_step(lgf_plan *p, const float *u_in, float *u_out, const doubl
     RkPlan *r = p->rk;
     cudaStream_t s = (cudaStream_t)stream;
     const double dt = r->dt;
-    // shifted Scheme A coefficients (eq. herk_shift)
-    const double r3 = std::sqrt(3.0);
-    const double a11 = 0.5, a21 = r3 / 3.0, a22 = (3.0 - r3) / 3.0;
-    const double a31 = (3.0 + r3) / 6.0, a32 = -r3 / 3.0, a33 = (3.0 + r3) / 6.0;
+    const double a11 = r->at[1][1], a21 = r->at[2][1], a22 = r->at[2][2];
+    const double a31 = r->at[3][1], a32 = r->at[3][2], a33 = r->at[3][3];
     const size_t V = r->vec;
     float *g = r->work, *rv = g + V, *w11 = rv + V, *w22 = w11 + V, *t1 = w22 + V, *u1 = t1 + 2 * V,
           *u2 = u1 + V;
@@ -294,36 +345,47 @@ lgf_status lgf_rk_step(lgf_plan *p, const float *u_in, float *u_out, const doubl
         return timed(pr, "op_nonlinear", s,
                      [&] { return op_launch(4, B, r->n_x, r->d_nbr27, r->d_soln_keep, u, g, r->dx, -a * dt, uinf, s); });
     };
-    // y = H(x0 + c1 x1) + add, the combinations folded into the integrating factor's passes
-    auto H = [&](const float *x, float *y, const float *x1 = nullptr, double c1 = 0.0, const float *add = nullptr) {
+    // y = Hk(x0 + c1 x1) + add, the combinations folded into the integrating factor's
+    // passes; an identity Hk is one linear combination
+    auto H = [&](int k, const float *x, float *y, const float *x1 = nullptr, double c1 = 0.0,
+                 const float *add = nullptr) -> lgf_status {
+        if (!r->ifp[k - 1])
+            return timed(pr, "lincomb", s, [&] {
+                return lincomb_launch(y, (int64_t)V, x, 1.0, x1, x1 ? c1 : 0.0, add, add ? 1.0 : 0.0, nullptr, 0.0, s);
+            });
         IfIO io;
         io.x0 = x;
         io.x1 = x1;
         io.c1 = c1;
         io.add = add;
-        return ifactor_apply_io(r->ifp, io, y, s);
+        return ifactor_apply_io(r->ifp[k - 1], io, y, s);
     };
     auto LC = [&](float *o, const float *x0, double c0, const float *x1 = nullptr, double c1 = 0,
                   const float *x2 = nullptr, double c2 = 0, const float *x3 = nullptr, double c3 = 0) {
         return timed(pr, "lincomb", s, [&] { return lincomb_launch(o, (int64_t)V, x0, c0, x1, c1, x2, c2, x3, c3, s); });
     };
-    // project(r, w, c): t = r - G d^ (the projected stage value) and w = c (g - G d^)
+    // project(r, t, w, c): t = r - G d^ (the projected stage value) and w = c (g - G d^)
     auto project = [&](const float *rvv, float *t, float *w, double c) { return rk_project(r, pr, rvv, g, t, w, c, s); };
     // stage 1
     LGF_TRY(NL(u0, a11));
     LGF_TRY(LC(rv, u0, 1.0, g, 1.0));
     LGF_TRY(project(rv, t1, w11, 1.0 / (a11 * dt)));
-    LGF_TRY(H(t1, u1));
-    // stage 2: rv = H(u0 + dt a21 w11) + g
+    LGF_TRY(H(1, t1, u1));
+    // stage 2: r2 = H1(u0 + dt a21 w11) + g2
     LGF_TRY(NL(u1, a22));
-    LGF_TRY(H(u0, rv, w11, dt * a21, g));
+    LGF_TRY(H(1, u0, rv, w11, dt * a21, g));
     LGF_TRY(project(rv, t1, w22, 1.0 / (a22 * dt)));
-    LGF_TRY(H(t1, u2));
-    // stage 3 (H^3 = I): rv = H(H(u0 + dt a31 w11) + dt a32 w22) + g
+    LGF_TRY(H(2, t1, u2));
+    // stage 3: r3 = H2(H1(u0 + dt a31 w11) + dt a32 w22) + g3
     LGF_TRY(NL(u2, a33));
-    LGF_TRY(H(u0, u1, w11, dt * a31));  // u1 no longer needed
-    LGF_TRY(H(u1, rv, w22, dt * a32, g));
-    LGF_TRY(project(rv, u_out, nullptr, 0.0));
+    LGF_TRY(H(1, u0, u1, w11, dt * a31));  // u1 no longer needed
+    LGF_TRY(H(2, u1, rv, w22, dt * a32, g));
+    if (r->ifp[2]) {
+        LGF_TRY(project(rv, t1, nullptr, 0.0));
+        LGF_TRY(H(3, t1, u_out));
+    } else {
+        LGF_TRY(project(rv, u_out, nullptr, 0.0));
+    }
     return LGF_OK;
 }
 

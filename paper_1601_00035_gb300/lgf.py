@@ -292,16 +292,19 @@ class Plan:
 OP_CURL, OP_CURL_T, OP_DIV_T, OP_GRAD, OP_NONLINEAR = 0, 1, 2, 3, 4
 
 
-class RKPlan:
-    """One IF-HERK (Scheme A) step on a block set (lgf_rk_plan / lgf_rk_step)."""
+SCHEME_A, SCHEME_B, SCHEME_C = 0, 1, 2
 
-    def __init__(self, B: int, soln_blocks, dx: float, dt: float, re: float, stream=None):
+
+class RKPlan:
+    """One IF-HERK step (Scheme A, B or C) on a block set (lgf_rk_plan / lgf_rk_step)."""
+
+    def __init__(self, B: int, soln_blocks, dx: float, dt: float, re: float, stream=None, scheme: int = SCHEME_A):
         L = load()
         self._soln = np.ascontiguousarray(soln_blocks, dtype=np.int32).reshape(-1, 3)
         d = _RkDesc()
         d.B, d.n_soln = int(B), len(self._soln)
         d.soln_blocks = self._soln.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
-        d.dx, d.dt, d.re, d.scheme = float(dx), float(dt), float(re), 0
+        d.dx, d.dt, d.re, d.scheme = float(dx), float(dt), float(re), int(scheme)
         h = ctypes.c_void_p()
         _check(L.lgf_rk_plan(ctypes.byref(d), _stream(stream), ctypes.byref(h)))
         self._h = h

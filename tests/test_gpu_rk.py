@@ -1,7 +1,8 @@
 """GPU parity of the stage local operators (App. A) and of one IF-HERK step
-(Scheme A, Sec. 3.2-3.3, xIF-HERK masks of Sec. 5) against the FP64 oracle.
+(Schemes A, B and C of eq. ifherk_schemes, Sec. 3.2-3.3, xIF-HERK masks of
+Sec. 5) against the FP64 oracle.
 
-The GPU step uses a rearranged form with five integrating-factor applications;
+The GPU step uses a rearranged form with five (C: six) integrating-factor applications;
 the oracle runs the paper's q/w recursions, so this also checks the
 rearrangement.  Tolerances: operators relative L2 <= 1e-6; the step (three
 FP32 Poisson solves, five integrating factors, three nonlinear terms)
@@ -18,8 +19,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def _plan(lgf, cs, dt, re):
-    rk = lgf.RKPlan(cs["B"], cs["soln"], cs["dx"], dt, re)
+def _plan(lgf, cs, dt, re, scheme=0):
+    rk = lgf.RKPlan(cs["B"], cs["soln"], cs["dx"], dt, re, scheme=scheme)
     xs = rk.blocks(0)
     assert set(map(tuple, xs.tolist())) == set(map(tuple, cs["xsoln"].tolist()))
     return rk, xs
@@ -51,15 +52,17 @@ def test_local_operators():
         assert rel_l2(got, refm) < 1e-6, (op, rel_l2(got, refm))
 
 
-@pytest.mark.parametrize("uinf", [(0.0, 0.0, 0.0), (0.05, -0.02, 0.1)])
-def test_if_herk_step_matches_oracle(uinf):
+@pytest.mark.parametrize("scheme,uinf", [("A", (0.0, 0.0, 0.0)), ("A", (0.05, -0.02, 0.1)),
+                                         ("B", (0.05, -0.02, 0.1)), ("C", (0.05, -0.02, 0.1))])
+def test_if_herk_step_matches_oracle(scheme, uinf):
     lgf = built()
     cs = small_case(B=8, amp=3.0)
     B, n, org, dx = cs["B"], cs["n"], cs["origin"], cs["dx"]
     dt, re = 0.5, 10.0
-    rk, xs = _plan(lgf, cs, dt, re)
+    rk, xs = _plan(lgf, cs, dt, re, scheme="ABC".index(scheme))
     u0 = cs["u0"]
-    ref = O.if_herk_step(u0, dt, re, dx, uinf, cs["masks"], O.lgf_cube(64), nonlinear=True)
+    ref = O.if_herk_step(u0, dt, re, dx, uinf, cs["masks"], O.lgf_cube(64), nonlinear=True,
+                         tab=O.SCHEMES[scheme])
     d_u0 = torch.from_numpy(to_blocks_dense(u0, B, xs, org)).cuda()
     d_u1 = torch.zeros_like(d_u0)
     rk.step(d_u0, d_u1, uinf)
@@ -83,3 +86,29 @@ def test_step_divergence_free_on_gpu():
     nsoln = len(cs["soln"])  # soln blocks come first in the field order
     d = div[:nsoln].abs().max().item()
     assert d < 1e-5 * d_u1.abs().max().item() / dx, d
+
+
+def test_temporal_order_of_schemes():
+    """Observed order of the velocity over T = 2 (Re = 10, the ring case at amplitude 10)
+    against a 128-step reference: Scheme A 2, Schemes B and C 3 (the y-orders of the paper's
+    table of scheme orders)."""
+    lgf = built()
+    cs = small_case(B=8, amp=10.0)
+    B, org = cs["B"], cs["origin"]
+    re, T, uinf = 10.0, 2.0, (0.05, -0.02, 0.1)
+    want = {0: (1.7, 2.3), 1: (2.6, 3.4), 2: (2.6, 3.4)}
+    for scheme, (lo, hi) in want.items():
+        out = {}
+        for nst in (4, 8, 16, 128):
+            rk = lgf.RKPlan(B, cs["soln"], cs["dx"], T / nst, re, scheme=scheme)
+            xs = rk.blocks(0)
+            u = torch.from_numpy(to_blocks_dense(cs["u0"], B, xs, org)).cuda()
+            v = torch.zeros_like(u)
+            for _ in range(nst):
+                rk.step(u, v, uinf)
+                u, v = v, u
+            torch.cuda.synchronize()
+            out[nst] = u.double().cpu().numpy()
+        err = [np.linalg.norm(out[n] - out[128]) / np.linalg.norm(out[128]) for n in (4, 8, 16)]
+        orders = [np.log2(err[0] / err[1]), np.log2(err[1] / err[2])]
+        assert all(lo <= o <= hi for o in orders), (scheme, err, orders)

@@ -12,6 +12,7 @@ projection, Sec. 5 masks).
 import math
 
 import numpy as np
+import pytest
 
 import oracle as O
 from tests.rk_cases import small_case
@@ -26,6 +27,29 @@ def test_shifted_tableau_scheme_a():
     assert math.isclose(at[(3, 1)] + at[(3, 2)] + at[(3, 3)], 1.0)  # b sums to 1
 
 
+@pytest.mark.parametrize("name", ["A", "B", "C"])
+def test_tableau_order_conditions(name):
+    """Row sums give c; the classical order conditions hold to the order the
+    paper's table of scheme orders gives for y (A: 2, B and C: 3)."""
+    tab = O.SCHEMES[name]
+    A, b, c = tab["A"], tab["b"], tab["c"]
+    assert np.allclose(A.sum(1), c, atol=1e-15)
+    assert np.all(np.triu(A) == 0)                     # explicit
+    assert math.isclose(b.sum(), 1.0)
+    assert math.isclose(b @ c, 0.5)
+    third = math.isclose(b @ c ** 2, 1 / 3) and math.isclose(b @ A @ c, 1 / 6)
+    assert third == (name in ("B", "C"))
+
+
+@pytest.mark.parametrize("name,ct", [("B", (1 / 3, 1.0, 1.0)), ("C", (8 / 15, 2 / 3, 1.0))])
+def test_shifted_tableau_b_c(name, ct):
+    at, c_t, s = O.shifted_tableau(O.SCHEMES[name])
+    assert [c_t[i] for i in (1, 2, 3)] == pytest.approx(list(ct))
+    tab = O.SCHEMES[name]
+    assert at[(1, 1)] == pytest.approx(tab["A"][1, 0])
+    assert [at[(3, j)] for j in (1, 2, 3)] == pytest.approx(list(tab["b"]))
+
+
 def test_linear_step_is_one_integrating_factor():
     cs = small_case(B=8)
     u0 = cs["u0"]
@@ -34,6 +58,18 @@ def test_linear_step_is_one_integrating_factor():
     u1 = O.if_herk_step(u0, dt, re, dx, (0.0, 0.0, 0.0), cs["masks"], cube, nonlinear=False)
     ref = O.ifactor_masked(O.ifactor_taps(dt / (re * dx * dx)), u0, cs["masks"]["xsoln"])
     assert np.abs(u1 - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("name", ["B", "C"])
+def test_linear_step_b_c(name):
+    """Schemes B and C, nonlinear term off: H^3 H^2 H^1 = E((c~_3 - c~_0) alpha) = E(alpha)."""
+    cs = small_case(B=8)
+    u0 = cs["u0"]
+    dt, re, dx = 0.5, 10.0, 1.0
+    u1 = O.if_herk_step(u0, dt, re, dx, (0.0, 0.0, 0.0), cs["masks"], O.lgf_cube(64), nonlinear=False,
+                        tab=O.SCHEMES[name])
+    ref = O.ifactor_masked(O.ifactor_taps(dt / (re * dx * dx)), u0, cs["masks"]["xsoln"])
+    assert np.abs(u1 - ref).max() < 1e-10 * np.abs(ref).max()
 
 
 def test_step_is_divergence_free_on_supp():
