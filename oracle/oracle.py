@@ -30,7 +30,8 @@ __all__ = [
     "direct_conv_box", "ifactor_direct", "shift", "op_G", "op_Gt", "op_C", "op_Ct", "op_D",
     "op_Dbar", "op_L", "op_N", "residual_L", "WATSON_W", "num_threads", "SCHEME_A", "SCHEME_B", "SCHEME_C",
     "SCHEMES", "shifted_tableau",
-    "block_mask", "ifactor_masked", "poisson_masked", "if_herk_step", "lgf_points",
+    "block_mask", "ifactor_masked", "poisson_masked", "if_herk_step", "lgf_points", "ifactor_tail", "rk_qmax",
+    "vor2vel",
 ]
 
 # Watson's integral for the simple cubic lattice, closed form (Watson 1939):
@@ -365,6 +366,37 @@ def poisson_masked(cube, f, supp_mask, xsoln_mask, dx):
     out = np.zeros_like(f)
     out[z, y, x] = dx * dx * direct_conv_box(cube, np.where(supp_mask, f, 0.0), tgt)
     return out
+
+
+def ifactor_tail(k: int, alpha: float, nmax: int = 400) -> float:
+    """Truncation error of the integrating factor at depth k inside a masked
+    region (App. D): for a uniform field kept only on n > 0, the relative
+    difference between E(alpha) u and M E(alpha) M u at n = k is the kernel's
+    mass beyond the mask edge, sum_{n >= k} g(n), g(n) = exp(-2 alpha) I_n(2 alpha).
+    (Reading: the App. D sum is written with index k - j + 1; the mass that the
+    mask removes at depth k is the tail n >= k of the 1-D kernel.)"""
+    g = bessel_scaled(alpha, nmax)
+    return float(g[k:].sum()) if k <= nmax else 0.0
+
+
+def rk_qmax(beta: float, depth: int, eps: float, qcap: int = 1 << 16) -> int:
+    """Largest number of steps q (>= 1 when possible, else 0) over which the
+    integrating factors of a step, E(q beta) with beta = dt / (dx^2 Re), keep the
+    truncation error at depth n_E = depth below eps relative to max |u| (Sec. 5
+    velocity refresh, App. D)."""
+    q = 0
+    while q < qcap and ifactor_tail(depth, (q + 1) * beta) <= eps:
+        q += 1
+    return q
+
+
+def vor2vel(u, masks, cube, dx):
+    """Velocity refresh of Sec. 5 (eq. vel_refresh): w = M^xsoln C M^xsoln u,
+    a = -M^xsoln L^{-1} M^supp w (per component, eq. vel_vor), u' = M^xsoln C^T M^xsoln a."""
+    xs = masks["xsoln"]
+    w = op_C(u * xs, dx) * xs
+    a = np.stack([-poisson_masked(cube, w[q], masks["supp"], xs, dx) for q in range(3)])
+    return op_Ct(a * xs, dx) * xs
 
 
 def if_herk_step(u, dt, re, dx, uinf, masks, cube, nonlinear=True, tab=SCHEME_A):

@@ -82,3 +82,38 @@ def test_step_is_divergence_free_on_supp():
     supp = cs["masks"]["supp"]
     assert np.abs(div[supp]).max() < 1e-11 * np.abs(u1).max() / dx
     assert np.abs(u1 - u0).max() > 1e-4 * np.abs(u0).max()  # the step did something
+
+
+@pytest.mark.parametrize("alpha", [0.05, 0.3, 1.0])
+def test_ifactor_tail_is_masked_convolution_error(alpha):
+    """App. D: (I - M' E M') u at depth k for a uniform u kept on n > 0, by an explicit
+    1-D convolution, equals the kernel tail; and tail(0) = (1 + g(0)) / 2 (kernel mass 1,
+    symmetric)."""
+    R = 120
+    g = O.bessel_scaled(alpha, R)
+    kern = np.concatenate([g[:0:-1], g])            # g(-R..R)
+    n = np.arange(-300, 301)
+    u = (n > 0).astype(float)                        # M' applied to the uniform field 1
+    y = np.convolve(u, kern, mode="same") * (n > 0)   # M' E M' u
+    for k in (1, 2, 5, 9):
+        err = 1.0 - y[n == k][0]
+        assert abs(err - O.ifactor_tail(k, alpha)) < 1e-15
+    assert abs(O.ifactor_tail(0, alpha) - 0.5 * (1 + g[0])) < 1e-15
+
+
+def test_rk_qmax_brackets_the_tolerance():
+    for beta, depth, eps in [(0.05, 8, 1e-6), (0.086, 16, 1e-6), (0.02, 8, 1e-10)]:
+        q = O.rk_qmax(beta, depth, eps)
+        assert q >= 1
+        assert O.ifactor_tail(depth, q * beta) <= eps < O.ifactor_tail(depth, (q + 1) * beta)
+
+
+def test_vor2vel_recovers_divergence_free_velocity():
+    """u0 = C^T a0 with compact a0: Vor2Vel(u0) = C^T(-L^{-1} C u0) reproduces u0 on D_soln
+    (the identity -L = C C^T + D^T D on edges with D C u0 = 0; the masks only touch the
+    outermost xsoln layer)."""
+    cs = small_case(B=8)
+    u0 = cs["u0"]
+    u1 = O.vor2vel(u0, cs["masks"], O.lgf_cube(64), cs["dx"])
+    so = cs["masks"]["soln"]
+    assert np.abs(u1[:, so] - u0[:, so]).max() < 1e-10 * np.abs(u0).max()
