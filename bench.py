@@ -403,7 +403,7 @@ def aux_workload(name, lgf, torch):
         return step, plans + [pp], 3 * x.numel() + 32 ** 3, {
             "workload": "integrating factor on a 3 x 128^3 two-ring velocity, alpha in {0.05, 0.2, 1.0} "
                         "(R = 7, 9, 15), plus the 32^3 Poisson solve, one captured graph per step"}, tabs + [tp]
-    if name in ("rk256", "rk256_b", "rk256_c"):
+    if name in ("rk256", "rk256_b", "rk256_c", "rk256_refresh"):
         n, R0c, dcells = 256, 50.0, 10.0
         dx = 1.0 / R0c                      # R0 = 1, Gamma = 1
         dt, re = 0.01721, 500.0             # Sec. 6.4: dt Gamma/R0^2 = 0.01721, Re = 500
@@ -411,7 +411,7 @@ def aux_workload(name, lgf, torch):
         axis = inputs.random_axis_tilted(inputs.rng_for(4))
         w = inputs.vortex_ring_edges(n, R0c, dcells, axis) / dx ** 2   # physical vorticity
         supp = inputs.active_blocks(w, B, 1e-6)
-        scheme = {"rk256": 0, "rk256_b": 1, "rk256_c": 2}[name]
+        scheme = {"rk256": 0, "rk256_b": 1, "rk256_c": 2, "rk256_refresh": 0}[name]
         rk = lgf.RKPlan(B, supp, dx, dt, re, scheme=scheme)
         xs = rk.blocks(0)
         # initial velocity by the method itself: a = -L^-1 w (vector, D_supp -> D_xsoln), u = C^T a
@@ -424,6 +424,11 @@ def aux_workload(name, lgf, torch):
         u0 = torch.zeros_like(a)
         rk.op(lgf.OP_CURL_T, a, u0)
         u1 = torch.zeros_like(u0)
+        if name == "rk256_refresh":
+            return (lambda: rk.refresh(u0, u1)), [rk], len(xs) * B ** 3, {
+                "workload": "velocity refresh u = C^T(-L^-1 C u) (vector Poisson D_supp -> D_xsoln), Re=500 ring, "
+                            "256^3 bounding box", "supp_blocks": int(len(supp)), "xsoln_blocks": int(len(xs)),
+                "qmax_eps_1e-6": rk.qmax(1e-6), "points": "D_xsoln points per refresh"}, [t, pv]
         return (lambda: rk.step(u0, u1, uinf)), [rk], len(xs) * B ** 3, {
             "workload": ("one Scheme-%s IF-HERK step, Re=500 ring (R0 = 50 dx, core 10 dx), 256^3 bounding box, "
                          "D_supp = blocks with |w| > 1e-6 max, D_xsoln = one-block dilation") % "ABC"[scheme],
@@ -513,7 +518,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="ring128", choices=["ring128", "blobs32", "if128", "rk256", "rk256_b", "rk256_c", "ragged64"],
+    ap.add_argument("--workload", default="ring128", choices=["ring128", "blobs32", "if128", "rk256", "rk256_b", "rk256_c", "rk256_refresh",
+                                                                 "ragged64"],
                     help="ring128 is the headline workload; the others print their own throughput")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -229,6 +229,21 @@ lgf_status lgf_rk_blocks(const lgf_plan *p, int which, int32_t *coords, int n);
  * five integrating-factor applications (six for Scheme C, whose H^3 is not the identity), three
  * nonlinear terms.  Asynchronous; no allocation. */
 lgf_status lgf_rk_step(lgf_plan *p, const float *u_in, float *u_out, const double uinf[3], void *stream);
+/* Velocity refresh of Sec. 5 (eq. vel_refresh): u_out = M^xsoln C^T M^xsoln a with
+ * a = -M^xsoln L^{-1} M^supp w and w = M^xsoln C M^xsoln u_in (a vector Poisson solve
+ * D_supp -> D_xsoln).  u_in, u_out device [n_xsoln][3][B^3]; u_out may equal u_in.
+ * Asynchronous; no allocation. */
+lgf_status lgf_rk_refresh(lgf_plan *p, const float *u_in, float *u_out, void *stream);
+/* Largest number of steps q over which the composed integrating factors E(q alpha) keep the
+ * error the D_xsoln mask causes at depth B (one buffer block) below eps relative to max |u|
+ * (App. D, with the truncation error read as the kernel mass beyond that depth); 0 if not
+ * even one step does; -1 (lgf_last_error set) for a bad argument.  Host only. */
+int lgf_rk_qmax(const lgf_plan *p, double eps);
+/* nsteps IF-HERK steps u_in -> u_out with a velocity refresh before every step k > 0 with
+ * k % qmax == 0 (qmax = 0: never); u_in is not modified; u_in and u_out must not alias.
+ * Asynchronous; no allocation. */
+lgf_status lgf_rk_run(lgf_plan *p, const float *u_in, float *u_out, int nsteps, const double uinf[3], int qmax,
+                      void *stream);
 /* One App. A operator on the D_xsoln block set (zero outside it):
  *   op 0: e = C f (faces -> edges)      op 1: f = C^T e (edges -> faces)
  *   op 2: c = G^T f (faces -> cells)    op 3: f = G c (cells -> faces)

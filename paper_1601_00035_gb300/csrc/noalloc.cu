@@ -36,8 +36,10 @@ static void *g_scratch_addr[64] = {nullptr};
 static int32_t g_lut_S[kMaxBBox], g_lut_1[kMaxBBox], g_lut_2[kMaxBBox];
 static int32_t g_nb[3 * 3 * kMaxBlocks];
 
+}  // namespace
+
 // e^{-x} I_n(x), n = 0..nmax, by Miller's backward recurrence normalised with
-// e^{-x} (I_0 + 2 sum_{n>=1} I_n) = 1 (host copy for the taps; x <= 100 here).
+// e^{-x} (I_0 + 2 sum_{n>=1} I_n) = 1 (host copy for the taps).
 void host_scaled_bessel(double x, int nmax, double *out)
 {
     for (int n = 0; n <= nmax; n++) out[n] = 0.0;
@@ -64,6 +66,8 @@ void host_scaled_bessel(double x, int nmax, double *out)
     out[0] = cur;
     for (int n = 0; n <= nmax; n++) out[n] /= norm;
 }
+
+namespace {
 
 lgf_status scratch_base(unsigned char **base)
 {

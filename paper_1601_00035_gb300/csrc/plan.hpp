@@ -128,6 +128,9 @@ lgf_status gather_launch(const float *in, float *out, const int *d_idx, int n, i
 lgf_status grad_combine_launch(int B, int nblk, const int *d_nbr27, const float *dhat, const float *rv, const float *g,
                                float *out1, float *out2, double c2, double dx, cudaStream_t s);
 
+// e^{-x} I_n(x), n = 0..nmax, on the host (noalloc.cu)
+void host_scaled_bessel(double x, int nmax, double *out);
+
 // one IF-HERK step on a block set (rk.cu)
 struct RkPlan {
     int B = 0, n_soln = 0, n_x = 0;
@@ -143,6 +146,7 @@ struct RkPlan {
     int scheme = 0;
     double at[4][4] = {};  // shifted tableau a~_{i,j}, 1-based
     lgf_plan *poisson = nullptr;
+    lgf_plan *poisson3 = nullptr;  // vector Poisson supp -> xsoln (velocity refresh)
     int *d_nbr27 = nullptr;
     unsigned char *d_soln_keep = nullptr;
     int *d_supp_idx = nullptr;

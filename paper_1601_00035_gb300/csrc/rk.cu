@@ -56,6 +56,7 @@ void free_rk(RkPlan *r)
 {
     if (!r) return;
     lgf_plan_destroy(r->poisson);
+    lgf_plan_destroy(r->poisson3);
     for (int i = 0; i < 3; i++)
         if (r->if_owned[i]) {
             lgf_plan_destroy(r->ifp[i]);
@@ -217,6 +218,11 @@ lgf_status lgf_rk_plan(const lgf_rk_desc *d, void *stream, lgf_plan **out)
     pd.dx = d->dx;
     pd.scale = -1.0;
     if ((st = lgf_conv_plan(r->lgf_table, &pd, 1, nullptr, stream, &r->poisson)) != LGF_OK) return fail(st);
+    {
+        lgf_solve_desc pv = pd;  // vector potential a = -L^{-1} w (velocity refresh)
+        pv.ncomp = 3;
+        if ((st = lgf_conv_plan(r->lgf_table, &pv, 1, nullptr, stream, &r->poisson3)) != LGF_OK) return fail(st);
+    }
     // shifted tableau of the scheme (eq. ifherk_schemes, eq. herk_shift)
     {
         const double r3 = std::sqrt(3.0);
@@ -277,7 +283,9 @@ lgf_status lgf_rk_plan(const lgf_rk_desc *d, void *stream, lgf_plan **out)
     r->vec = (size_t)nx * 3 * B3;
     r->scal_x = (size_t)nx * B3;
     r->scal_s = (size_t)nsoln * B3;
-    const size_t total = 8 * r->vec + r->scal_x + r->scal_s;
+    // 8 vectors (slot 5 holds a multi-step run's intermediate state), d^ on D_xsoln and
+    // D_supp, and w on D_supp (3 components) for the refresh
+    const size_t total = 8 * r->vec + r->scal_x + r->scal_s + 3 * r->scal_s;
     if (cudaMalloc(&r->work, total * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         set_error("lgf_rk_plan: workspace allocation of %zu bytes failed", total * sizeof(float));
@@ -336,6 +344,7 @@ lgf_status lgf_rk_step(lgf_plan *p, const float *u_in, float *u_out, const doubl
     const double a11 = r->at[1][1], a21 = r->at[2][1], a22 = r->at[2][2];
     const double a31 = r->at[3][1], a32 = r->at[3][2], a33 = r->at[3][3];
     const size_t V = r->vec;
+    // slots 0-7: g, rv, w11, w22, t1, (lgf_rk_run's state), u1, u2
     float *g = r->work, *rv = g + V, *w11 = rv + V, *w22 = w11 + V, *t1 = w22 + V, *u1 = t1 + 2 * V,
           *u2 = u1 + V;
     const int B = r->B;
@@ -385,6 +394,72 @@ lgf_status lgf_rk_step(lgf_plan *p, const float *u_in, float *u_out, const doubl
         LGF_TRY(H(3, t1, u_out));
     } else {
         LGF_TRY(project(rv, u_out, nullptr, 0.0));
+    }
+    return LGF_OK;
+}
+
+lgf_status lgf_rk_refresh(lgf_plan *p, const float *u_in, float *u_out, void *stream)
+{
+    clear_error();
+    LGF_CHECK_ARG(p && u_in && u_out, "lgf_rk_refresh: NULL argument");
+    LGF_CHECK_ARG(p->kind == LGF_PLAN_RK, "lgf_rk_refresh: needs a plan from lgf_rk_plan");
+    RkPlan *r = p->rk;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t V = r->vec;
+    float *wx = r->work, *ax = wx + V;                          // w and a on D_xsoln
+    float *ws = r->work + 8 * V + r->scal_x + r->scal_s;         // w on D_supp
+    const int B3 = r->B * r->B * r->B;
+    Profiler &pr = p->prof;
+    // w = M^xsoln C M^xsoln u; a = -M^xsoln L^{-1} M^supp w; u' = M^xsoln C^T M^xsoln a (eq. vel_refresh)
+    LGF_TRY(timed(pr, "op_curl", s, [&] { return op_launch(0, r->B, r->n_x, r->d_nbr27, nullptr, u_in, wx, r->dx, 1.0, nullptr, s); }));
+    LGF_TRY(timed(pr, "gather_supp", s, [&] { return gather_launch(wx, ws, r->d_supp_idx, r->n_soln, 3 * B3, s); }));
+    const float *srcs[1] = {ws};
+    float *dsts[1] = {ax};
+    LGF_TRY(lgf_conv_execute(r->poisson3, srcs, dsts, s));
+    LGF_TRY(timed(pr, "op_curl_t", s, [&] { return op_launch(1, r->B, r->n_x, r->d_nbr27, nullptr, ax, u_out, r->dx, 1.0, nullptr, s); }));
+    return LGF_OK;
+}
+
+int lgf_rk_qmax(const lgf_plan *p, double eps)
+{
+    clear_error();
+    if (!p || p->kind != LGF_PLAN_RK || !(eps > 0.0)) {
+        set_error("lgf_rk_qmax: needs an RK plan and eps > 0");
+        return -1;
+    }
+    // App. D: the integrating factors of q steps compose to E(q alpha) (alpha = dt / (dx^2 Re));
+    // the relative error the D_xsoln mask causes at depth n_E = B (one buffer block) is the
+    // kernel mass beyond n_E, sum_{n >= B} e^{-2 q alpha} I_n(2 q alpha)
+    const RkPlan *r = p->rk;
+    const int depth = r->B;
+    const int nmax = depth + 400;
+    std::vector<double> g(nmax + 1);
+    int q = 0;
+    while (q < 100000) {
+        host_scaled_bessel(2.0 * (q + 1) * r->alpha, nmax, g.data());
+        double tail = 0.0;  // sum_{n >= depth} g(n), smallest terms first
+        for (int n = nmax; n >= depth; n--) tail += g[n];
+        if (tail > eps) break;
+        q++;
+    }
+    return q;
+}
+
+lgf_status lgf_rk_run(lgf_plan *p, const float *u_in, float *u_out, int nsteps, const double uinf[3], int qmax,
+                      void *stream)
+{
+    clear_error();
+    LGF_CHECK_ARG(p && u_in && u_out && uinf && u_in != u_out, "lgf_rk_run: NULL or aliasing argument");
+    LGF_CHECK_ARG(p->kind == LGF_PLAN_RK, "lgf_rk_run: needs a plan from lgf_rk_plan");
+    LGF_CHECK_ARG(nsteps >= 1 && qmax >= 0, "lgf_rk_run: nsteps >= 1 and qmax >= 0 required");
+    RkPlan *r = p->rk;
+    float *tmp = r->work + 5 * r->vec;  // the vector slot the step leaves unused
+    const float *cur = u_in;
+    for (int k = 0; k < nsteps; k++) {
+        float *nxt = ((nsteps - 1 - k) % 2 == 0) ? u_out : tmp;
+        if (k > 0 && qmax > 0 && k % qmax == 0) LGF_TRY(lgf_rk_refresh(p, cur, const_cast<float *>(cur), stream));
+        LGF_TRY(lgf_rk_step(p, cur, nxt, uinf, stream));
+        cur = nxt;
     }
     return LGF_OK;
 }

@@ -102,6 +102,10 @@ _SIGS = {
                                    ctypes.c_void_p]),
     "lgf_op_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                                     ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "lgf_rk_refresh": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "lgf_rk_qmax": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "lgf_rk_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                  ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_void_p]),
     "lgf_plan_destroy": (None, [ctypes.c_void_p]),
     "lgf_last_error": (ctypes.c_char_p, []),
     "lgf_version": (ctypes.c_char_p, []),
@@ -326,6 +330,21 @@ class RKPlan:
     def step(self, u_in, u_out, uinf=(0.0, 0.0, 0.0), stream=None):
         ui = (ctypes.c_double * 3)(*[float(v) for v in uinf])
         _check(load().lgf_rk_step(self._h, _ptr(u_in), _ptr(u_out), ui, _stream(stream)))
+
+    def refresh(self, u_in, u_out, stream=None):
+        """Velocity refresh (lgf_rk_refresh); u_out may be u_in."""
+        _check(load().lgf_rk_refresh(self._h, _ptr(u_in), _ptr(u_out), _stream(stream)))
+
+    def qmax(self, eps: float) -> int:
+        q = load().lgf_rk_qmax(self._h, float(eps))
+        if q < 0:
+            raise LGFError(LGF_ERR_ARG, load().lgf_last_error().decode())
+        return int(q)
+
+    def run(self, u_in, u_out, nsteps: int, uinf=(0.0, 0.0, 0.0), qmax: int = 0, stream=None):
+        """nsteps steps with a refresh every qmax steps (lgf_rk_run)."""
+        ui = (ctypes.c_double * 3)(*[float(v) for v in uinf])
+        _check(load().lgf_rk_run(self._h, _ptr(u_in), _ptr(u_out), int(nsteps), ui, int(qmax), _stream(stream)))
 
     def op(self, op: int, inp, out, coef: float = 1.0, uinf=(0.0, 0.0, 0.0), stream=None):
         ui = (ctypes.c_double * 3)(*[float(v) for v in uinf])

@@ -112,3 +112,58 @@ def test_temporal_order_of_schemes():
         err = [np.linalg.norm(out[n] - out[128]) / np.linalg.norm(out[128]) for n in (4, 8, 16)]
         orders = [np.log2(err[0] / err[1]), np.log2(err[1] / err[2])]
         assert all(lo <= o <= hi for o in orders), (scheme, err, orders)
+
+
+def test_velocity_refresh_matches_oracle():
+    """lgf_rk_refresh (eq. vel_refresh) against the oracle's Vor2Vel on a field that is
+    not divergence-free near the xsoln edge (one IF-HERK step of the ring)."""
+    lgf = built()
+    cs = small_case(B=8, amp=3.0)
+    B, n, org, dx = cs["B"], cs["n"], cs["origin"], cs["dx"]
+    rk, xs = _plan(lgf, cs, 0.5, 10.0)
+    u = O.if_herk_step(cs["u0"], 0.5, 10.0, dx, (0.05, -0.02, 0.1), cs["masks"], O.lgf_cube(64), nonlinear=True)
+    ref = O.vor2vel(u, cs["masks"], O.lgf_cube(64), dx)
+    d_u = torch.from_numpy(to_blocks_dense(u, B, xs, org)).cuda()
+    d_v = torch.zeros_like(d_u)
+    rk.refresh(d_u, d_v)
+    got = from_blocks_dense(d_v.cpu().numpy(), B, xs, org, (n, n, n))
+    assert rel_l2(got, ref) < 1e-6, rel_l2(got, ref)
+    rk.refresh(d_u, d_u)  # in place
+    assert torch.equal(d_u, d_v)
+
+
+@pytest.mark.parametrize("dt,re,eps", [(0.5, 10.0, 1e-6), (0.01721, 500.0 * 0.02 ** 2, 1e-8)])
+def test_qmax_matches_oracle(dt, re, eps):
+    lgf = built()
+    cs = small_case(B=8)
+    rk, _ = _plan(lgf, cs, dt, re)
+    assert rk.qmax(eps) == O.rk_qmax(dt / (re * cs["dx"] ** 2), cs["B"], eps)
+
+
+def test_multi_step_run_with_refresh():
+    """lgf_rk_run: three steps with a refresh before steps 1 and 2 (qmax = 1) against the
+    oracle's step / Vor2Vel sequence; qmax = 0 equals three plain steps."""
+    lgf = built()
+    cs = small_case(B=8, amp=3.0)
+    B, n, org, dx = cs["B"], cs["n"], cs["origin"], cs["dx"]
+    dt, re, uinf = 0.5, 10.0, (0.05, -0.02, 0.1)
+    rk, xs = _plan(lgf, cs, dt, re)
+    cube = O.lgf_cube(64)
+    u = cs["u0"]
+    for k in range(3):
+        if k > 0:
+            u = O.vor2vel(u, cs["masks"], cube, dx)
+        u = O.if_herk_step(u, dt, re, dx, uinf, cs["masks"], cube, nonlinear=True)
+    d_u0 = torch.from_numpy(to_blocks_dense(cs["u0"], B, xs, org)).cuda()
+    d_u3 = torch.zeros_like(d_u0)
+    rk.run(d_u0, d_u3, 3, uinf, qmax=1)
+    got = from_blocks_dense(d_u3.cpu().numpy(), B, xs, org, (n, n, n))
+    assert rel_l2(got - cs["u0"], u - cs["u0"]) < 5e-6, rel_l2(got - cs["u0"], u - cs["u0"])
+    # no refresh: the same as three calls of step
+    d_a = torch.zeros_like(d_u0)
+    d_b = torch.zeros_like(d_u0)
+    rk.step(d_u0, d_a, uinf)
+    rk.step(d_a, d_b, uinf)
+    rk.step(d_b, d_a, uinf)
+    rk.run(d_u0, d_u3, 3, uinf, qmax=0)
+    assert torch.equal(d_u3, d_a)
