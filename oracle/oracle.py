@@ -31,7 +31,7 @@ __all__ = [
     "op_Dbar", "op_L", "op_N", "residual_L", "WATSON_W", "num_threads", "SCHEME_A", "SCHEME_B", "SCHEME_C",
     "SCHEMES", "shifted_tableau",
     "block_mask", "ifactor_masked", "poisson_masked", "if_herk_step", "lgf_points", "ifactor_tail", "rk_qmax",
-    "vor2vel",
+    "vor2vel", "ring_diagnostics",
 ]
 
 # Watson's integral for the simple cubic lattice, closed form (Watson 1939):
@@ -388,6 +388,51 @@ def rk_qmax(beta: float, depth: int, eps: float, qcap: int = 1 << 16) -> int:
     while q < qcap and ifactor_tail(depth, (q + 1) * beta) <= eps:
         q += 1
     return q
+
+
+def ring_diagnostics(u, dx, origin_cells, xs_mask, int_mask):
+    """The volume integrals of Sec. 6 eq. int_quantities on the lattice: impulse
+    I = 1/2 sum x cross w, K = sum u . (x cross w), E = 1/2 sum |w|^2, J = sum u . w
+    and the centroid X = 1/2 sum ((x cross w) . I / |I|^2) x (without the
+    freestream term), each times dx^3, over int_mask (D_soln: the integrands'
+    support, Sec. 6; the mask edge of D_xsoln carries a spurious vortex sheet that
+    these sums must not see).
+    Readings: w = M C M u on edges (eq. w_k of the algorithm summary, M = M^xsoln).
+    I, E and X are sums over edges, each vorticity component at its own edge
+    (edge (q) of vertex n at n - e_q / 2); K and J pair u with w at cell centres,
+    averaging the 2 faces / 4 edges around each cell (cell n at n - (1,1,1)/2).
+    Positions add origin_cells; an edge or face belongs to the cell of its index."""
+    w = op_C(u * xs_mask, dx) * xs_mask * int_mask
+    nz, ny, nx = int_mask.shape
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    vert = [(i + origin_cells[0]) * dx, (j + origin_cells[1]) * dx, (k + origin_cells[2]) * dx]
+    dv = dx ** 3
+    # x cross w, term by term at the edges of the vorticity component involved
+    def x_at_edge(a, q):  # coordinate a of edge (q)
+        return vert[a] - (0.5 * dx if a == q else 0.0)
+    I = np.zeros(3)
+    M = np.zeros((3, 3))
+    for a_ in range(3):
+        b_, c_ = (a_ + 1) % 3, (a_ + 2) % 3
+        # (x cross w)_a = x_b w_c - x_c w_b
+        t1, t2 = x_at_edge(b_, c_) * w[c_], x_at_edge(c_, b_) * w[b_]
+        I[a_] = 0.5 * (t1.sum() - t2.sum()) * dv
+        for bb in range(3):
+            M[a_, bb] = 0.5 * ((t1 * x_at_edge(bb, c_)).sum() - (t2 * x_at_edge(bb, b_)).sum()) * dv
+    E = float(0.5 * (w * w).sum() * dv)
+    X = (M.T @ I) / float(I @ I) if float(I @ I) > 0 else np.zeros(3)
+    # cell-centred products for K and J
+    uc = np.stack([0.5 * (u[q] + shift(u[q], q, -1)) for q in range(3)]) * int_mask
+    wc = []
+    for q in range(3):
+        r, s_ = (q + 1) % 3, (q + 2) % 3
+        wc.append(0.25 * (w[q] + shift(w[q], r, -1) + shift(w[q], s_, -1) + shift(shift(w[q], r, -1), s_, -1)))
+    wc = np.stack(wc) * int_mask
+    pos = [v - 0.5 * dx for v in vert]
+    xw = np.stack([pos[1] * wc[2] - pos[2] * wc[1], pos[2] * wc[0] - pos[0] * wc[2], pos[0] * wc[1] - pos[1] * wc[0]])
+    K = float((uc * xw).sum() * dv)
+    J = float((uc * wc).sum() * dv)
+    return {"I": I, "K": K, "E": E, "J": J, "X": X}
 
 
 def vor2vel(u, masks, cube, dx):
