@@ -239,6 +239,16 @@ lgf_status lgf_rk_refresh(lgf_plan *p, const float *u_in, float *u_out, void *st
  * (App. D, with the truncation error read as the kernel mass beyond that depth); 0 if not
  * even one step does; -1 (lgf_last_error set) for a bad argument.  Host only. */
 int lgf_rk_qmax(const lgf_plan *p, double eps);
+/* Ring diagnostics of Sec. 6 (eq. int_quantities) of the velocity perturbation u (device
+ * [n_xsoln][3][B^3]) over D_soln, with w = C u on edges: out[0..2] impulse I = 1/2 sum x cross w,
+ * out[3] K = sum u . (x cross w), out[4] enstrophy E = 1/2 sum |w|^2, out[5] helicity
+ * J = sum u . w, out[6..8] centroid X = 1/2 sum ((x cross w) . I / |I|^2) x without the
+ * freestream term (its component along I is the ring position); all times dx^3, positions
+ * in the lattice's absolute coordinates (block coordinate times B, times dx).  I, E and X sum
+ * over edges, each component at its own edge (n - e_q / 2); K and J pair u and w at cell
+ * centres (n - (1,1,1)/2), averaging the 2 faces / 4 edges around the cell.  FP64 sums;
+ * synchronises `stream` (out is host memory). */
+lgf_status lgf_rk_diagnostics(lgf_plan *p, const float *u, double out[9], void *stream);
 /* nsteps IF-HERK steps u_in -> u_out with a velocity refresh before every step k > 0 with
  * k % qmax == 0 (qmax = 0: never); u_in is not modified; u_in and u_out must not alias.
  * Asynchronous; no allocation. */

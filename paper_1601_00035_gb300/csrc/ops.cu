@@ -259,6 +259,92 @@ __global__ void __launch_bounds__(B *B) k_grad_combine(const float *__restrict__
     }
 }
 
+// Ring diagnostics (Sec. 6 eq. int_quantities) over the first n_soln blocks of
+// the set (D_soln): 15 FP64 sums, acc[0..2] = sum (x cross w) / 2, acc[3] = sum
+// u . (x cross w) at cell centres, acc[4] = sum |w|^2 / 2, acc[5] = sum u . w at
+// cell centres, acc[6 + 3a + b] = sum (x cross w)_a x_b / 2 (all without dx^3).
+// w = C u on edges (computed here in FP64 from u), counted only on D_soln edges;
+// edge (q) of cell index n sits at n - e_q / 2, cell n at n - (1,1,1)/2 (units
+// of dx); cell values average the 2 faces / 4 edges around the cell.
+template <int B>
+__global__ void __launch_bounds__(B *B) k_diag(const float *__restrict__ u, const float *__restrict__ w,
+                                               const int *__restrict__ nbr27, const int *__restrict__ coords,
+                                               int n_soln, double dx, double *__restrict__ acc)
+{
+    const int blk = blockIdx.x;
+    __shared__ int nb[27];
+    __shared__ double red[15][B * B / 32];
+    if (threadIdx.x < 27) {
+        const int n = nbr27[blk * 27 + threadIdx.x];
+        nb[threadIdx.x] = n < n_soln ? n : -1;  // w counts on D_soln only
+    }
+    __syncthreads();
+    const int x = threadIdx.x % B, y = threadIdx.x / B;
+    Fetch<B> U{u, 3, nbr27 + blk * 27};  // u: the whole set (global table)
+    // w = C u at edge (q) of index (px, py, pz) in FP64 (App. A), zero off D_soln
+    const double idx = 1.0 / dx;
+    auto W = [&](int q, int px, int py, int pz) -> double {
+        const int bx = px < 0 ? -1 : (px >= B ? 1 : 0);
+        const int by = py < 0 ? -1 : (py >= B ? 1 : 0);
+        const int bz = pz < 0 ? -1 : (pz >= B ? 1 : 0);
+        if (nb[(bz + 1) * 9 + (by + 1) * 3 + (bx + 1)] < 0) return 0.0;
+        const int r = (q + 1) % 3, s2 = (q + 2) % 3;
+        const int o[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+        return ((double)U(r, px, py, pz) - U(r, px + o[s2][0], py + o[s2][1], pz + o[s2][2]) +
+                U(s2, px + o[r][0], py + o[r][1], pz + o[r][2]) - U(s2, px, py, pz)) * idx;
+    };
+    (void)w;
+    const double ox = (double)coords[3 * blk] * B, oy = (double)coords[3 * blk + 1] * B,
+                 oz = (double)coords[3 * blk + 2] * B;
+    double a[15];
+#pragma unroll
+    for (int k = 0; k < 15; k++) a[k] = 0.0;
+    for (int z = 0; z < B; z++) {
+        const double vx = (ox + x) * dx, vy = (oy + y) * dx, vz = (oz + z) * dx;  // vertex of index n
+        const double h = 0.5 * dx;
+        // own-block edges
+        const double w0 = W(0, x, y, z), w1 = W(1, x, y, z), w2 = W(2, x, y, z);
+        // edge (q) positions: coordinate q shifted by -1/2
+        const double e[3][3] = {{vx - h, vy, vz}, {vx, vy - h, vz}, {vx, vy, vz - h}};  // e[q][a]
+        const double wv[3] = {w0, w1, w2};
+#pragma unroll
+        for (int ai = 0; ai < 3; ai++) {
+            const int bi = (ai + 1) % 3, ci = (ai + 2) % 3;
+            const double t1 = e[ci][bi] * wv[ci], t2 = e[bi][ci] * wv[bi];  // (x cross w)_a = x_b w_c - x_c w_b
+            a[ai] += 0.5 * (t1 - t2);
+#pragma unroll
+            for (int bb = 0; bb < 3; bb++) a[6 + 3 * ai + bb] += 0.5 * (t1 * e[ci][bb] - t2 * e[bi][bb]);
+        }
+        a[4] += 0.5 * (w0 * w0 + w1 * w1 + w2 * w2);
+        // cell-centred u and w
+        const double uc[3] = {0.5 * ((double)U(0, x, y, z) + U(0, x - 1, y, z)),
+                              0.5 * ((double)U(1, x, y, z) + U(1, x, y - 1, z)),
+                              0.5 * ((double)U(2, x, y, z) + U(2, x, y, z - 1))};
+        const double wc[3] = {
+            0.25 * ((double)w0 + W(0, x, y - 1, z) + W(0, x, y, z - 1) + W(0, x, y - 1, z - 1)),
+            0.25 * ((double)w1 + W(1, x, y, z - 1) + W(1, x - 1, y, z) + W(1, x - 1, y, z - 1)),
+            0.25 * ((double)w2 + W(2, x - 1, y, z) + W(2, x, y - 1, z) + W(2, x - 1, y - 1, z))};
+        const double px = vx - h, py = vy - h, pz = vz - h;
+        const double xw[3] = {py * wc[2] - pz * wc[1], pz * wc[0] - px * wc[2], px * wc[1] - py * wc[0]};
+        a[3] += uc[0] * xw[0] + uc[1] * xw[1] + uc[2] * xw[2];
+        a[5] += uc[0] * wc[0] + uc[1] * wc[1] + uc[2] * wc[2];
+    }
+    // block reduction: warp shuffles, then one partial per warp in shared memory
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+#pragma unroll
+    for (int k = 0; k < 15; k++) {
+        double v = a[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 15) {
+        double v = 0.0;
+        for (int i = 0; i < B * B / 32; i++) v += red[threadIdx.x][i];
+        atomicAdd(acc + threadIdx.x, v);
+    }
+}
+
 // out = sum_t c_t x_t over n floats (up to 4 terms; null x_t skipped).  out may
 // alias an input (each element is read and written by the same thread), so no
 // __restrict__ and no read-only-cache loads here.
@@ -341,6 +427,21 @@ lgf_status lincomb_launch(float *out, int64_t n, const float *x0, double c0, con
     const int blocks = (int)std::min<int64_t>((n / 4 + threads - 1) / threads, 152 * 16);
     k_lincomb<<<blocks, threads, 0, s>>>(out, n, x0, (float)c0, x1, (float)c1, x2, (float)c2, x3, (float)c3);
     LGF_LAUNCH_CHECK("lincomb");
+    return LGF_OK;
+}
+
+lgf_status diag_launch(int B, int n_soln, const int *d_nbr27, const int *d_coords, const float *u, const float *w,
+                       double dx, double *d_acc, cudaStream_t s)
+{
+    if (B == 8)
+        k_diag<8><<<n_soln, 64, 0, s>>>(u, w, d_nbr27, d_coords, n_soln, dx, d_acc);
+    else if (B == 16)
+        k_diag<16><<<n_soln, 256, 0, s>>>(u, w, d_nbr27, d_coords, n_soln, dx, d_acc);
+    else {
+        set_error("operators support B in {8, 16} (got %d)", B);
+        return LGF_ERR_ARG;
+    }
+    LGF_LAUNCH_CHECK("diagnostics");
     return LGF_OK;
 }
 

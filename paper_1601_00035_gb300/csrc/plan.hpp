@@ -123,6 +123,9 @@ lgf_status op_launch(int op, int B, int nblk, const int *d_nbr27, const unsigned
 lgf_status lincomb_launch(float *out, int64_t n, const float *x0, double c0, const float *x1, double c1,
                           const float *x2, double c2, const float *x3, double c3, cudaStream_t s);
 lgf_status gather_launch(const float *in, float *out, const int *d_idx, int n, int block_floats, cudaStream_t s);
+// ring diagnostics sums over D_soln (the first n_soln blocks): 15 FP64 accumulators
+lgf_status diag_launch(int B, int n_soln, const int *d_nbr27, const int *d_coords, const float *u, const float *w,
+                       double dx, double *d_acc, cudaStream_t s);
 // projection tail of a stage: with gd = G dhat (cells -> faces),
 // out1 = rv - gd and, when out2 != nullptr, out2 = c2 (g - gd)
 lgf_status grad_combine_launch(int B, int nblk, const int *d_nbr27, const float *dhat, const float *rv, const float *g,
@@ -148,6 +151,8 @@ struct RkPlan {
     lgf_plan *poisson = nullptr;
     lgf_plan *poisson3 = nullptr;  // vector Poisson supp -> xsoln (velocity refresh)
     int *d_nbr27 = nullptr;
+    int *d_coords = nullptr;   // [n_x][3] block coordinates
+    double *d_acc = nullptr;   // diagnostics accumulators
     unsigned char *d_soln_keep = nullptr;
     int *d_supp_idx = nullptr;
     float *work = nullptr;

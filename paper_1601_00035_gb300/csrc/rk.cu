@@ -64,6 +64,8 @@ void free_rk(RkPlan *r)
         }
     lgf_table_destroy(r->lgf_table);
     cudaFree(r->d_nbr27);
+    cudaFree(r->d_coords);
+    cudaFree(r->d_acc);
     cudaFree(r->d_soln_keep);
     cudaFree(r->d_supp_idx);
     cudaFree(r->work);
@@ -176,6 +178,12 @@ lgf_status lgf_rk_plan(const lgf_rk_desc *d, void *stream, lgf_plan **out)
         supp[i] = i;
     }
     if ((st = alloc_upload(&r->d_nbr27, nbr, r->bytes)) != LGF_OK) return fail(st);
+    if ((st = alloc_upload(&r->d_coords, xs, r->bytes)) != LGF_OK) return fail(st);
+    if (cudaMalloc(&r->d_acc, 15 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("lgf_rk_plan: allocation failed");
+        return fail(LGF_ERR_OOM);
+    }
     if ((st = alloc_upload(&r->d_soln_keep, keep, r->bytes)) != LGF_OK) return fail(st);
     if ((st = alloc_upload(&r->d_supp_idx, supp, r->bytes)) != LGF_OK) return fail(st);
     // Poisson sub-plan: supp -> xsoln, scalar, d^ = -L^{-1} f (scale -1)
@@ -443,6 +451,33 @@ int lgf_rk_qmax(const lgf_plan *p, double eps)
         q++;
     }
     return q;
+}
+
+lgf_status lgf_rk_diagnostics(lgf_plan *p, const float *u, double out[9], void *stream)
+{
+    clear_error();
+    LGF_CHECK_ARG(p && u && out, "lgf_rk_diagnostics: NULL argument");
+    LGF_CHECK_ARG(p->kind == LGF_PLAN_RK, "lgf_rk_diagnostics: needs a plan from lgf_rk_plan");
+    RkPlan *r = p->rk;
+    cudaStream_t s = (cudaStream_t)stream;
+    LGF_CUDA_TRY(cudaMemsetAsync(r->d_acc, 0, 15 * sizeof(double), s));
+    LGF_TRY(diag_launch(r->B, r->n_soln, r->d_nbr27, r->d_coords, u, nullptr, r->dx, r->d_acc, s));
+    double h[15];
+    LGF_CUDA_TRY(cudaMemcpyAsync(h, r->d_acc, sizeof(h), cudaMemcpyDeviceToHost, s));
+    LGF_CUDA_TRY(cudaStreamSynchronize(s));
+    const double dv = r->dx * r->dx * r->dx;
+    const double I[3] = {h[0] * dv, h[1] * dv, h[2] * dv};
+    const double ii = I[0] * I[0] + I[1] * I[1] + I[2] * I[2];
+    for (int a = 0; a < 3; a++) out[a] = I[a];
+    out[3] = h[3] * dv;
+    out[4] = h[4] * dv;
+    out[5] = h[5] * dv;
+    for (int b = 0; b < 3; b++) {  // X_b = sum_a M_ab I_a / |I|^2
+        double v = 0.0;
+        for (int a = 0; a < 3; a++) v += h[6 + 3 * a + b] * dv * I[a];
+        out[6 + b] = ii > 0.0 ? v / ii : 0.0;
+    }
+    return LGF_OK;
 }
 
 lgf_status lgf_rk_run(lgf_plan *p, const float *u_in, float *u_out, int nsteps, const double uinf[3], int qmax,

@@ -106,6 +106,8 @@ _SIGS = {
     "lgf_rk_qmax": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "lgf_rk_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_void_p]),
+    "lgf_rk_diagnostics": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.c_void_p]),
     "lgf_plan_destroy": (None, [ctypes.c_void_p]),
     "lgf_last_error": (ctypes.c_char_p, []),
     "lgf_version": (ctypes.c_char_p, []),
@@ -340,6 +342,13 @@ class RKPlan:
         if q < 0:
             raise LGFError(LGF_ERR_ARG, load().lgf_last_error().decode())
         return int(q)
+
+    def diagnostics(self, u, stream=None) -> dict:
+        """Ring diagnostics over D_soln (lgf_rk_diagnostics): I, K, E, J, X."""
+        out = (ctypes.c_double * 9)()
+        _check(load().lgf_rk_diagnostics(self._h, _ptr(u), out, _stream(stream)))
+        v = list(out)
+        return {"I": np.array(v[0:3]), "K": v[3], "E": v[4], "J": v[5], "X": np.array(v[6:9])}
 
     def run(self, u_in, u_out, nsteps: int, uinf=(0.0, 0.0, 0.0), qmax: int = 0, stream=None):
         """nsteps steps with a refresh every qmax steps (lgf_rk_run)."""

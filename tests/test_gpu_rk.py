@@ -167,3 +167,78 @@ def test_multi_step_run_with_refresh():
     rk.step(d_b, d_a, uinf)
     rk.run(d_u0, d_u3, 3, uinf, qmax=0)
     assert torch.equal(d_u3, d_a)
+
+
+def test_diagnostics_match_oracle():
+    """lgf_rk_diagnostics against the oracle's ring diagnostics on the field after one step."""
+    lgf = built()
+    cs = small_case(B=8, amp=3.0)
+    B, n, org, dx = cs["B"], cs["n"], cs["origin"], cs["dx"]
+    rk, xs = _plan(lgf, cs, 0.5, 10.0)
+    d_u0 = torch.from_numpy(to_blocks_dense(cs["u0"], B, xs, org)).cuda()
+    d_u1 = torch.zeros_like(d_u0)
+    rk.step(d_u0, d_u1, (0.05, -0.02, 0.1))
+    u1 = from_blocks_dense(d_u1.double().cpu().numpy(), B, xs, org, (n, n, n))
+    ref = O.ring_diagnostics(u1, dx, tuple(np.asarray(org) * B), cs["masks"]["xsoln"], cs["masks"]["soln"])
+    got = rk.diagnostics(d_u1)
+    for k in ("K", "E", "J"):
+        scale = max(abs(ref[k]), 1e-3 * abs(ref["E"]))
+        assert abs(got[k] - ref[k]) < 1e-6 * scale, (k, got[k], ref[k])
+    assert np.abs(got["I"] - ref["I"]).max() < 1e-6 * np.abs(ref["I"]).max()
+    assert np.abs(got["X"] - ref["X"]).max() < 1e-6 * np.abs(ref["X"]).max()
+
+
+def _ring_run(lgf, n, R0c, dcells, nsteps=7):
+    """The Re = 500 ring of the IF-HERK benchmark at resolution R0 / dx = R0c (core
+    dcells cells), Scheme B, u_inf along -z as in Sec. 6; diagnostics at every step."""
+    from paper_1601_00035_gb300 import inputs
+    B = 16
+    dx = 1.0 / R0c
+    dt, re = 0.01721 * (50.0 / R0c), 500.0
+    uinf = (0.0, 0.0, -0.18686)
+    axis = inputs.random_axis_tilted(inputs.rng_for(4))
+    w = inputs.vortex_ring_edges(n, R0c, dcells, axis) / dx ** 2
+    supp = inputs.active_blocks(w, B, 1e-6)
+    rk = lgf.RKPlan(B, supp, dx, dt, re, scheme=1)
+    xs = rk.blocks(0)
+    t = lgf.Table(lgf.LAPLACE7, max_offset=lgf.required_max_offset(supp, xs, B))
+    pv = lgf.Plan(t, [lgf.Solve(B, 3, supp, xs, dx=dx, scale=-1.0)])
+    a = torch.zeros((len(xs), 3, B, B, B), device="cuda")
+    pv.execute([torch.from_numpy(inputs.to_blocks(w, B, supp)).cuda()], [a])
+    u = torch.zeros_like(a)
+    rk.op(lgf.OP_CURL_T, a, u)
+    v = torch.zeros_like(u)
+    ds = []
+    for _ in range(nsteps):
+        ds.append(rk.diagnostics(u))
+        rk.step(u, v, uinf)
+        u, v = v, u
+    return ds, dt, re, np.asarray(uinf), dcells / R0c
+
+
+def test_ring_energy_impulse_and_speed():
+    """Physics of the IF-HERK solution (Sec. 6 eq. int_quantities and eq. u_saffman):
+    * dK/dt = -2 nu E (nu = 1/Re) by central differences, to second order in dx: the
+      relative defect falls by (dx ratio)^2 between R0/dx = 24 and 50;
+    * the impulse |I| = pi Gamma (R0^2 + delta^2/2) and is conserved over the steps;
+    * E(0) = Gamma^2 R0 / (2 delta^2);
+    * the ring speed (dX/dt along I, plus the freestream) is within 10 % of
+      Saffman's leading-order value for delta / R0 = 0.2."""
+    import math
+    lgf = built()
+    defects = []
+    for n, R0c, dcells in [(128, 24.0, 4.8), (256, 50.0, 10.0)]:
+        ds, dt, re, uinf, eps = _ring_run(lgf, n, R0c, dcells)
+        K = np.array([d["K"] for d in ds])
+        E = np.array([d["E"] for d in ds])
+        ratio = (K[2:] - K[:-2]) / (2 * dt) / (-2.0 / re * E[1:-1])
+        defects.append(1.0 - ratio.mean())
+        I0, I1 = ds[0]["I"], ds[-1]["I"]
+        assert abs(np.linalg.norm(I0) / (math.pi * (1 + eps * eps / 2)) - 1) < 0.01
+        assert np.abs(I1 - I0).max() < 1e-5 * np.linalg.norm(I0)
+        assert abs(E[0] / (1.0 / (2 * eps * eps)) - 1) < 0.01
+        ih = I0 / np.linalg.norm(I0)
+        speed = (ds[-1]["X"] - ds[0]["X"]) @ ih / ((len(ds) - 1) * dt) - uinf @ ih
+        saffman = (math.log(8 / eps) - 0.557966) / (4 * math.pi)
+        assert abs(speed / saffman - 1) < 0.1, (n, speed, saffman)
+    assert 0 < defects[1] < 0.02 and 3.0 < defects[0] / defects[1] < 6.5, defects
