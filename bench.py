@@ -434,6 +434,47 @@ def aux_workload(name, lgf, torch):
                          "D_supp = blocks with |w| > 1e-6 max, D_xsoln = one-block dilation") % "ABC"[scheme],
             "supp_blocks": int(len(supp)), "xsoln_blocks": int(len(xs)), "alpha": dt / (re * dx * dx),
             "points": "D_xsoln points per step"}, [t, pv]
+    if name == "vecscal256":
+        # vector vs scalar Poisson solve on the 256^3 ring's D_supp -> D_xsoln (the wall-time
+        # ratio the paper quotes as ~2.8 for its LGF-FMM; here the three components share
+        # every launch of the FFT passes)
+        n, R0c, dcells = 256, 50.0, 10.0
+        dx = 1.0 / R0c
+        axis = inputs.random_axis_tilted(inputs.rng_for(4))
+        w = inputs.vortex_ring_edges(n, R0c, dcells, axis) / dx ** 2
+        supp = inputs.active_blocks(w, B, 1e-6)
+        xs = _dilate(supp)
+        t = lgf.Table(lgf.LAPLACE7, max_offset=lgf.required_max_offset(supp, xs, B))
+        p1 = lgf.Plan(t, [lgf.Solve(B, 1, supp, xs, dx=dx, scale=-1.0)])
+        p3 = lgf.Plan(t, [lgf.Solve(B, 3, supp, xs, dx=dx, scale=-1.0)])
+        f3 = torch.from_numpy(inputs.to_blocks(w, B, supp)).cuda()
+        f1 = f3[:, :1].contiguous()
+        o1 = torch.zeros((len(xs), 1, B, B, B), device="cuda")
+        o3 = torch.zeros((len(xs), 3, B, B, B), device="cuda")
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+        def timed_ms(fn, reps=20):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            tot = 0.0
+            for _ in range(reps):
+                flush.fill_(1.0)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fn()
+                b.record()
+                torch.cuda.synchronize()
+                tot += a.elapsed_time(b)
+            return tot / reps
+        ms1 = timed_ms(lambda: p1.execute([f1], [o1]))
+        ms3 = timed_ms(lambda: p3.execute([f3], [o3]))
+        return (lambda: p3.execute([f3], [o3])), [p3], 3 * len(xs) * B ** 3, {
+            "workload": "vector (3-component) Poisson solve D_supp -> D_xsoln of the 256^3 Re=500 ring, "
+                        "against the scalar solve on the same blocks",
+            "supp_blocks": int(len(supp)), "xsoln_blocks": int(len(xs)), "scalar_ms": round(ms1, 4),
+            "vector_ms": round(ms3, 4), "vector_to_scalar_ratio": round(ms3 / ms1, 3),
+            "points": "3 x D_xsoln points per vector solve"}, [t, p1]
     if name == "ragged64":
         fs = inputs.ragged_ring_sources(nsolve=64)
         solves, srcs, dsts, pts = [], [], [], 0
@@ -519,7 +560,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="ring128", choices=["ring128", "blobs32", "if128", "rk256", "rk256_b", "rk256_c", "rk256_refresh",
-                                                                 "ragged64"],
+                                                                 "vecscal256", "ragged64"],
                     help="ring128 is the headline workload; the others print their own throughput")
     args = ap.parse_args()
     if args.warmup < 3:
