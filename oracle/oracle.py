@@ -31,7 +31,7 @@ __all__ = [
     "op_Dbar", "op_L", "op_N", "residual_L", "WATSON_W", "num_threads", "SCHEME_A", "SCHEME_B", "SCHEME_C",
     "SCHEMES", "shifted_tableau",
     "block_mask", "ifactor_masked", "poisson_masked", "if_herk_step", "lgf_points", "ifactor_tail", "rk_qmax",
-    "vor2vel", "ring_diagnostics",
+    "vor2vel", "ring_diagnostics", "regrid_weights",
 ]
 
 # Watson's integral for the simple cubic lattice, closed form (Watson 1939):
@@ -433,6 +433,34 @@ def ring_diagnostics(u, dx, origin_cells, xs_mask, int_mask):
     K = float((uc * xw).sum() * dv)
     J = float((uc * wc).sum() * dv)
     return {"I": I, "K": K, "E": E, "J": J, "X": X}
+
+
+def regrid_weights(u, uinf, dx, xs_mask, B, blocks, origin_blocks):
+    """Block weights of Sec. 5 eq. weight_fun on D_xsoln: W = max(mu / mu_global,
+    nu / nu_global), mu = max |C u| and nu = max |G^T N~(u + u_inf)| over the block,
+    from w = M C M u and q = -M G^T M N~(M (u + u_inf)) (algorithm summary, step 1).
+    Reading of 'contaminated by finite boundary errors': w and q are zeroed on the
+    cells whose 3x3x3 neighbourhood leaves D_xsoln (the mask edge's spurious layer).
+    blocks: [n][3] block coordinates (the dense box's block (0,0,0) at origin_blocks);
+    returns W per listed block."""
+    xs = xs_mask
+    w = op_C(u * xs, dx) * xs
+    uf = (u + np.asarray(uinf, dtype=float).reshape(3, 1, 1, 1)) * xs
+    q = -op_Gt(op_N(uf, dx) * xs, dx) * xs
+    inner = xs.copy()
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dxx in (-1, 0, 1):
+                inner &= shift(shift(shift(xs, 0, dxx), 1, dy), 2, dz)
+    w = w * inner
+    q = q * inner
+    mu, nu = [], []
+    for bx, by, bz in (np.asarray(blocks) - np.asarray(origin_blocks)).tolist():
+        sl = (slice(bz * B, (bz + 1) * B), slice(by * B, (by + 1) * B), slice(bx * B, (bx + 1) * B))
+        mu.append(np.abs(w[(slice(None),) + sl]).max())
+        nu.append(np.abs(q[sl]).max())
+    mu, nu = np.array(mu), np.array(nu)
+    return np.maximum(mu / mu.max(), nu / nu.max() if nu.max() > 0 else 0.0 * nu)
 
 
 def vor2vel(u, masks, cube, dx):

@@ -117,3 +117,24 @@ def test_vor2vel_recovers_divergence_free_velocity():
     u1 = O.vor2vel(u0, cs["masks"], O.lgf_cube(64), cs["dx"])
     so = cs["masks"]["soln"]
     assert np.abs(u1[:, so] - u0[:, so]).max() < 1e-10 * np.abs(u0).max()
+
+
+def test_regrid_weights():
+    """Weights of eq. weight_fun on D_xsoln: in [0, 1] with maximum 1; the blocks that
+    hold the ring's vorticity outweigh the buffer; a field that vanishes except on the
+    mask-edge layer (the contaminated cells) has zero vorticity weight."""
+    cs = small_case(B=8, amp=3.0)
+    B, org = cs["B"], cs["origin"]
+    W = O.regrid_weights(cs["u0"], (0.05, -0.02, 0.1), cs["dx"], cs["masks"]["xsoln"], B, cs["xsoln"], org)
+    assert W.max() == pytest.approx(1.0) and W.min() >= 0.0
+    soln = set(map(tuple, cs["soln"].tolist()))
+    ws = [W[i] for i, b in enumerate(cs["xsoln"].tolist()) if tuple(b) in soln]
+    wb = [W[i] for i, b in enumerate(cs["xsoln"].tolist()) if tuple(b) not in soln]
+    assert min(ws) > max(wb)
+    # a uniform field: its masked curl and Lamb-vector divergence live only on the mask
+    # edge's cell layer, which the weights leave out
+    xs = cs["masks"]["xsoln"]
+    uni = np.ones_like(cs["u0"]) * np.array([0.3, -0.2, 0.5]).reshape(3, 1, 1, 1) * xs
+    with np.errstate(invalid="ignore"):
+        W2 = O.regrid_weights(uni, (0.1, 0.0, 0.0), cs["dx"], xs, B, cs["xsoln"], org)
+    assert np.all(np.isnan(W2) | (W2 == 0))
