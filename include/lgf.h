@@ -239,6 +239,20 @@ lgf_status lgf_rk_refresh(lgf_plan *p, const float *u_in, float *u_out, void *st
  * (App. D, with the truncation error read as the kernel mass beyond that depth); 0 if not
  * even one step does; -1 (lgf_last_error set) for a bad argument.  Host only. */
 int lgf_rk_qmax(const lgf_plan *p, double eps);
+/* Grid update query of Sec. 5 (eq. d_supp with the weight function eq. weight_fun): from
+ * w = M C M u and q = -M G^T M N~(M (u + uinf)) on D_xsoln, with the cells within 3 cells
+ * of the outside of D_xsoln zeroed (the mask edge's contaminated layer), the blocks with
+ * W = max(max|w| / max_global|w|, max|q| / max_global|q|) > eps_supp.  Writes up to `capacity`
+ * block coordinates ([n][3], host) in D_xsoln order and returns their count (which may exceed
+ * capacity); -1 on a bad argument.  Synchronises `stream`. */
+int lgf_rk_regrid_blocks(lgf_plan *p, const float *u, const double uinf[3], double eps_supp, int32_t *blocks_out,
+                         int capacity, void *stream);
+/* Vorticity copy and velocity refresh onto a new grid (Sec. 5 grid update): w = C u_from on
+ * `from`'s D_xsoln, zeroed within 3 cells of its outside (the mask edge's spurious vortex
+ * sheet), copied to the D_supp blocks of `to` (every one of which must lie in
+ * `from`'s D_xsoln, else LGF_ERR_ARG), then u_to = Vor2Vel(w) on `to`'s D_xsoln
+ * (eq. vel_refresh).  Same B and dx.  Synchronises `stream`. */
+lgf_status lgf_rk_transfer(lgf_plan *from, const float *u_from, lgf_plan *to, float *u_to, void *stream);
 /* Ring diagnostics of Sec. 6 (eq. int_quantities) of the velocity perturbation u (device
  * [n_xsoln][3][B^3]) over D_soln, with w = C u on edges: out[0..2] impulse I = 1/2 sum x cross w,
  * out[3] K = sum u . (x cross w), out[4] enstrophy E = 1/2 sum |w|^2, out[5] helicity

@@ -440,7 +440,9 @@ def regrid_weights(u, uinf, dx, xs_mask, B, blocks, origin_blocks):
     nu / nu_global), mu = max |C u| and nu = max |G^T N~(u + u_inf)| over the block,
     from w = M C M u and q = -M G^T M N~(M (u + u_inf)) (algorithm summary, step 1).
     Reading of 'contaminated by finite boundary errors': w and q are zeroed on the
-    cells whose 3x3x3 neighbourhood leaves D_xsoln (the mask edge's spurious layer).
+    cells within 3 cells of the outside of D_xsoln.  The masked curl is spurious on the
+    last cell layer; N~ and G^T each reach one cell further, so q carries that error
+    3 cells deep.
     blocks: [n][3] block coordinates (the dense box's block (0,0,0) at origin_blocks);
     returns W per listed block."""
     xs = xs_mask
@@ -448,10 +450,12 @@ def regrid_weights(u, uinf, dx, xs_mask, B, blocks, origin_blocks):
     uf = (u + np.asarray(uinf, dtype=float).reshape(3, 1, 1, 1)) * xs
     q = -op_Gt(op_N(uf, dx) * xs, dx) * xs
     inner = xs.copy()
-    for dz in (-1, 0, 1):
-        for dy in (-1, 0, 1):
-            for dxx in (-1, 0, 1):
-                inner &= shift(shift(shift(xs, 0, dxx), 1, dy), 2, dz)
+    for _ in range(3):  # erode by one cell (26-neighbourhood) three times
+        prev = inner.copy()
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dxx in (-1, 0, 1):
+                    inner &= shift(shift(shift(prev, 0, dxx), 1, dy), 2, dz)
     w = w * inner
     q = q * inner
     mu, nu = [], []

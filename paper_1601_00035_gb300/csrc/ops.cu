@@ -345,6 +345,78 @@ __global__ void __launch_bounds__(B *B) k_diag(const float *__restrict__ u, cons
     }
 }
 
+// Regrid weights' raw maxima (Sec. 5 eq. weight_fun): mu[b] = max |w| (3 edge
+// components) and nu[b] = max |q| (cells) over block b, leaving out the cells within
+// RIM = 3 cells of a block outside the set: the masked curl is spurious on the last
+// layer, and N~ and G^T carry that one cell further each.
+template <int B>
+__global__ void __launch_bounds__(B *B) k_block_max(const float *__restrict__ w, const float *__restrict__ q,
+                                                    const int *__restrict__ nbr27, float *__restrict__ mu,
+                                                    float *__restrict__ nu)
+{
+    const int blk = blockIdx.x;
+    __shared__ int nb[27];
+    __shared__ float red[2][B * B / 32];
+    if (threadIdx.x < 27) nb[threadIdx.x] = nbr27[blk * 27 + threadIdx.x];
+    __syncthreads();
+    const int x = threadIdx.x % B, y = threadIdx.x / B;
+    const size_t b3 = (size_t)B * B * B;
+    float m1 = 0.f, m2 = 0.f;
+    for (int z = 0; z < B; z++) {
+        bool inner = true;
+        constexpr int RIM = 3;
+        for (int oz = (z < RIM ? -1 : 0); oz <= (z >= B - RIM ? 1 : 0); oz++)
+            for (int oy = (y < RIM ? -1 : 0); oy <= (y >= B - RIM ? 1 : 0); oy++)
+                for (int ox = (x < RIM ? -1 : 0); ox <= (x >= B - RIM ? 1 : 0); ox++)
+                    if (nb[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)] < 0) inner = false;
+        if (!inner) continue;
+        const size_t o = (size_t)z * B * B + y * B + x;
+#pragma unroll
+        for (int c = 0; c < 3; c++) m1 = fmaxf(m1, fabsf(__ldg(w + ((size_t)blk * 3 + c) * b3 + o)));
+        m2 = fmaxf(m2, fabsf(__ldg(q + (size_t)blk * b3 + o)));
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        m1 = fmaxf(m1, __shfl_down_sync(0xffffffffu, m1, off));
+        m2 = fmaxf(m2, __shfl_down_sync(0xffffffffu, m2, off));
+    }
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    if (lane == 0) {
+        red[0][warp] = m1;
+        red[1][warp] = m2;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        float m = 0.f;
+        for (int i = 0; i < B * B / 32; i++) m = fmaxf(m, red[threadIdx.x][i]);
+        (threadIdx.x == 0 ? mu : nu)[blk] = m;
+    }
+}
+
+// Zero a vector field on the cells within RIM = 3 cells of a block outside the set
+// (the mask edge's contaminated layer; the same cells the regrid weights leave out).
+template <int B>
+__global__ void __launch_bounds__(B *B) k_zero_rim(float *__restrict__ f, const int *__restrict__ nbr27)
+{
+    const int blk = blockIdx.x;
+    __shared__ int nb[27];
+    if (threadIdx.x < 27) nb[threadIdx.x] = nbr27[blk * 27 + threadIdx.x];
+    __syncthreads();
+    const int x = threadIdx.x % B, y = threadIdx.x / B;
+    const size_t b3 = (size_t)B * B * B;
+    constexpr int RIM = 3;
+    for (int z = 0; z < B; z++) {
+        bool inner = true;
+        for (int oz = (z < RIM ? -1 : 0); oz <= (z >= B - RIM ? 1 : 0); oz++)
+            for (int oy = (y < RIM ? -1 : 0); oy <= (y >= B - RIM ? 1 : 0); oy++)
+                for (int ox = (x < RIM ? -1 : 0); ox <= (x >= B - RIM ? 1 : 0); ox++)
+                    if (nb[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)] < 0) inner = false;
+        if (inner) continue;
+        const size_t o = (size_t)z * B * B + y * B + x;
+#pragma unroll
+        for (int c = 0; c < 3; c++) f[((size_t)blk * 3 + c) * b3 + o] = 0.f;
+    }
+}
+
 // out = sum_t c_t x_t over n floats (up to 4 terms; null x_t skipped).  out may
 // alias an input (each element is read and written by the same thread), so no
 // __restrict__ and no read-only-cache loads here.
@@ -442,6 +514,35 @@ lgf_status diag_launch(int B, int n_soln, const int *d_nbr27, const int *d_coord
         return LGF_ERR_ARG;
     }
     LGF_LAUNCH_CHECK("diagnostics");
+    return LGF_OK;
+}
+
+lgf_status block_max_launch(int B, int nblk, const int *d_nbr27, const float *w, const float *q, float *mu, float *nu,
+                            cudaStream_t s)
+{
+    if (B == 8)
+        k_block_max<8><<<nblk, 64, 0, s>>>(w, q, d_nbr27, mu, nu);
+    else if (B == 16)
+        k_block_max<16><<<nblk, 256, 0, s>>>(w, q, d_nbr27, mu, nu);
+    else {
+        set_error("operators support B in {8, 16} (got %d)", B);
+        return LGF_ERR_ARG;
+    }
+    LGF_LAUNCH_CHECK("block_max");
+    return LGF_OK;
+}
+
+lgf_status zero_rim_launch(int B, int nblk, const int *d_nbr27, float *f, cudaStream_t s)
+{
+    if (B == 8)
+        k_zero_rim<8><<<nblk, 64, 0, s>>>(f, d_nbr27);
+    else if (B == 16)
+        k_zero_rim<16><<<nblk, 256, 0, s>>>(f, d_nbr27);
+    else {
+        set_error("operators support B in {8, 16} (got %d)", B);
+        return LGF_ERR_ARG;
+    }
+    LGF_LAUNCH_CHECK("zero_rim");
     return LGF_OK;
 }
 

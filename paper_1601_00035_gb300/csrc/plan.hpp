@@ -123,6 +123,11 @@ lgf_status op_launch(int op, int B, int nblk, const int *d_nbr27, const unsigned
 lgf_status lincomb_launch(float *out, int64_t n, const float *x0, double c0, const float *x1, double c1,
                           const float *x2, double c2, const float *x3, double c3, cudaStream_t s);
 lgf_status gather_launch(const float *in, float *out, const int *d_idx, int n, int block_floats, cudaStream_t s);
+// per-block maxima of |w| (3 components) and |q| off the mask-edge layer (regrid weights)
+lgf_status block_max_launch(int B, int nblk, const int *d_nbr27, const float *w, const float *q, float *mu, float *nu,
+                            cudaStream_t s);
+// zero a vector field on the mask edge's contaminated layer (3 cells)
+lgf_status zero_rim_launch(int B, int nblk, const int *d_nbr27, float *f, cudaStream_t s);
 // ring diagnostics sums over D_soln (the first n_soln blocks): 15 FP64 accumulators
 lgf_status diag_launch(int B, int n_soln, const int *d_nbr27, const int *d_coords, const float *u, const float *w,
                        double dx, double *d_acc, cudaStream_t s);
@@ -153,6 +158,8 @@ struct RkPlan {
     int *d_nbr27 = nullptr;
     int *d_coords = nullptr;   // [n_x][3] block coordinates
     double *d_acc = nullptr;   // diagnostics accumulators
+    float *d_mu = nullptr;     // [2][n_x] regrid maxima
+    int *d_tidx = nullptr;     // [n_soln] transfer gather indices
     unsigned char *d_soln_keep = nullptr;
     int *d_supp_idx = nullptr;
     float *work = nullptr;

@@ -66,6 +66,8 @@ void free_rk(RkPlan *r)
     cudaFree(r->d_nbr27);
     cudaFree(r->d_coords);
     cudaFree(r->d_acc);
+    cudaFree(r->d_mu);
+    cudaFree(r->d_tidx);
     cudaFree(r->d_soln_keep);
     cudaFree(r->d_supp_idx);
     cudaFree(r->work);
@@ -179,7 +181,9 @@ lgf_status lgf_rk_plan(const lgf_rk_desc *d, void *stream, lgf_plan **out)
     }
     if ((st = alloc_upload(&r->d_nbr27, nbr, r->bytes)) != LGF_OK) return fail(st);
     if ((st = alloc_upload(&r->d_coords, xs, r->bytes)) != LGF_OK) return fail(st);
-    if (cudaMalloc(&r->d_acc, 15 * sizeof(double)) != cudaSuccess) {
+    if (cudaMalloc(&r->d_acc, 15 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&r->d_mu, 2 * (size_t)nx * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&r->d_tidx, (size_t)nsoln * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         set_error("lgf_rk_plan: allocation failed");
         return fail(LGF_ERR_OOM);
@@ -406,6 +410,25 @@ lgf_status lgf_rk_step(lgf_plan *p, const float *u_in, float *u_out, const doubl
     return LGF_OK;
 }
 
+}  // extern "C"
+
+namespace lgf {
+// u_out = M^xsoln C^T M^xsoln (-M^xsoln L^{-1} M^supp w), w on D_supp in the plan's staging buffer
+lgf_status rk_vor2vel_supp(lgf_plan *p, float *u_out, cudaStream_t s)
+{
+    RkPlan *r = p->rk;
+    float *ax = r->work + r->vec;
+    float *ws = r->work + 8 * r->vec + r->scal_x + r->scal_s;
+    const float *srcs[1] = {ws};
+    float *dsts[1] = {ax};
+    LGF_TRY(lgf_conv_execute(r->poisson3, srcs, dsts, s));
+    return timed(p->prof, "op_curl_t", s,
+                 [&] { return op_launch(1, r->B, r->n_x, r->d_nbr27, nullptr, ax, u_out, r->dx, 1.0, nullptr, s); });
+}
+}  // namespace lgf
+
+extern "C" {
+
 lgf_status lgf_rk_refresh(lgf_plan *p, const float *u_in, float *u_out, void *stream)
 {
     clear_error();
@@ -414,18 +437,14 @@ lgf_status lgf_rk_refresh(lgf_plan *p, const float *u_in, float *u_out, void *st
     RkPlan *r = p->rk;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t V = r->vec;
-    float *wx = r->work, *ax = wx + V;                          // w and a on D_xsoln
+    float *wx = r->work;                                         // w on D_xsoln
     float *ws = r->work + 8 * V + r->scal_x + r->scal_s;         // w on D_supp
     const int B3 = r->B * r->B * r->B;
     Profiler &pr = p->prof;
     // w = M^xsoln C M^xsoln u; a = -M^xsoln L^{-1} M^supp w; u' = M^xsoln C^T M^xsoln a (eq. vel_refresh)
     LGF_TRY(timed(pr, "op_curl", s, [&] { return op_launch(0, r->B, r->n_x, r->d_nbr27, nullptr, u_in, wx, r->dx, 1.0, nullptr, s); }));
     LGF_TRY(timed(pr, "gather_supp", s, [&] { return gather_launch(wx, ws, r->d_supp_idx, r->n_soln, 3 * B3, s); }));
-    const float *srcs[1] = {ws};
-    float *dsts[1] = {ax};
-    LGF_TRY(lgf_conv_execute(r->poisson3, srcs, dsts, s));
-    LGF_TRY(timed(pr, "op_curl_t", s, [&] { return op_launch(1, r->B, r->n_x, r->d_nbr27, nullptr, ax, u_out, r->dx, 1.0, nullptr, s); }));
-    return LGF_OK;
+    return rk_vor2vel_supp(p, u_out, s);
 }
 
 int lgf_rk_qmax(const lgf_plan *p, double eps)
@@ -477,6 +496,81 @@ lgf_status lgf_rk_diagnostics(lgf_plan *p, const float *u, double out[9], void *
         for (int a = 0; a < 3; a++) v += h[6 + 3 * a + b] * dv * I[a];
         out[6 + b] = ii > 0.0 ? v / ii : 0.0;
     }
+    return LGF_OK;
+}
+
+int lgf_rk_regrid_blocks(lgf_plan *p, const float *u, const double uinf[3], double eps_supp, int32_t *blocks_out,
+                         int capacity, void *stream)
+{
+    clear_error();
+    if (!p || !u || !uinf || p->kind != LGF_PLAN_RK || !(eps_supp > 0.0) || capacity < 0) {
+        set_error("lgf_rk_regrid_blocks: bad argument");
+        return -1;
+    }
+    RkPlan *r = p->rk;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t V = r->vec;
+    float *w = r->work, *nl = r->work + V, *q = r->work + 8 * V;  // slot 0, slot 1, the d^ scalars
+    auto ok = [](lgf_status st) { return st == LGF_OK; };
+    // w = M C M u;  q = -M G^T M N~(M (u + u_inf)) (algorithm summary, step 1)
+    if (!ok(op_launch(0, r->B, r->n_x, r->d_nbr27, nullptr, u, w, r->dx, 1.0, nullptr, s)) ||
+        !ok(op_launch(4, r->B, r->n_x, r->d_nbr27, nullptr, u, nl, r->dx, 1.0, uinf, s)) ||
+        !ok(op_launch(2, r->B, r->n_x, r->d_nbr27, nullptr, nl, q, r->dx, 1.0, nullptr, s)) ||
+        !ok(block_max_launch(r->B, r->n_x, r->d_nbr27, w, q, r->d_mu, r->d_mu + r->n_x, s)))
+        return -1;
+    std::vector<float> h(2 * (size_t)r->n_x);
+    if (cudaMemcpyAsync(h.data(), r->d_mu, h.size() * sizeof(float), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("lgf_rk_regrid_blocks: copy failed");
+        return -1;
+    }
+    float mg = 0.f, ng = 0.f;
+    for (int b = 0; b < r->n_x; b++) {
+        mg = std::max(mg, h[b]);
+        ng = std::max(ng, h[r->n_x + b]);
+    }
+    int n = 0;
+    for (int b = 0; b < r->n_x; b++) {
+        // eq. weight_fun: W = max(mu / mu_global, nu / nu_global), kept where W > eps_supp
+        const double W = std::max(mg > 0.f ? (double)h[b] / mg : 0.0, ng > 0.f ? (double)h[r->n_x + b] / ng : 0.0);
+        if (W > eps_supp) {
+            if (n < capacity) std::copy(r->xsoln.begin() + 3 * (size_t)b, r->xsoln.begin() + 3 * (size_t)b + 3,
+                                        blocks_out + 3 * (size_t)n);
+            n++;
+        }
+    }
+    return n;
+}
+
+lgf_status lgf_rk_transfer(lgf_plan *from, const float *u_from, lgf_plan *to, float *u_to, void *stream)
+{
+    clear_error();
+    LGF_CHECK_ARG(from && to && u_from && u_to && from->kind == LGF_PLAN_RK && to->kind == LGF_PLAN_RK,
+                  "lgf_rk_transfer: needs two RK plans and buffers");
+    RkPlan *a = from->rk, *b = to->rk;
+    LGF_CHECK_ARG(a->B == b->B && a->dx == b->dx, "lgf_rk_transfer: plans differ in B or dx");
+    cudaStream_t s = (cudaStream_t)stream;
+    // index in `from`'s D_xsoln of every block of `to`'s D_supp (the vorticity copy of
+    // the grid update; new D_supp blocks come from the old D_xsoln)
+    std::unordered_map<int64_t, int> pos;
+    for (int i = 0; i < a->n_x; i++) pos.emplace(pack3(a->xsoln[3 * i], a->xsoln[3 * i + 1], a->xsoln[3 * i + 2]), i);
+    std::vector<int> idx(b->n_soln);
+    for (int i = 0; i < b->n_soln; i++) {
+        auto it = pos.find(pack3(b->xsoln[3 * i], b->xsoln[3 * i + 1], b->xsoln[3 * i + 2]));
+        LGF_CHECK_ARG(it != pos.end(), "lgf_rk_transfer: D_supp block %d of the new plan is outside the old D_xsoln", i);
+        idx[i] = it->second;
+    }
+    LGF_CUDA_TRY(cudaMemcpyAsync(b->d_tidx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    const int B3 = a->B * a->B * a->B;
+    float *w_old = a->work;
+    float *ws_new = b->work + 8 * b->vec + b->scal_x + b->scal_s;
+    LGF_TRY(op_launch(0, a->B, a->n_x, a->d_nbr27, nullptr, u_from, w_old, a->dx, 1.0, nullptr, s));
+    // the old mask edge's spurious vortex sheet must not enter the new D_supp
+    LGF_TRY(zero_rim_launch(a->B, a->n_x, a->d_nbr27, w_old, s));
+    LGF_TRY(gather_launch(w_old, ws_new, b->d_tidx, b->n_soln, 3 * B3, s));
+    LGF_TRY(rk_vor2vel_supp(to, u_to, s));
+    // the host index array must outlive the copy
+    LGF_CUDA_TRY(cudaStreamSynchronize(s));
     return LGF_OK;
 }
 

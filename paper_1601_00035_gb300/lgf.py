@@ -108,6 +108,11 @@ _SIGS = {
                                   ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_void_p]),
     "lgf_rk_diagnostics": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                           ctypes.c_void_p]),
+    "lgf_rk_regrid_blocks": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.c_double, ctypes.POINTER(ctypes.c_int32), ctypes.c_int,
+                                            ctypes.c_void_p]),
+    "lgf_rk_transfer": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
     "lgf_plan_destroy": (None, [ctypes.c_void_p]),
     "lgf_last_error": (ctypes.c_char_p, []),
     "lgf_version": (ctypes.c_char_p, []),
@@ -342,6 +347,22 @@ class RKPlan:
         if q < 0:
             raise LGFError(LGF_ERR_ARG, load().lgf_last_error().decode())
         return int(q)
+
+    def regrid_blocks(self, u, uinf=(0.0, 0.0, 0.0), eps_supp: float = 1e-6, stream=None) -> np.ndarray:
+        """New D_supp from the weights of the current field (lgf_rk_regrid_blocks)."""
+        L = load()
+        ui = (ctypes.c_double * 3)(*[float(v) for v in uinf])
+        cap = L.lgf_rk_block_count(self._h, 0)
+        out = np.zeros((max(cap, 1), 3), dtype=np.int32)
+        n = L.lgf_rk_regrid_blocks(self._h, _ptr(u), ui, float(eps_supp),
+                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), cap, _stream(stream))
+        if n < 0:
+            raise LGFError(LGF_ERR_ARG, L.lgf_last_error().decode())
+        return out[:n].copy()
+
+    def transfer_to(self, u_from, other: "RKPlan", u_to, stream=None):
+        """Vorticity copy + velocity refresh onto another plan's grid (lgf_rk_transfer)."""
+        _check(load().lgf_rk_transfer(self._h, _ptr(u_from), other._h, _ptr(u_to), _stream(stream)))
 
     def diagnostics(self, u, stream=None) -> dict:
         """Ring diagnostics over D_soln (lgf_rk_diagnostics): I, K, E, J, X."""
