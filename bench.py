@@ -181,9 +181,10 @@ def ncu_traffic(kernel: str):
     return float(m.group(1)) if m else None
 
 
-def cpu_oracle_rate(f, src_c, target_seconds: float, rng_seed: int = 11):
-    """Time the FP64 direct sum (the oracle, as it stands) on a bounded sample of
-    target points of the same workload; returns (Mpoints/s, points, seconds, threads)."""
+def oracle_sampler(f, src_c, rng_seed: int = 11):
+    """The FP64 direct sum (the oracle, as it stands) prepared on the workload's
+    sources; returns (run, ncomp, threads), run(n) timing n random target
+    points per component in seconds."""
     import oracle as O
     from paper_1601_00035_gb300 import inputs
     cube = O.lgf_cube(127)
@@ -202,11 +203,26 @@ def cpu_oracle_rate(f, src_c, target_seconds: float, rng_seed: int = 11):
             O.direct_conv(cube, sp, -sv, tgt)
         return time.perf_counter() - t0
 
-    t_small = run(24)
-    n = max(24, int(24 * target_seconds / max(t_small, 1e-3)))
+    return run, len(comps), O.num_threads()
+
+
+def calibrate(run, target_seconds: float) -> int:
+    """Sample size whose run takes about target_seconds: grow the sample until
+    the fixed cost of a call is amortised, then scale."""
+    n, t = 24, run(24)
+    while t < target_seconds / 16 and n < 1 << 22:
+        n *= 4
+        t = run(n)
+    return max(24, int(n * target_seconds / max(t, 1e-3)))
+
+
+def cpu_oracle_rate(f, src_c, target_seconds: float, rng_seed: int = 11):
+    """Mpoints/s of the oracle on one bounded sample of about target_seconds;
+    returns (Mpoints/s, points, seconds, threads)."""
+    run, nc, thr = oracle_sampler(f, src_c, rng_seed)
+    n = calibrate(run, target_seconds)
     dt = run(n)
-    pts = n * len(comps)
-    return pts / dt / 1e6, pts, dt, O.num_threads()
+    return n * nc / dt / 1e6, n * nc, dt, thr
 
 
 def bench_reference(args):
@@ -214,21 +230,24 @@ def bench_reference(args):
     if r != 0:
         return 0
     f, src_c, dst_c, cfg = workload()
+    # each step a bounded sample; the whole run stays within a few minutes
     per_step = float(os.environ.get("LGF_REF_STEP_SECONDS", "2.0"))
-    times, pts_tot = [], 0
+    per_step = min(per_step, max(0.25, 150.0 / (args.steps + args.warmup)))
+    run, nc, thr = oracle_sampler(f, src_c, rng_seed=100)
+    n = calibrate(run, per_step)
+    times = []
     for i in range(args.warmup + args.steps):
-        rate, pts, dt, thr = cpu_oracle_rate(f, src_c, per_step, rng_seed=100 + i)
+        dt = run(n)
         if i >= args.warmup:
             times.append(dt)
-            pts_tot += pts
     total = sum(times)
-    value = pts_tot / total / 1e6
+    value = n * nc * len(times) / total / 1e6
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
-                             "sample": "FP64 direct sum at %d random target points x 3 components per step "
-                                       "(~%.0f s of host work each)" % (pts_tot // len(times) // 3, per_step)},
+                             "sample": "FP64 direct sum at %d random target points x %d components per step "
+                                       "(~%.2f s of host work each)" % (n, nc, per_step)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -382,6 +401,16 @@ def aux_workload(name, lgf, torch):
         dst = torch.zeros_like(src)
         return (lambda: p.execute([src], [dst])), [p], 32 ** 3, {
             "workload": "scalar Poisson, 32^3 box, 3 Gaussian blobs, 16^3 blocks"}, [t]
+    if name == "blobs32_f64":
+        # the same solve with FP64 data, transforms and spectrum (plan precision 1)
+        f = inputs.gaussian_blobs(32)
+        c = inputs.block_grid(f.shape, B)
+        t = lgf.Table(lgf.LAPLACE7, max_offset=lgf.required_max_offset(c, c, B))
+        p = lgf.Plan(t, [lgf.Solve(B, 1, c, c)], precision=1)
+        src = torch.from_numpy(inputs.to_blocks(f, B, c, dtype=np.float64)).cuda()
+        dst = torch.zeros_like(src)
+        return (lambda: p.execute_f64([src], [dst])), [p], 32 ** 3, {
+            "workload": "scalar Poisson in FP64, 32^3 box, 3 Gaussian blobs, 16^3 blocks"}, [t]
     if name == "if128":
         u = inputs.two_ring_velocity()
         c = inputs.block_grid(u.shape[1:], B)
@@ -543,8 +572,8 @@ def bench_aux(args):
     tot = sum(v[1] for v in kt.values()) or 1.0
     line = {"metric": "Mpoints/s (%s)" % args.workload, "value": round(pts * args.steps / (dev_ms / 1e3) / 1e6, 1),
             "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(dev_ms / args.steps, 5), "higher_is_better": True, "dtype": "f32",
-            "data": "synthetic", "config": cfg,
+            "ms_per_step": round(dev_ms / args.steps, 5), "higher_is_better": True,
+            "dtype": "f64" if args.workload.endswith("_f64") else "f32", "data": "synthetic", "config": cfg,
             "kernels": {k: {"launches": v[0], "ms_per_launch": round(v[1] / max(v[0], 1), 5),
                             "share": round(v[1] / tot, 4)} for k, v in kt.items()}}
     print(json.dumps(line))
@@ -559,8 +588,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="ring128", choices=["ring128", "blobs32", "if128", "rk256", "rk256_b", "rk256_c", "rk256_refresh",
-                                                                 "vecscal256", "ragged64"],
+    ap.add_argument("--workload", default="ring128",
+                    choices=["ring128", "blobs32", "blobs32_f64", "if128", "rk256", "rk256_b", "rk256_c",
+                             "rk256_refresh", "vecscal256", "ragged64"],
                     help="ring128 is the headline workload; the others print their own throughput")
     args = ap.parse_args()
     if args.warmup < 3:

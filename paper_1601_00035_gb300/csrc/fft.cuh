@@ -19,6 +19,7 @@
 // w = exp(-2 pi i/N), inverse the conjugate (unnormalised).
 #pragma once
 #include <cmath>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -141,6 +142,130 @@ __device__ __forceinline__ void butterfly(cx<T> &u, cx<T> &v, int k, int len)
     a.x = fma(-v.y, ws, fma(v.x, w.x, u.x));
     a.y = fma(v.y, w.x, fma(v.x, ws, u.y));
     const cx<T> b = {fma((T)2, u.x, -a.x), fma((T)2, u.y, -a.y)};
+    u = a;
+    v = b;
+}
+
+// ---------------------------------------------------------------------------
+// Two lines per lane.  A packed value holds the same quantity of two lines
+// (low half: the first line, high half: the second) and every arithmetic step
+// is one .f32x2 instruction (add, sub, mul, fma; sm_100 and later), so a lane
+// runs both lines' transforms with one instruction stream.  cx<f32x2> is then
+// {(re_a, re_b), (im_a, im_b)}.
+struct f32x2 {
+    unsigned long long r;
+};
+}  // namespace fft
+// 16-byte aligned, so that a packed complex value moves with one 128-bit access
+template <>
+struct __align__(16) cx<fft::f32x2> {
+    fft::f32x2 x, y;
+};
+namespace fft {
+__device__ __forceinline__ f32x2 pk2(float lo, float hi)
+{
+    f32x2 o;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(o.r) : "f"(lo), "f"(hi));
+    return o;
+}
+__device__ __forceinline__ void unpk2(f32x2 a, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.r));
+}
+__device__ __forceinline__ f32x2 operator+(f32x2 a, f32x2 b)
+{
+    f32x2 o;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(o.r) : "l"(a.r), "l"(b.r));
+    return o;
+}
+__device__ __forceinline__ f32x2 operator-(f32x2 a, f32x2 b)
+{
+    f32x2 o;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(o.r) : "l"(a.r), "l"(b.r));
+    return o;
+}
+__device__ __forceinline__ f32x2 operator*(f32x2 a, f32x2 b)
+{
+    f32x2 o;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(o.r) : "l"(a.r), "l"(b.r));
+    return o;
+}
+__device__ __forceinline__ f32x2 fma(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 o;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(o.r) : "l"(a.r), "l"(b.r), "l"(c.r));
+    return o;
+}
+__device__ __forceinline__ f32x2 bc2(float c) { return pk2(c, c); }
+
+// cos(2 pi j / 64), j = 0..16 (the other octants by symmetry), as literals so
+// that the packed twiddle constants of an unrolled DFT are immediates
+__host__ __device__ constexpr double cos64_q(int j)
+{
+    constexpr double t[17] = {1.0, 0.99518472667219693, 0.98078528040323043, 0.95694033573220882,
+                              0.92387953251128674, 0.88192126434835505, 0.83146961230254524, 0.77301045336273699,
+                              0.70710678118654757, 0.63439328416364549, 0.55557023301960229, 0.47139673682599781,
+                              0.38268343236508984, 0.29028467725446233, 0.19509032201612833, 0.09801714032956077,
+                              0.0};
+    return t[j];
+}
+__host__ __device__ constexpr double cos64(int j)
+{
+    j &= 63;
+    return j <= 16 ? cos64_q(j) : (j <= 32 ? -cos64_q(32 - j) : (j <= 48 ? -cos64_q(j - 32) : cos64_q(64 - j)));
+}
+__host__ __device__ constexpr double sin64(int j) { return cos64(j + 48); }
+
+// complex products on packed values (a w and a conj(w))
+__device__ __forceinline__ cx<f32x2> cmul(cx<f32x2> a, cx<f32x2> w)
+{
+    return {a.x * w.x - a.y * w.y, fma(a.x, w.y, a.y * w.x)};
+}
+__device__ __forceinline__ cx<f32x2> cmulc(cx<f32x2> a, cx<f32x2> w)
+{
+    return {fma(a.y, w.y, a.x * w.x), a.y * w.x - a.x * w.y};
+}
+
+// The butterfly of the scalar path on packed values.  Negated constants are
+// separate immediates, so no step needs a negation instruction.
+template <bool INV>
+__device__ __forceinline__ void butterfly(cx<f32x2> &u, cx<f32x2> &v, int k, int len)
+{
+    cx<f32x2> a, b;
+    if (k == 0) {
+        a = u + v;
+        b = u - v;
+    } else if (4 * k == len) {  // w v = (v.y, -v.x) forward, (-v.y, v.x) inverse
+        if (!INV) {
+            a = {u.x + v.y, u.y - v.x};
+            b = {u.x - v.y, u.y + v.x};
+        } else {
+            a = {u.x - v.y, u.y + v.x};
+            b = {u.x + v.y, u.y - v.x};
+        }
+    } else if (8 * k == len || 8 * k == 3 * len) {
+        // w v = h (sx Tx, sy Ty) with Tx, Ty sums or differences of v.x, v.y
+        const bool s = 8 * k == len;
+        f32x2 tx, ty;
+        float sx = 1.f, sy = 1.f;
+        if (!INV) {
+            if (s) { tx = v.x + v.y; ty = v.y - v.x; }
+            else { tx = v.y - v.x; ty = v.x + v.y; sy = -1.f; }
+        } else {
+            if (s) { tx = v.x - v.y; ty = v.x + v.y; }
+            else { tx = v.x + v.y; ty = v.x - v.y; sx = -1.f; }
+        }
+        const float h = 0.70710678118654752440f;
+        a = {fma(bc2(sx * h), tx, u.x), fma(bc2(sy * h), ty, u.y)};
+        b = {fma(bc2(-sx * h), tx, u.x), fma(bc2(-sy * h), ty, u.y)};
+    } else {
+        // applied twiddle (wr, ws): w_len^k forward, its conjugate inverse
+        const int jj = k * (64 / len);
+        const float wr = (float)cos64(jj);
+        const float ws = INV ? (float)sin64(jj) : -(float)sin64(jj);
+        a = {fma(v.y, bc2(-ws), fma(v.x, bc2(wr), u.x)), fma(v.x, bc2(ws), fma(v.y, bc2(wr), u.y))};
+        b = {fma(v.y, bc2(ws), fma(v.x, bc2(-wr), u.x)), fma(v.x, bc2(-ws), fma(v.y, bc2(-wr), u.y))};
+    }
     u = a;
     v = b;
 }
@@ -407,7 +532,10 @@ __host__ __device__ constexpr bool in_lower_half(int e)
 template <typename T>
 __device__ __forceinline__ cx<T> tw_global_at(const void *tw_global, int idx)
 {
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (std::is_same<T, f32x2>::value) {
+        const float2 w = __ldg((const float2 *)tw_global + idx);
+        return {bc2(w.x), bc2(w.y)};
+    } else if constexpr (sizeof(T) == 8) {
         const double2 w = __ldg((const double2 *)tw_global + idx);
         return {w.x, w.y};
     } else {

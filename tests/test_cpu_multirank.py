@@ -73,5 +73,6 @@ def test_reference_arm_other_rank_does_no_work(monkeypatch):
         raise AssertionError("rank 1 must not run the oracle")
 
     monkeypatch.setattr(bench, "cpu_oracle_rate", boom)
+    monkeypatch.setattr(bench, "oracle_sampler", boom)
     monkeypatch.setattr(bench, "workload", boom)
     assert bench.bench_reference(Args()) == 0
