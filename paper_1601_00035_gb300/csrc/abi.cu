@@ -387,6 +387,8 @@ static lgf_status plan_poisson(lgf_plan *p, const lgf_table *t, const lgf_solve_
         g.B = d.B;
         g.lB = d.B == 8 ? 3 : (d.B == 16 ? 4 : 5);
         g.ncomp = d.ncomp;
+        g.c0 = 0;
+        g.nc = d.ncomp;
         ps.nsrc = d.n_src;
         ps.ndst = d.n_dst;
         ps.dx = d.dx;
@@ -501,30 +503,38 @@ static lgf_status plan_poisson(lgf_plan *p, const lgf_table *t, const lgf_solve_
         LGF_TRY(dalloc(&p->d_wsB64, maxB, p->bytes));
         return LGF_OK;
     }
-    if (n_solves == 1) {
+    if (n_solves == 1 && p->solves[0].g.ncomp == 1) {
         LGF_TRY(dalloc(&p->d_wsA, maxA, p->bytes));
         LGF_TRY(dalloc(&p->d_wsB, maxB, p->bytes));
         p->wsA = maxA;
         p->wsB = maxB;
         return LGF_OK;
     }
-    // independent solves run on up to 8 worker streams; longest-first greedy
-    // assignment on the workspace size as the cost estimate
-    const int nl = std::min(8, n_solves);
-    std::vector<int> order(n_solves);
-    for (int i = 0; i < n_solves; i++) order[i] = i;
+    // Several independent units, one per (solve, component): each runs the five
+    // passes on its own worker stream (up to 8), so the passes of different
+    // units overlap (a memory-bound pass beside the compute-bound z pass).
+    // Longest-first greedy assignment, the workspace size as the cost estimate.
+    for (int i = 0; i < n_solves; i++) {
+        const PoissonSolve &q = p->solves[i];
+        for (int c = 0; c < q.g.ncomp; c++)
+            p->units.push_back({i, c, 1, 0, q.elemsA / q.g.ncomp, q.elemsB / q.g.ncomp});
+    }
+    const int nu = (int)p->units.size();
+    const int nl = std::min(8, nu);
+    std::vector<int> order(nu);
+    for (int i = 0; i < nu; i++) order[i] = i;
     std::sort(order.begin(), order.end(), [&](int a, int b) {
-        return p->solves[a].elemsA + p->solves[a].elemsB > p->solves[b].elemsA + p->solves[b].elemsB;
+        return p->units[a].elemsA + p->units[a].elemsB > p->units[b].elemsA + p->units[b].elemsB;
     });
     std::vector<double> load(nl, 0.0);
     std::vector<size_t> la(nl, 0), lb(nl, 0);
-    p->solve_lane.assign(n_solves, 0);
     for (int i : order) {
+        lgf_plan::Unit &u = p->units[i];
         const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-        p->solve_lane[i] = k;
-        load[k] += (double)(p->solves[i].elemsA + p->solves[i].elemsB);
-        la[k] = std::max(la[k], p->solves[i].elemsA);
-        lb[k] = std::max(lb[k], p->solves[i].elemsB);
+        u.lane = k;
+        load[k] += (double)(u.elemsA + u.elemsB);
+        la[k] = std::max(la[k], u.elemsA);
+        lb[k] = std::max(lb[k], u.elemsB);
     }
     p->lanes.assign(nl, nullptr);
     p->lane_done.assign(nl, nullptr);
@@ -682,13 +692,26 @@ static lgf_status run_poisson(lgf_plan *p, const float *const *src, float *const
             LGF_TRY(poisson_launch(p->solves[i].g, src[i], dst[i], p->d_wsA, p->d_wsB, s, prof));
         return LGF_OK;
     }
+    auto unit_geom = [&](const lgf_plan::Unit &u) {
+        Geom g = p->solves[u.solve].g;
+        g.c0 = u.c0;
+        g.nc = u.nc;
+        return g;
+    };
+    if (prof && prof->on) {
+        // per-pass event timing: the units run one after another on the
+        // caller's stream, so that each pass is timed alone
+        for (const auto &u : p->units)
+            LGF_TRY(poisson_launch(unit_geom(u), src[u.solve], dst[u.solve], p->lane_wsA[u.lane], p->lane_wsB[u.lane], s,
+                                   prof));
+        return LGF_OK;
+    }
     // fork: every lane waits for the work queued so far on the caller's stream
     LGF_CUDA_TRY(cudaEventRecord(p->fork, s));
     for (size_t k = 0; k < p->lanes.size(); k++) LGF_CUDA_TRY(cudaStreamWaitEvent(p->lanes[k], p->fork, 0));
-    for (size_t i = 0; i < p->solves.size(); i++) {
-        const int k = p->solve_lane[i];
-        LGF_TRY(poisson_launch(p->solves[i].g, src[i], dst[i], p->lane_wsA[k], p->lane_wsB[k], p->lanes[k], prof));
-    }
+    for (const auto &u : p->units)
+        LGF_TRY(poisson_launch(unit_geom(u), src[u.solve], dst[u.solve], p->lane_wsA[u.lane], p->lane_wsB[u.lane],
+                               p->lanes[u.lane], nullptr));
     // join: the caller's stream waits for every lane
     for (size_t k = 0; k < p->lanes.size(); k++) {
         LGF_CUDA_TRY(cudaEventRecord(p->lane_done[k], p->lanes[k]));

@@ -13,7 +13,8 @@
 // Axis order everywhere: 0 = x, 1 = y, 2 = z.  Positions in cells.
 namespace lgf {
 struct Geom {
-    int B, ncomp;
+    int B, ncomp;      // block edge; components per point (the stride of the block layout)
+    int c0, nc;        // components c0 .. c0+nc-1 in this launch (grid.y = nc; workspaces hold nc)
     int lB;            // log2(B)
     int S0[3], Es[3];  // source bounding box: origin, extent (multiples of B)
     int T0[3], Et[3];  // target bounding box
@@ -204,7 +205,13 @@ struct lgf_plan {
     std::vector<cudaEvent_t> lane_done;
     cudaEvent_t fork = nullptr;
     std::vector<lgf::cx<float> *> lane_wsA, lane_wsB;
-    std::vector<int> solve_lane;
+    // FP32 work units: one per (solve, component) when a plan has more than one
+    // unit, so that the components of a vector solve also run on separate lanes
+    struct Unit {
+        int solve, c0, nc, lane;
+        size_t elemsA, elemsB;
+    };
+    std::vector<Unit> units;
     double *d_acc = nullptr;  // residual accumulators
     // IF
     int B = 0, ncomp = 0, nblk = 0, R = 0;

@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_f
     __shared__ cx<T> tw[fft::tw_size<N>()];
     __shared__ int lut_s[TL::LS * NBX];
     fft::load_twiddles<N, T>(tw, tw_g);
-    const int c = blockIdx.y;
+    const int c = blockIdx.y;  // workspace component; g.c0 + c in the source layout
     const int j = threadIdx.x % TL::G, l = threadIdx.x / TL::G;
     const int nrows = g.Es[1] * g.Es[2];
     const int B = g.B;
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_f
             if (row_ok && pos < g.Es[0]) {
                 const int blk = lut[pos >> lB];
                 if (blk >= 0) {
-                    const T *p = src + ((size_t)(blk * g.ncomp + c) << (3 * lB)) + in_blk + (pos & mB);
+                    const T *p = src + ((size_t)(blk * g.ncomp + g.c0 + c) << (3 * lB)) + in_blk + (pos & mB);
                     v[e] = {__ldg(p), __ldg(p + B)};
                 }
             }
@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_i
     __shared__ int lut_d[TL::LS * NBX];
     fft::load_twiddles<N, T>(tw, tw_g);
     constexpr int KX = N / 2 + 1;
-    const int c = blockIdx.y;
+    const int c = blockIdx.y;  // workspace component; g.c0 + c in the target layout
     const int j = threadIdx.x % TL::G, l = threadIdx.x / TL::G;
     const int nrows = g.Et[1] * g.Et[2];
     const int lB = g.lB;
@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_i
         if (xt < g.Et[0]) {
             const int blk = lut[xt >> lB];
             if (blk >= 0) {
-                T *p = dst + ((size_t)(blk * g.ncomp + c) << (3 * lB)) + out_blk + (xt & mB);
+                T *p = dst + ((size_t)(blk * g.ncomp + g.c0 + c) << (3 * lB)) + out_blk + (xt & mB);
                 p[0] = v[e].x;
                 p[B] = v[e].y;
             }
@@ -491,7 +491,7 @@ lgf_status launch_x_fwd(const Geom &g, const T *src, cx<T> *out, cudaStream_t s)
 {
     using TL = TileX<N, T>;
     const int nrows = g.Es[1] * g.Es[2];
-    dim3 grid(ceil_div(nrows / 2, TL::LS), g.ncomp);
+    dim3 grid(ceil_div(nrows / 2, TL::LS), g.nc);
     LGF_CUDA_TRY(launch_pdl(k_x_fwd<N, T>, grid, dim3(TL::threads), s, g, src, out, tw_table<T>()));
     return LGF_OK;
 }
@@ -500,7 +500,7 @@ lgf_status launch_line(const Geom &g, const cx<T> *in, cx<T> *out, cudaStream_t 
 {
     using TL = TileY<N, T>;
     const int planes = MODE == 0 ? g.Es[2] : (MODE == 1 ? g.N[1] : g.Et[2]);
-    dim3 grid(ceil_div(g.KX * planes, TL::LS), g.ncomp);
+    dim3 grid(ceil_div(g.KX * planes, TL::LS), g.nc);
     LGF_CUDA_TRY(launch_pdl(k_line<N, MODE, T>, grid, dim3(TL::threads), s, g, in, out, tw_table<T>()));
     return LGF_OK;
 }
@@ -508,7 +508,7 @@ template <int N>
 lgf_status launch_zmid2(const Geom &g, const cx<float> *in, cx<float> *out, cudaStream_t s)
 {
     using TL = TileZ2<N>;
-    dim3 grid(ceil_div(g.KX * g.N[1] / 2, TL::LS), g.ncomp);
+    dim3 grid(ceil_div(g.KX * g.N[1] / 2, TL::LS), g.nc);
     LGF_CUDA_TRY(launch_pdl(k_zmid2<N>, grid, dim3(TL::threads), s, g, in, out, tw_table<float>()));
     return LGF_OK;
 }
@@ -520,7 +520,7 @@ lgf_status launch_x_inv(const Geom &g, const cx<T> *in, T *dst, cudaStream_t s)
 {
     using TL = TileX<N, T>;
     const int nrows = g.Et[1] * g.Et[2];
-    dim3 grid(ceil_div(nrows / 2, TL::LS), g.ncomp);
+    dim3 grid(ceil_div(nrows / 2, TL::LS), g.nc);
     LGF_CUDA_TRY(launch_pdl(k_x_inv<N, T>, grid, dim3(TL::threads), s, g, in, dst, tw_table<T>()));
     return LGF_OK;
 }
