@@ -683,35 +683,64 @@ lgf_status lgf_plan_workspace_bytes(const lgf_plan *p, size_t *bytes)
     return LGF_OK;
 }
 
+// Host buffers of lgf_conv_execute_host: each unit copies its own component
+// slice in before its passes and out after them, on its own stream, so the
+// copies of one unit overlap the passes of the others.
+struct HostIO {
+    const float *const *src;
+    float *const *dst;
+};
+
+// components c0 .. c0+nc-1 of a [n][ncomp][B^3] block array (2-D copy: one row per block)
+static lgf_status copy_slice(float *d, const float *h, const PoissonSolve &q, int n, int c0, int nc, bool to_device,
+                             cudaStream_t s)
+{
+    const size_t B3 = (size_t)q.g.B * q.g.B * q.g.B, pitch = (size_t)q.g.ncomp * B3 * sizeof(float);
+    const size_t off = (size_t)c0 * B3;
+    if (to_device)
+        LGF_CUDA_TRY(cudaMemcpy2DAsync(d + off, pitch, h + off, pitch, nc * B3 * sizeof(float), n,
+                                       cudaMemcpyHostToDevice, s));
+    else
+        LGF_CUDA_TRY(cudaMemcpy2DAsync((float *)h + off, pitch, d + off, pitch, nc * B3 * sizeof(float), n,
+                                       cudaMemcpyDeviceToHost, s));
+    return LGF_OK;
+}
+
 static lgf_status run_poisson(lgf_plan *p, const float *const *src, float *const *dst, cudaStream_t s,
-                              bool capturing = false)
+                              bool capturing = false, const HostIO *host = nullptr)
 {
     Profiler *prof = capturing ? nullptr : &p->prof;
-    if (p->lanes.empty()) {
-        for (size_t i = 0; i < p->solves.size(); i++)
-            LGF_TRY(poisson_launch(p->solves[i].g, src[i], dst[i], p->d_wsA, p->d_wsB, s, prof));
-        return LGF_OK;
-    }
     auto unit_geom = [&](const lgf_plan::Unit &u) {
         Geom g = p->solves[u.solve].g;
         g.c0 = u.c0;
         g.nc = u.nc;
         return g;
     };
+    // one unit on stream st: host copy in, five passes, host copy out
+    auto run_unit = [&](const lgf_plan::Unit &u, cx<float> *wa, cx<float> *wb, cudaStream_t st,
+                        Profiler *pr) -> lgf_status {
+        const PoissonSolve &q = p->solves[u.solve];
+        if (host) LGF_TRY(copy_slice((float *)src[u.solve], host->src[u.solve], q, q.nsrc, u.c0, u.nc, true, st));
+        LGF_TRY(poisson_launch(unit_geom(u), src[u.solve], dst[u.solve], wa, wb, st, pr));
+        if (host) LGF_TRY(copy_slice(dst[u.solve], host->dst[u.solve], q, q.ndst, u.c0, u.nc, false, st));
+        return LGF_OK;
+    };
+    if (p->lanes.empty()) {
+        for (size_t i = 0; i < p->solves.size(); i++)
+            LGF_TRY(run_unit({(int)i, 0, p->solves[i].g.ncomp, 0, 0, 0}, p->d_wsA, p->d_wsB, s, prof));
+        return LGF_OK;
+    }
     if (prof && prof->on) {
         // per-pass event timing: the units run one after another on the
         // caller's stream, so that each pass is timed alone
-        for (const auto &u : p->units)
-            LGF_TRY(poisson_launch(unit_geom(u), src[u.solve], dst[u.solve], p->lane_wsA[u.lane], p->lane_wsB[u.lane], s,
-                                   prof));
+        for (const auto &u : p->units) LGF_TRY(run_unit(u, p->lane_wsA[u.lane], p->lane_wsB[u.lane], s, prof));
         return LGF_OK;
     }
     // fork: every lane waits for the work queued so far on the caller's stream
     LGF_CUDA_TRY(cudaEventRecord(p->fork, s));
     for (size_t k = 0; k < p->lanes.size(); k++) LGF_CUDA_TRY(cudaStreamWaitEvent(p->lanes[k], p->fork, 0));
     for (const auto &u : p->units)
-        LGF_TRY(poisson_launch(unit_geom(u), src[u.solve], dst[u.solve], p->lane_wsA[u.lane], p->lane_wsB[u.lane],
-                               p->lanes[u.lane], nullptr));
+        LGF_TRY(run_unit(u, p->lane_wsA[u.lane], p->lane_wsB[u.lane], p->lanes[u.lane], nullptr));
     // join: the caller's stream waits for every lane
     for (size_t k = 0; k < p->lanes.size(); k++) {
         LGF_CUDA_TRY(cudaEventRecord(p->lane_done[k], p->lanes[k]));
@@ -806,19 +835,11 @@ lgf_status lgf_conv_execute_host(lgf_plan *p, const float *const *src, float *co
     for (size_t i = 0; i < p->solves.size(); i++) {
         const PoissonSolve &q = p->solves[i];
         LGF_CHECK_ARG(src[i] && dst[i], "lgf_conv_execute_host: NULL buffer for solve %zu", i);
-        const size_t B3 = (size_t)q.g.B * q.g.B * q.g.B;
-        LGF_CUDA_TRY(cudaMemcpyAsync(q.d_stage_src, src[i], (size_t)q.nsrc * q.g.ncomp * B3 * sizeof(float),
-                                     cudaMemcpyHostToDevice, s));
         ds[i] = q.d_stage_src;
         dd[i] = q.d_stage_dst;
     }
-    LGF_TRY(run_poisson(p, ds.data(), dd.data(), s));
-    for (size_t i = 0; i < p->solves.size(); i++) {
-        const PoissonSolve &q = p->solves[i];
-        const size_t B3 = (size_t)q.g.B * q.g.B * q.g.B;
-        LGF_CUDA_TRY(cudaMemcpyAsync(dst[i], q.d_stage_dst, (size_t)q.ndst * q.g.ncomp * B3 * sizeof(float),
-                                     cudaMemcpyDeviceToHost, s));
-    }
+    const HostIO host{src, dst};
+    LGF_TRY(run_poisson(p, ds.data(), dd.data(), s, false, &host));
     LGF_CUDA_TRY(cudaStreamSynchronize(s));
     return LGF_OK;
 }
