@@ -170,21 +170,41 @@ __global__ void __launch_bounds__(B *B) k_nonlinear(const float *__restrict__ in
     if (threadIdx.x < 27) nb[threadIdx.x] = nbr27[blk * 27 + threadIdx.x];
     __syncthreads();
     const float uinf[3] = {u0, u1, u2};
-    // f plane zp (-1 .. B) into its slot
-    auto load_f = [&](int zp) {
+    // f plane zp (-1 .. B): fetch_f reads it from global memory into registers
+    // (each thread holds at most 2 points x 3 components: (B + 2)^2 < 2 B^2),
+    // commit_f stores it into its slot, so a plane's loads can be in flight
+    // while the previous plane is computed
+    constexpr int PT = (H * H + B * B - 1) / (B * B);
+    static_assert(PT <= 2, "halo plane points per thread");
+    float pre[PT][3];
+    auto fetch_f = [&](int zp) {
         const int dz = zp < 0 ? -1 : (zp >= B ? 1 : 0);
         const int lz = zp - dz * B;
-        float *dst = &Fs[(zp + 1) % 3][0][0];
-        for (int idx = threadIdx.x; idx < H * H; idx += B * B) {
+#pragma unroll
+        for (int t = 0; t < PT; t++) {
+            const int idx = threadIdx.x + t * B * B;
             const int hx = idx % H - 1, hy = idx / H - 1;
             const int dx = hx < 0 ? -1 : (hx >= B ? 1 : 0);
             const int dy = hy < 0 ? -1 : (hy >= B ? 1 : 0);
-            const int n = nb[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)];
+            const int n = idx < H * H ? nb[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] : -1;
             const size_t base = n >= 0 ? ((size_t)n * 3 * B + lz) * B * B + (hy - dy * B) * B + (hx - dx * B) : 0;
 #pragma unroll
-            for (int c = 0; c < 3; c++)
-                dst[c * H * H + idx] = n >= 0 ? __ldg(in + base + (size_t)c * B * B * B) + uinf[c] : 0.f;
+            for (int c = 0; c < 3; c++) pre[t][c] = n >= 0 ? __ldg(in + base + (size_t)c * B * B * B) + uinf[c] : 0.f;
         }
+    };
+    auto commit_f = [&](int zp) {
+        float *dst = &Fs[(zp + 1) % 3][0][0];
+#pragma unroll
+        for (int t = 0; t < PT; t++) {
+            const int idx = threadIdx.x + t * B * B;
+            if (idx < H * H)
+#pragma unroll
+                for (int c = 0; c < 3; c++) dst[c * H * H + idx] = pre[t][c];
+        }
+    };
+    auto load_f = [&](int zp) {
+        fetch_f(zp);
+        commit_f(zp);
     };
     auto F = [&](int c, int px, int py, int pz) -> float { return Fs[(pz + 1) % 3][c][(py + 1) * H + (px + 1)]; };
     // e plane zp (-1 .. B-1): e^c(p) = f^r(p) - f^r(p + e_s) + f^s(p + e_r) - f^s(p), (c, r, s) cyclic
@@ -205,6 +225,7 @@ __global__ void __launch_bounds__(B *B) k_nonlinear(const float *__restrict__ in
     load_f(1);
     __syncthreads();
     make_e(-1);
+    fetch_f(2);  // B >= 8
     for (int z = 0; z < B; z++) {
         make_e(z);  // reads f planes z, z + 1
         __syncthreads();
@@ -223,7 +244,10 @@ __global__ void __launch_bounds__(B *B) k_nonlinear(const float *__restrict__ in
             out[((size_t)(blk * 3 + q) * B + z) * B * B + y * B + x] = v * 0.25f * coef;
         }
         __syncthreads();  // plane z - 1 of f and of e are no longer read
-        if (z + 2 <= B) load_f(z + 2);
+        if (z + 2 <= B) {
+            commit_f(z + 2);                  // into plane z - 1's slot
+            if (z + 3 <= B) fetch_f(z + 3);   // in flight during plane z + 1
+        }
         __syncthreads();
     }
 }
