@@ -158,11 +158,14 @@ __global__ void __launch_bounds__(B *B) k_nonlinear(const float *__restrict__ in
     __shared__ int nb[27];
     __shared__ float Fs[3][3][H * H];   // [slot][component][(y+1) H + (x+1)]
     __shared__ float Es[2][3][HE * HE]; // [slot][component][(y+1) HE + (x+1)]
-    const int blk = blockIdx.x;
+    // thread block (blk, zs) walks output planes z0 .. z1 - 1 of block blk
+    constexpr int ZS = B >= 16 ? 2 : 1;
+    const int blk = blockIdx.x / ZS;
+    const int z0 = (blockIdx.x % ZS) * (B / ZS), z1 = z0 + B / ZS;
     const int x = threadIdx.x % B, y = threadIdx.x / B;
     const bool keep = out_keep == nullptr || out_keep[blk];
     if (!keep) {
-        for (int z = 0; z < B; z++)
+        for (int z = z0; z < z1; z++)
 #pragma unroll
             for (int q = 0; q < 3; q++) out[((size_t)(blk * 3 + q) * B + z) * B * B + y * B + x] = 0.f;
         return;
@@ -220,13 +223,13 @@ __global__ void __launch_bounds__(B *B) k_nonlinear(const float *__restrict__ in
         }
     };
     auto Ev = [&](int c, int px, int py, int pz) -> float { return Es[(pz + 1) % 2][c][(py + 1) * HE + (px + 1)]; };
-    load_f(-1);
-    load_f(0);
-    load_f(1);
+    load_f(z0 - 1);
+    load_f(z0);
+    load_f(z0 + 1);
     __syncthreads();
-    make_e(-1);
-    fetch_f(2);  // B >= 8
-    for (int z = 0; z < B; z++) {
+    make_e(z0 - 1);
+    fetch_f(z0 + 2);  // B / ZS >= 8
+    for (int z = z0; z < z1; z++) {
         make_e(z);  // reads f planes z, z + 1
         __syncthreads();
         const int o[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};  // unit offsets e_q
@@ -244,9 +247,9 @@ __global__ void __launch_bounds__(B *B) k_nonlinear(const float *__restrict__ in
             out[((size_t)(blk * 3 + q) * B + z) * B * B + y * B + x] = v * 0.25f * coef;
         }
         __syncthreads();  // plane z - 1 of f and of e are no longer read
-        if (z + 2 <= B) {
-            commit_f(z + 2);                  // into plane z - 1's slot
-            if (z + 3 <= B) fetch_f(z + 3);   // in flight during plane z + 1
+        if (z + 2 <= z1) {
+            commit_f(z + 2);                   // into plane z - 1's slot
+            if (z + 3 <= z1) fetch_f(z + 3);   // in flight during plane z + 1
         }
         __syncthreads();
     }
@@ -486,7 +489,8 @@ lgf_status op_launch(int op, int B, int nblk, const int *d_nbr27, const unsigned
     const float cf = (float)coef;
 #define LGF_OPCASE(BB, OPV)                                                                                     \
     if constexpr (OPV == 4)                                                                                     \
-        k_nonlinear<BB><<<nblk, BB * BB, 0, s>>>(in, out, d_nbr27, d_keep, inv_dx, cf, u0, u1, u2);          \
+        k_nonlinear<BB><<<nblk * (BB >= 16 ? 2 : 1), BB * BB, 0, s>>>(in, out, d_nbr27, d_keep, inv_dx, cf, u0,  \
+                                                                       u1, u2);                                \
     else                                                                                                        \
         k_op<BB, OPV><<<nblk, BB * BB, 0, s>>>(in, out, d_nbr27, d_keep, inv_dx, cf, u0, u1, u2);
 #define LGF_OPSWITCH(BB)                                                                                        \
