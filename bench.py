@@ -317,6 +317,17 @@ def bench_gpu(args):
     torch.cuda.synchronize()
     clocks = clock_summary(sampler) if r == 0 else None
 
+    # the plain form for comparison (outside the timed region): one component per
+    # solve, the three solves one after another on one stream, no graph
+    plain = lgf.Plan(table, [lgf.Solve(B, 1, src_c, dst_c, scale=-1.0)])
+    srcs1 = [d_src[:, q:q + 1].contiguous() for q in range(3)]
+    dsts1 = [torch.zeros((len(dst_c), 1, B, B, B), device="cuda") for _ in range(3)]
+
+    def run_plain():
+        for a, b in zip(srcs1, dsts1):
+            plain.execute([a], [b])
+    plain_ms = _timed_ms(torch, run_plain)
+
     # e2e: host (pinned) buffers through lgf_conv_execute_host, copies included
     h_src = torch.from_numpy(f).pin_memory()
     h_dst = torch.empty((len(dst_c), 3, B, B, B), dtype=torch.float32).pin_memory()
@@ -361,6 +372,8 @@ def bench_gpu(args):
                "sample": "FP64 direct sum (oracle) at %d random target points x 3 components, %.1f s" % (pts // 3, dt)}
     cfg = dict(cfg)
     cfg.update({"fft_grid": geom["N"], "execution": "one stream per component, launch sequence replayed as a CUDA graph",
+                "plain_ms": round(plain_ms, 4), "batched_over_plain": round(plain_ms / (dev_ms / args.steps), 3),
+                "plain": "one component per solve, three solves one after another on one stream, no graph",
                 "l2": "256 MiB buffer rewritten between timed steps (outside the events)",
                 "precision": "FP32 data and FFTs; FP64 LGF table and kernel spectrum",
                 "parity": "rel L2 <= 1e-6 vs FP64 direct sum (tests/test_gpu_poisson.py)"})
@@ -433,9 +446,31 @@ def aux_workload(name, lgf, torch):
             for pl, y in zip(plans, ys):
                 pl.ifactor(x, y)
             pp.execute([fs], [fd])
+        # the plain form for comparison: one component per application, separate
+        # launches on one stream, no graph
+        plans1 = [lgf.Plan(tb, [lgf.Solve(B, 1, c, None)]) for tb in tabs]
+        x1 = [x[:, q:q + 1].contiguous() for q in range(3)]
+        y1 = [torch.zeros_like(x1[0]) for _ in range(3)]
+
+        def run_plain():
+            for pl in plans1:
+                for q in range(3):
+                    pl.ifactor(x1[q], y1[q])
+            pp.execute([fs], [fd])
+        plain_ms = _timed_ms(torch, run_plain)
+        g = torch.cuda.CUDAGraph()
+        step()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            step()
+        batched_ms = _timed_ms(torch, g.replay)
         return step, plans + [pp], 3 * x.numel() + 32 ** 3, {
             "workload": "integrating factor on a 3 x 128^3 two-ring velocity, alpha in {0.05, 0.2, 1.0} "
-                        "(R = 7, 9, 15), plus the 32^3 Poisson solve, one captured graph per step"}, tabs + [tp]
+                        "(R = 7, 9, 15), plus the 32^3 Poisson solve, one captured graph per step",
+            "plain_ms": round(plain_ms, 4), "batched_ms": round(batched_ms, 4),
+            "batched_over_plain": round(plain_ms / batched_ms, 3),
+            "plain": "one component per integrating-factor application (9 applications) and the Poisson "
+                     "solve, separate launches on one stream, no graph"}, tabs + [tp]
     if name in ("rk256", "rk256_b", "rk256_c", "rk256_refresh"):
         n, R0c, dcells = 256, 50.0, 10.0
         dx = 1.0 / R0c                      # R0 = 1, Gamma = 1
@@ -521,10 +556,40 @@ def aux_workload(name, lgf, torch):
         K = max(lgf.required_max_offset(s_.src_blocks, s_.dst_blocks, B) for s_ in solves)
         t = lgf.Table(lgf.LAPLACE7, max_offset=K)
         p = lgf.Plan(t, solves, use_graph=True)
+        # the plain form for comparison: one plan per solve, executed one after
+        # another on one stream, no graph
+        plain = [lgf.Plan(t, [s_]) for s_ in solves]
+
+        def run_plain():
+            for pl, a, b in zip(plain, srcs, dsts):
+                pl.execute([a], [b])
+        plain_ms = _timed_ms(torch, run_plain)
+        batched_ms = _timed_ms(torch, lambda: p.execute(srcs, dsts))
         return (lambda: p.execute(srcs, dsts)), [p], pts, {
             "workload": "ragged batch of 64 scalar ring solves, edges 24..192 (log-uniform), one captured graph",
-            "points": "sum of e^3 over the batch"}, [t]
+            "points": "sum of e^3 over the batch",
+            "plain_ms": round(plain_ms, 4), "batched_ms": round(batched_ms, 4),
+            "batched_over_plain": round(plain_ms / batched_ms, 3),
+            "plain": "64 single-solve plans executed one after another on one stream, no graph"}, [t]
     raise ValueError(name)
+
+
+def _timed_ms(torch, fn, reps=20):
+    """Mean device time of fn in ms (CUDA events, 256 MiB L2 flush before each rep)."""
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(reps):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / reps
 
 
 def bench_aux(args):
