@@ -149,6 +149,7 @@ def pass_bytes(plan_geom):
 
 
 def geometry(src_c, dst_c, ncomp):
+    from paper_1601_00035_gb300.lgf import fft_length
     s, t = np.asarray(src_c), np.asarray(dst_c)
     Es = [int((s[:, a].max() - s[:, a].min() + 1) * B) for a in range(3)]
     Et = [int((t[:, a].max() - t[:, a].min() + 1) * B) for a in range(3)]
@@ -157,10 +158,7 @@ def geometry(src_c, dst_c, ncomp):
         S0, S1 = s[:, a].min() * B, (s[:, a].max() + 1) * B - 1
         T0, T1 = t[:, a].min() * B, (t[:, a].max() + 1) * B - 1
         m = max(abs(T0 - S1), abs(T1 - S0))
-        n = 16
-        while n < max(2 * m + 2, 2 * (S1 - S0 + 1)):
-            n *= 2
-        N.append(n)
+        N.append(fft_length(max(2 * m + 2, 2 * (S1 - S0 + 1))))
     return {"Es": Es, "Et": Et, "N": N, "ncomp": ncomp, "nsrc": len(s), "ndst": len(t)}
 
 

@@ -1,5 +1,5 @@
-// 1-D complex FFTs of power-of-two length N (16..1024) with the data held in
-// registers, for batches of lines processed by one thread block.
+// 1-D complex FFTs of length N = 2^k (16..1024) or 3 * 2^k (96, 192, 384) with
+// the data held in registers, for batches of lines processed by one thread block.
 //
 // A line is transformed by G lanes (threads); lane j holds E = N / G elements.
 // Algorithm: Stockham autosort, mixed radix R_0 .. R_{S-1} (product N).  In
@@ -307,11 +307,93 @@ __device__ __forceinline__ void levels(cx<T> *a)
 
 // In-register DFT of length R on a[OFF .. OFF+R), natural order in and out
 // (radix-2 decimation in time).  HALF: inputs R/2 .. R-1 are known to be zero.
+__host__ __device__ constexpr bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// cos(2 pi j / 48), j = 0..12 (the other quadrants by symmetry): the twiddles
+// of the in-register DFTs whose length has a factor 3 (R divides 48)
+__host__ __device__ constexpr double cos48_q(int j)
+{
+    constexpr double t[13] = {1.0, 0.99144486137381041114, 0.96592582628906828675, 0.92387953251128675613,
+                              0.86602540378443864676, 0.79335334029123516458, 0.70710678118654752440,
+                              0.60876142900872063942, 0.5, 0.38268343236508977173, 0.25881904510252076235,
+                              0.13052619222005159155, 0.0};
+    return t[j];
+}
+__host__ __device__ constexpr double cos48(int j)
+{
+    j = ((j % 48) + 48) % 48;
+    return j <= 12 ? cos48_q(j) : (j <= 24 ? -cos48_q(24 - j) : (j <= 36 ? -cos48_q(j - 24) : cos48_q(48 - j)));
+}
+__host__ __device__ constexpr double sin48(int j) { return cos48(j - 12); }
+
+// v times w_R^j = exp(-2 pi i j / R) (its conjugate for the inverse); R divides
+// 48, j compile-time.  Quarter turns are swaps, the rest complex products with
+// literal constants.
+template <bool INV, int R, typename T>
+__device__ __forceinline__ cx<T> twiddle48(cx<T> v, int j)
+{
+    j %= R;
+    if (j == 0) return v;
+    if (2 * j == R) return {-v.x, -v.y};
+    if (4 * j == R) return INV ? cx<T>{-v.y, v.x} : cx<T>{v.y, -v.x};
+    if (4 * j == 3 * R) return INV ? cx<T>{v.y, -v.x} : cx<T>{-v.y, v.x};
+    const int q = j * (48 / R);
+    const T c = (T)cos48(q), sn = INV ? (T)sin48(q) : -(T)sin48(q);  // w = c + i sn
+    return {::fma(v.x, c, -v.y * sn), ::fma(v.x, sn, v.y * c)};
+}
+
+// In-register DFT of length R = 3 M (M a power of two), natural order in and
+// out: the three stride-3 subsequences x[3 n + r] are transformed by the
+// radix-2 DFT of length M, then X[k + m M] = sum_r w_R^{r k} Y_r[k] w_3^{r m}
+// (a length-3 DFT per k < M).  HALF: inputs R/2 .. R-1 are zero, which leaves
+// the upper half of every subsequence zero.
+template <int R, bool INV, typename T, int OFF, bool HALF>
+__device__ __forceinline__ void dft_reg3(cx<T> *a)
+{
+    constexpr int M = R / 3;
+    static_assert(R == 3 * M && is_pow2(M) && 48 % R == 0, "R = 3 M, R divides 48");
+    cx<T> y[3][M];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int n = 0; n < M; n++) y[r][n] = a[OFF + 3 * n + r];
+    if constexpr (M > 1) {
+#pragma unroll
+        for (int r = 0; r < 3; r++) {
+            bitrev_perm<M, T, 0>(y[r]);
+            levels<M, INV, T, 0, HALF>(y[r]);
+        }
+    }
+    const T h = (T)0.5, s3 = (T)0.86602540378443864676;  // cos(pi/3), sin(pi/3)
+#pragma unroll
+    for (int k = 0; k < M; k++) {
+        const cx<T> b0 = y[0][k];
+        const cx<T> b1 = twiddle48<INV, R>(y[1][k], k);
+        const cx<T> b2 = twiddle48<INV, R>(y[2][k], 2 * k);
+        // length-3 DFT: X0 = b0 + b1 + b2, X1,2 = b0 - (b1 + b2)/2 -+ i sqrt3/2 (b1 - b2) (forward)
+        const cx<T> t1 = b1 + b2;
+        const cx<T> t2 = {::fma(-h, t1.x, b0.x), ::fma(-h, t1.y, b0.y)};
+        const cx<T> t3 = {s3 * (b1.x - b2.x), s3 * (b1.y - b2.y)};
+        a[OFF + k] = b0 + t1;
+        if (!INV) {
+            a[OFF + k + M] = {t2.x + t3.y, t2.y - t3.x};
+            a[OFF + k + 2 * M] = {t2.x - t3.y, t2.y + t3.x};
+        } else {
+            a[OFF + k + M] = {t2.x - t3.y, t2.y + t3.x};
+            a[OFF + k + 2 * M] = {t2.x + t3.y, t2.y - t3.x};
+        }
+    }
+}
+
 template <int R, bool INV, typename T, int OFF, bool HALF = false>
 __device__ __forceinline__ void dft_reg(cx<T> *a)
 {
-    bitrev_perm<R, T, OFF>(a);
-    levels<R, INV, T, OFF, HALF>(a);
+    if constexpr (is_pow2(R)) {
+        bitrev_perm<R, T, OFF>(a);
+        levels<R, INV, T, OFF, HALF>(a);
+    } else {
+        dft_reg3<R, INV, T, OFF, HALF>(a);
+    }
 }
 
 // G lanes per line, E = N / G elements per lane, radices (forward order).
@@ -346,6 +428,22 @@ template <>
 struct Plan<512> {
     static constexpr int G = 16, E = 32, S = 2;
     static constexpr int R[2] = {16, 32};
+};
+// lengths 3 * 2^k: one in-register radix has the factor 3
+template <>
+struct Plan<96> {
+    static constexpr int G = 4, E = 24, S = 2;
+    static constexpr int R[2] = {12, 8};
+};
+template <>
+struct Plan<192> {
+    static constexpr int G = 8, E = 24, S = 2;
+    static constexpr int R[2] = {24, 8};
+};
+template <>
+struct Plan<384> {
+    static constexpr int G = 16, E = 24, S = 3;
+    static constexpr int R[3] = {8, 6, 8};
 };
 template <>
 struct Plan<1024> {
@@ -527,7 +625,7 @@ __host__ __device__ constexpr bool in_lower_half(int e)
     return (e % R) * (N / R) < N / 2;
 }
 
-// Fill the shared twiddle array (tw_size<N>() entries) from the 1024-entry
+// Fill the shared twiddle array (tw_size<N>() entries) from the TW_MAX-entry
 // global table of the same precision (float2 for T = float, double2 for double).
 template <typename T>
 __device__ __forceinline__ cx<T> tw_global_at(const void *tw_global, int idx)
@@ -547,12 +645,13 @@ template <int N, bool INV, typename T, int s = 1>
 __device__ __forceinline__ void load_dir(cx<T> *tw_s, const void *tw_global)
 {
     if constexpr (s < Plan<N>::S) {
+        static_assert(TW_MAX % N == 0, "N divides the twiddle table length");
         constexpr int SC = TW_MAX / N;
         constexpr int R = radix<N, INV>(s), L = span<N, INV>(s), STEP = N / (R * L);
         cx<T> *ts = tw_s + tw_base<N>(INV) + tw_stage_off<N, INV>(s);
         for (int q = threadIdx.x; q < L * R; q += blockDim.x) {
             const int m = q / L, k = q - m * L;
-            ts[q] = tw_global_at<T>(tw_global, (m * k * STEP * SC) & (TW_MAX - 1));
+            ts[q] = tw_global_at<T>(tw_global, (m * k * STEP * SC) % TW_MAX);
         }
         load_dir<N, INV, T, s + 1>(tw_s, tw_global);
     }

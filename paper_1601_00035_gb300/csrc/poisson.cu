@@ -41,7 +41,7 @@ constexpr int lines_fit(int want, int pad)
 template <int N, typename T>
 struct TileY {
     static constexpr int G = Plan<N>::G;
-    static constexpr int LS32 = G == 1 ? 64 : (G >= 64 ? (N >= 1024 ? 4 : 8) : (G == 8 ? 32 : 16));
+    static constexpr int LS32 = G == 1 ? 64 : (G >= 64 ? (N >= 1024 ? 4 : 8) : (G <= 8 ? 256 / G : 16));
     static constexpr int LS = lines_fit<N, T>(sizeof(T) == 8 ? (G >= 64 ? 2 : LS32 / 2) : LS32, 1);
     static constexpr int LSP = LS + 1;
     static constexpr int threads = LS * G;
@@ -77,12 +77,12 @@ __device__ __forceinline__ const double *kh_of<double>(const Geom &g) { return g
 template <typename T>
 __device__ __forceinline__ T mul_of(const Geom &g) { return sizeof(T) == 8 ? (T)g.mul64 : (T)g.mul; }
 
-// v mod N in [0, N) for any int v (two's complement, N a power of two)
+// v mod N in [0, N) for -N <= v < 2N
 template <int N>
 __device__ __forceinline__ int wrap_mod(int v)
 {
-    static_assert((N & (N - 1)) == 0, "power of two");
-    return v & (N - 1);
+    if constexpr ((N & (N - 1)) == 0) return v & (N - 1);
+    else return v < 0 ? v + N : (v >= N ? v - N : v);
 }
 
 // ---------------------------------------------------------------------------
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_f
         const int rr = 2 * (blockIdx.x * TL::LS + ll);
         if (rr >= nrows) continue;
         const cx<T> zk = buf[sm.at(k, ll)];
-        const cx<T> zn = buf[sm.at((N - k) & (N - 1), ll)];
+        const cx<T> zn = buf[sm.at(k == 0 ? 0 : N - k, ll)];
         const size_t row = ((size_t)c * nrows + rr) * KX;
         const T h = (T)0.5;
         out[row + k] = {h * (zk.x + zn.x), h * (zk.y - zn.y)};
@@ -531,8 +531,11 @@ lgf_status launch_x_inv(const Geom &g, const cx<T> *in, T *dst, cudaStream_t s)
         case 16: { constexpr int NN = 16; CALL; } break;                                    \
         case 32: { constexpr int NN = 32; CALL; } break;                                    \
         case 64: { constexpr int NN = 64; CALL; } break;                                    \
+        case 96: { constexpr int NN = 96; CALL; } break;                                    \
         case 128: { constexpr int NN = 128; CALL; } break;                                  \
+        case 192: { constexpr int NN = 192; CALL; } break;                                  \
         case 256: { constexpr int NN = 256; CALL; } break;                                  \
+        case 384: { constexpr int NN = 384; CALL; } break;                                  \
         case 512: { constexpr int NN = 512; CALL; } break;                                  \
         case 1024:                                                                          \
             if constexpr (sizeof(T) == 4) { constexpr int NN = 1024; CALL; }                \
@@ -582,15 +585,20 @@ lgf_status poisson_prepare()
     return ensure_twiddles();
 }
 
+// supported FFT lengths, ascending: powers of two and 3 times a power of two
+static const int kLengths[] = {16, 32, 64, 96, 128, 192, 256, 384, 512, 1024};
+
 bool poisson_supported_n(int n)
 {
-    return n == 16 || n == 32 || n == 64 || n == 128 || n == 256 || n == 512 || n == 1024;
+    for (int v : kLengths)
+        if (v == n) return true;
+    return false;
 }
 
 int poisson_pick_n(int need)
 {
-    for (int n = 16; n <= 1024; n *= 2)
-        if (n >= need) return n;
+    for (int v : kLengths)
+        if (v >= need) return v;
     return 0;
 }
 

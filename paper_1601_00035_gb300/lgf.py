@@ -405,6 +405,18 @@ def version() -> str:
     return load().lgf_version().decode()
 
 
+# FFT lengths the library supports, ascending (powers of two and 3 times a power of two)
+FFT_LENGTHS = (16, 32, 64, 96, 128, 192, 256, 384, 512, 1024)
+
+
+def fft_length(need: int) -> int:
+    """Smallest supported FFT length >= need (0 if none)."""
+    for n in FFT_LENGTHS:
+        if n >= need:
+            return n
+    return 0
+
+
 def required_max_offset(src_blocks: np.ndarray, dst_blocks: np.ndarray, B: int) -> int:
     """Smallest table max_offset a Poisson plan over these block lists needs
     (half the zero-padded FFT length minus one, per the plan's size rule)."""
@@ -415,8 +427,6 @@ def required_max_offset(src_blocks: np.ndarray, dst_blocks: np.ndarray, B: int) 
         S0, S1 = s[:, a].min() * B, (s[:, a].max() + 1) * B - 1
         T0, T1 = t[:, a].min() * B, (t[:, a].max() + 1) * B - 1
         m = max(abs(T0 - S1), abs(T1 - S0))
-        n = 16
-        while n < max(2 * m + 2, 2 * (S1 - S0 + 1)):
-            n *= 2
+        n = fft_length(max(2 * m + 2, 2 * (S1 - S0 + 1)))
         need = max(need, n // 2 - 1)
     return int(need)

@@ -41,9 +41,16 @@ def test_required_max_offset():
     b = np.array([[0, 0, 0], [7, 7, 7]])
     assert lgf.required_max_offset(b, b, 16) == 127
     # a target inside a long source: the offsets alone allow length 128, the
-    # source extent (96 points) needs 256 so that it fills at most half a line
+    # source extent (96 points) needs 192 so that it fills at most half a line
     s = np.array([[i, 0, 0] for i in range(6)])
     t = np.array([[3, 0, 0]])
-    assert lgf.required_max_offset(s, t, 16) == 127
+    assert lgf.required_max_offset(s, t, 16) == 95
     # far target: the offsets decide
     assert lgf.required_max_offset(np.array([[0, 0, 0]]), np.array([[30, 0, 0]]), 16) == 511
+    # lengths 3 * 2^k: a 40-point box needs 2 * 39 + 2 = 80 -> 96; 80 points -> 160 -> 192;
+    # 160 points -> 320 -> 384; 200 points -> 400 -> 512
+    for e, n in ((40, 96), (80, 192), (160, 384), (200, 512)):
+        c = np.array([[0, 0, 0], [e // 8 - 1, 0, 0]])
+        assert lgf.required_max_offset(c, c, 8) == n // 2 - 1, e
+    assert [lgf.fft_length(v) for v in (1, 17, 65, 97, 129, 193, 257, 385, 513, 1025)] == \
+        [16, 32, 96, 128, 192, 256, 384, 512, 1024, 0]

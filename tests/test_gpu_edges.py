@@ -75,7 +75,7 @@ def test_far_target_length_1024(dst):
 def test_wide_source_narrow_target(axis):
     """Source six blocks long on one axis, target one block inside it: the
     largest offset (63) alone would allow length 128, but the source extent (96)
-    must stay in the lower half of the line, so the plan takes 256 there."""
+    must stay in the lower half of the line, so the plan takes 192 there."""
     lgf = built()
     B = 16
     rng = np.random.default_rng(11 + axis)
@@ -86,7 +86,7 @@ def test_wide_source_narrow_target(axis):
     f = rng.standard_normal((6, 1, B, B, B))
     out = _solve(lgf, B, src_c, dst_c, f)
     K = lgf.required_max_offset(src_c, dst_c, B)
-    assert K == 127
+    assert K == 95
     ref = O.direct_conv(O.lgf_cube(K), inputs.block_points(src_c, B), f.reshape(-1), inputs.block_points(dst_c, B))
     assert rel_l2(out.reshape(-1), ref) < 1e-6
 
@@ -116,6 +116,52 @@ def test_length_512(precision):
     near = abs(O.lgf_value((0, 0, 0))) * np.sqrt(np.mean(f ** 2))
     scale = max(1.0, near / np.sqrt(np.mean(ref ** 2)))
     assert rel_l2(out[sel], ref) < (1e-12 if precision else 1e-6) * scale
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_lengths_3x2k(precision):
+    """FFT lengths 96, 192 and 384 at once (x, y, z): one source block and targets
+    5, 11 and 23 blocks away, in FP32 and FP64; sampled against the direct sum."""
+    lgf = built()
+    B = 8
+    rng = np.random.default_rng(23)
+    src_c = np.array([[0, 0, 0]], dtype=np.int32)
+    dst_c = np.array([[5, 0, 0], [0, 11, 0], [0, 0, 23], [2, 3, 4], [0, 0, 0]], dtype=np.int32)
+    f = rng.standard_normal((1, 1, B, B, B))
+    K = lgf.required_max_offset(src_c, dst_c, B)
+    assert K == 191
+    table = lgf.Table(lgf.LAPLACE7, max_offset=K)
+    plan = lgf.Plan(table, [lgf.Solve(B, 1, src_c, dst_c)], precision=precision)
+    dt = torch.float64 if precision else torch.float32
+    d_src = torch.from_numpy(f).to(dt).cuda()
+    d_dst = torch.zeros((len(dst_c), 1, B, B, B), dtype=dt, device="cuda")
+    (plan.execute_f64 if precision else plan.execute)([d_src], [d_dst])
+    out = d_dst.cpu().numpy().reshape(-1)
+    pts = inputs.block_points(dst_c, B)
+    sel = rng.choice(len(pts), 160, replace=False)
+    ref = _reference(f, src_c, dst_c, B, pts[sel])
+    near = abs(O.lgf_value((0, 0, 0))) * np.sqrt(np.mean(f ** 2))
+    scale = max(1.0, near / np.sqrt(np.mean(ref ** 2)))
+    assert rel_l2(out[sel], ref) < (1e-12 if precision else 1e-6) * scale
+
+
+@pytest.mark.parametrize("e", [40, 80, 160])
+def test_full_box_3x2k(e):
+    """A dense e^3 source on its own box (FFT length 96, 192, 384 on every axis),
+    FP32, sampled against the direct sum."""
+    lgf = built()
+    B = 8
+    rng = np.random.default_rng(e)
+    f = rng.standard_normal((e, e, e))
+    c = inputs.block_grid(f.shape, B)
+    K = lgf.required_max_offset(c, c, B)
+    assert K == {40: 47, 80: 95, 160: 191}[e]
+    out = _solve(lgf, B, c, c, inputs.to_blocks(f, B, c))
+    pts = inputs.block_points(c, B)
+    sel = rng.choice(len(pts), 64, replace=False)
+    ref = O.direct_conv_box(O.lgf_cube(K), f, pts[sel])
+    got = out.reshape(-1)[sel]
+    assert rel_l2(got, ref) < 1e-6
 
 
 def test_argument_errors():
