@@ -162,14 +162,25 @@ def geometry(src_c, dst_c, ncomp):
     return {"Es": Es, "Et": Et, "N": N, "ncomp": ncomp, "nsrc": len(s), "ndst": len(t)}
 
 
+KERNEL_SOURCES = ("poisson.cu", "fft.cuh", "common.cuh")
+
+
+def kernel_source_sha() -> str:
+    """sha256 prefix over the sources the FFT passes are compiled from."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1601_00035_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def ncu_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
-    summary was taken on the current kernel source (sha256 prefix recorded)."""
+    summary was taken on the current kernel sources (sha256 prefix recorded)."""
     path = os.path.join(ROOT, "profiles", "poisson_ring128_ncu.md")
-    src = os.path.join(ROOT, "paper_1601_00035_gb300", "csrc", "poisson.cu")
     try:
         txt = open(path).read()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = kernel_source_sha()
     except OSError:
         return None
     m = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
