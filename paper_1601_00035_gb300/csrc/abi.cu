@@ -95,6 +95,7 @@ void free_plan(lgf_plan *p)
     cudaFree(p->d_wsA64);
     cudaFree(p->d_wsB64);
     for (auto &sp : p->spectra) cudaFree(sp.d_Kh64);
+    for (auto e : p->unit_mark) cudaEventDestroy(e);
     for (auto w : p->lane_wsA) cudaFree(w);
     for (auto w : p->lane_wsB) cudaFree(w);
     for (auto st : p->lanes) cudaStreamDestroy(st);
@@ -541,6 +542,8 @@ static lgf_status plan_poisson(lgf_plan *p, const lgf_table *t, const lgf_solve_
     p->lane_wsA.assign(nl, nullptr);
     p->lane_wsB.assign(nl, nullptr);
     LGF_CUDA_TRY(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming));
+    p->unit_mark.assign(p->units.size(), nullptr);
+    for (auto &e : p->unit_mark) LGF_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     for (int k = 0; k < nl; k++) {
         LGF_CUDA_TRY(cudaStreamCreateWithFlags(&p->lanes[k], cudaStreamNonBlocking));
         LGF_CUDA_TRY(cudaEventCreateWithFlags(&p->lane_done[k], cudaEventDisableTiming));
@@ -717,11 +720,13 @@ static lgf_status run_poisson(lgf_plan *p, const float *const *src, float *const
         return g;
     };
     // one unit on stream st: host copy in, five passes, host copy out
-    auto run_unit = [&](const lgf_plan::Unit &u, cx<float> *wa, cx<float> *wb, cudaStream_t st,
-                        Profiler *pr) -> lgf_status {
+    // wait (optional): the unit (its copy in included) starts after that event
+    auto run_unit = [&](const lgf_plan::Unit &u, cx<float> *wa, cx<float> *wb, cudaStream_t st, Profiler *pr,
+                        cudaEvent_t wait = nullptr, cudaEvent_t mark = nullptr) -> lgf_status {
         const PoissonSolve &q = p->solves[u.solve];
+        if (wait) LGF_CUDA_TRY(cudaStreamWaitEvent(st, wait, 0));
         if (host) LGF_TRY(copy_slice((float *)src[u.solve], host->src[u.solve], q, q.nsrc, u.c0, u.nc, true, st));
-        LGF_TRY(poisson_launch(unit_geom(u), src[u.solve], dst[u.solve], wa, wb, st, pr));
+        LGF_TRY(poisson_launch(unit_geom(u), src[u.solve], dst[u.solve], wa, wb, st, pr, mark, mark ? 0 : -1));
         if (host) LGF_TRY(copy_slice(dst[u.solve], host->dst[u.solve], q, q.ndst, u.c0, u.nc, false, st));
         return LGF_OK;
     };
@@ -739,8 +744,17 @@ static lgf_status run_poisson(lgf_plan *p, const float *const *src, float *const
     // fork: every lane waits for the work queued so far on the caller's stream
     LGF_CUDA_TRY(cudaEventRecord(p->fork, s));
     for (size_t k = 0; k < p->lanes.size(); k++) LGF_CUDA_TRY(cudaStreamWaitEvent(p->lanes[k], p->fork, 0));
-    for (const auto &u : p->units)
-        LGF_TRY(run_unit(u, p->lane_wsA[u.lane], p->lane_wsB[u.lane], p->lanes[u.lane], nullptr));
+    // With host buffers the units start one pass apart: unit i (copy in, passes,
+    // copy out) waits for unit i-1's first pass, so the units finish one after
+    // another and each unit's copy out overlaps the passes of the others (device
+    // buffers: all units start together, which is faster there).  Only when
+    // every unit has a stream of its own.
+    const bool stagger = host != nullptr && p->units.size() <= p->lanes.size();
+    for (size_t i = 0; i < p->units.size(); i++) {
+        const auto &u = p->units[i];
+        LGF_TRY(run_unit(u, p->lane_wsA[u.lane], p->lane_wsB[u.lane], p->lanes[u.lane], nullptr,
+                         stagger && i > 0 ? p->unit_mark[i - 1] : nullptr, stagger ? p->unit_mark[i] : nullptr));
+    }
     // join: the caller's stream waits for every lane
     for (size_t k = 0; k < p->lanes.size(); k++) {
         LGF_CUDA_TRY(cudaEventRecord(p->lane_done[k], p->lanes[k]));

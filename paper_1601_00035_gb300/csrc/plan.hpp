@@ -74,8 +74,9 @@ struct Profiler {
 };
 
 // launchers (poisson.cu)
+// mark (optional): recorded on s right after pass mark_after (0 x forward, 1 y forward, 2 z)
 lgf_status poisson_launch(const Geom &g, const float *src, float *dst, cx<float> *wsA, cx<float> *wsB,
-                          cudaStream_t s, Profiler *prof = nullptr);
+                          cudaStream_t s, Profiler *prof = nullptr, cudaEvent_t mark = nullptr, int mark_after = -1);
 lgf_status poisson_launch64(const Geom &g, const double *src, double *dst, cx<double> *wsA, cx<double> *wsB,
                             cudaStream_t s, Profiler *prof = nullptr);
 bool poisson_supported_n(int n);
@@ -212,6 +213,7 @@ struct lgf_plan {
         size_t elemsA, elemsB;
     };
     std::vector<Unit> units;
+    std::vector<cudaEvent_t> unit_mark;  // per unit: recorded after one of its passes (staggered start)
     double *d_acc = nullptr;  // residual accumulators
     // IF
     int B = 0, ncomp = 0, nblk = 0, R = 0;

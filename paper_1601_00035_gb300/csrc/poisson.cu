@@ -545,8 +545,13 @@ lgf_status launch_x_inv(const Geom &g, const cx<T> *in, T *dst, cudaStream_t s)
     }
 
 template <typename T>
-lgf_status launch_all(const Geom &g, const T *src, T *dst, cx<T> *wsA, cx<T> *wsB, cudaStream_t s, Profiler *prof)
+lgf_status launch_all(const Geom &g, const T *src, T *dst, cx<T> *wsA, cx<T> *wsB, cudaStream_t s, Profiler *prof,
+                      cudaEvent_t mark = nullptr, int mark_after = -1)
 {
+    auto MARK = [&](int pass) -> lgf_status {
+        if (mark && mark_after == pass) LGF_CUDA_TRY(cudaEventRecord(mark, s));
+        return LGF_OK;
+    };
     if (fft::upload_tw64() != cudaSuccess) {
         set_error("twiddle upload failed");
         return LGF_ERR_CUDA;
@@ -555,9 +560,11 @@ lgf_status launch_all(const Geom &g, const T *src, T *dst, cx<T> *wsA, cx<T> *ws
     if (P) prof->begin(s);
     LGF_DISPATCH_N(T, g.N[0], LGF_TRY((launch_x_fwd<NN, T>(g, src, wsA, s))));
     if (P) prof->end("x_fwd_gather_r2c", s);
+    LGF_TRY(MARK(0));
     if (P) prof->begin(s);
     LGF_DISPATCH_N(T, g.N[1], LGF_TRY((launch_line<NN, 0, T>(g, wsA, wsB, s))));
     if (P) prof->end("y_fwd", s);
+    LGF_TRY(MARK(1));
     if (P) prof->begin(s);
     LGF_DISPATCH_N(T, g.N[2], if constexpr (use_zmid2<NN, T>()) {
         LGF_TRY((launch_zmid2<NN>(g, (const cx<float> *)wsB, (cx<float> *)wsA, s)));
@@ -565,6 +572,7 @@ lgf_status launch_all(const Geom &g, const T *src, T *dst, cx<T> *wsA, cx<T> *ws
         LGF_TRY((launch_line<NN, 1, T>(g, wsB, wsA, s)));
     });
     if (P) prof->end("z_fwd_mul_inv", s);
+    LGF_TRY(MARK(2));
     if (P) prof->begin(s);
     LGF_DISPATCH_N(T, g.N[1], LGF_TRY((launch_line<NN, 2, T>(g, wsA, wsB, s))));
     if (P) prof->end("y_inv", s);
@@ -603,9 +611,9 @@ int poisson_pick_n(int need)
 }
 
 lgf_status poisson_launch(const Geom &g, const float *src, float *dst, cx<float> *wsA, cx<float> *wsB,
-                          cudaStream_t s, Profiler *prof)
+                          cudaStream_t s, Profiler *prof, cudaEvent_t mark, int mark_after)
 {
-    return launch_all<float>(g, src, dst, wsA, wsB, s, prof);
+    return launch_all<float>(g, src, dst, wsA, wsB, s, prof, mark, mark_after);
 }
 
 lgf_status poisson_launch64(const Geom &g, const double *src, double *dst, cx<double> *wsA, cx<double> *wsB,
