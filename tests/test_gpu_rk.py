@@ -349,3 +349,19 @@ def test_adaptive_ring_run():
     K, E = np.array(Ks), np.array(Es)
     ratio = (K[2:] - K[:-2]) / (2 * dt) / (-2.0 / re * E[1:-1])
     assert np.all(np.abs(ratio - 0.967) < 0.03), ratio
+
+
+def test_ring_speed_approaches_saffman():
+    """Thinner cores approach Saffman's leading-order speed (eq. u_saffman, beta_0 =
+    0.557966 for the Gaussian core): the ring speed's relative deviation at
+    delta / R0 = 0.1 (R0 = 50 dx, core 5 cells) is below 3 % and below that at 0.2.
+    (Measured: -4.3 % at 0.2, -1.6 % at 0.1, -1.1 % at 0.05 with a 5-cell core.)"""
+    import math
+    lgf = built()
+    rel = []
+    for n, R0c, dcells in [(256, 50.0, 10.0), (256, 50.0, 5.0)]:
+        ds, dt, re, uinf, eps = _ring_run(lgf, n, R0c, dcells)
+        ih = ds[0]["I"] / np.linalg.norm(ds[0]["I"])
+        speed = (ds[-1]["X"] - ds[0]["X"]) @ ih / ((len(ds) - 1) * dt) - uinf @ ih
+        rel.append(speed / ((math.log(8 / eps) - 0.557966) / (4 * math.pi)) - 1)
+    assert abs(rel[1]) < 0.03 and abs(rel[1]) < abs(rel[0]), rel
