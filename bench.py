@@ -4,7 +4,8 @@ Workload (default): the 128^3 vector streamfunction solve a = -L^{-1} w of a
 tilted Gaussian-core vortex ring (R = 32, sigma = 3 cells, circulation 1),
 16^3 blocks, sources on the blocks where |w| > 1e-14 max, results on all 512
 blocks, FP32 data, seeded synthetic input.  One step = one lgf_conv_execute
-(all three components).  Points = target points x components.
+(all three components, one stream each, replayed as a CUDA graph).  Points =
+target points x components.
 
 Timing: W warm-up steps, then exactly K steps, each bracketed by CUDA events
 on the launching stream; a 256 MiB buffer (> the 129 MB L2) is rewritten
@@ -18,8 +19,9 @@ oracle's direct sum on a bounded sample of target points, host cores),
 e2e (the same solve through lgf_conv_execute_host with pinned host buffers,
 copies included), gpu_launches, clocks (nvidia-smi sampled during the run).
 
---impl reference runs the FP64 CPU oracle (direct summation, the reference of
-this build) on the same workload, each step a bounded sample of target points.
+--impl reference runs the FP64 CPU oracle (direct summation, the program the
+GPU path is checked against) on the same workload, each step a bounded sample
+of target points.
 """
 from __future__ import annotations
 
