@@ -118,6 +118,26 @@ def test_length_512(precision):
     assert rel_l2(out[sel], ref) < (1e-12 if precision else 1e-6) * scale
 
 
+@pytest.mark.parametrize("dst", [[[15, 0, 0], [0, 0, 7], [1, 0, 1]], [[0, 15, 0], [0, 0, 3], [1, 1, 1]]])
+def test_packed_z_with_long_x_or_y(dst):
+    """The packed z pass (lengths 128 and 256) beside a 512-point x or y axis:
+    targets 15 blocks away along x (KX = 257) or y, and 7 or 3 along z; sampled
+    against the direct sum."""
+    lgf = built()
+    B = 16
+    rng = np.random.default_rng(31)
+    src_c = np.array([[0, 0, 0]], dtype=np.int32)
+    dst_c = np.array(dst, dtype=np.int32)
+    f = rng.standard_normal((1, 1, B, B, B))
+    out = _solve(lgf, B, src_c, dst_c, f).reshape(-1)
+    pts = inputs.block_points(dst_c, B)
+    sel = rng.choice(len(pts), 128, replace=False)
+    ref = _reference(f, src_c, dst_c, B, pts[sel])
+    near = abs(O.lgf_value((0, 0, 0))) * np.sqrt(np.mean(f ** 2))
+    scale = max(1.0, near / np.sqrt(np.mean(ref ** 2)))
+    assert rel_l2(out[sel], ref) < 1e-6 * scale
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_lengths_3x2k(precision):
     """FFT lengths 96, 192 and 384 at once (x, y, z): one source block and targets
