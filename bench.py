@@ -491,7 +491,7 @@ def aux_workload(name, lgf, torch):
         w = inputs.vortex_ring_edges(n, R0c, dcells, axis) / dx ** 2   # physical vorticity
         supp = inputs.active_blocks(w, B, 1e-6)
         scheme = {"rk256": 0, "rk256_b": 1, "rk256_c": 2, "rk256_refresh": 0}[name]
-        rk = lgf.RKPlan(B, supp, dx, dt, re, scheme=scheme)
+        rk = lgf.RKPlan(B, supp, dx, dt, re, scheme=scheme, use_graph=True)
         xs = rk.blocks(0)
         # initial velocity by the method itself: a = -L^-1 w (vector, D_supp -> D_xsoln), u = C^T a
         K = lgf.required_max_offset(supp, xs, B)

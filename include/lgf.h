@@ -210,7 +210,9 @@ typedef struct {
     const int32_t *soln_blocks;  /* [n_soln][3] block coordinates (host) */
     double dx, dt, re;           /* grid spacing, time step, Reynolds number: alpha = dt / (dx^2 re) */
     int scheme;                  /* tableau of eq. ifherk_schemes: 0 = Scheme A, 1 = Scheme B, 2 = Scheme C */
-    int reserved[3];             /* must be zero */
+    int use_graph;               /* 1: lgf_rk_step captures its launch sequence in a CUDA graph on first
+                                    use for a given (u_in, u_out, u_inf) and replays it (two cached) */
+    int reserved[2];             /* must be zero */
 } lgf_rk_desc;
 
 /* Builds the LGF table, a scalar Poisson plan D_supp -> D_xsoln, the

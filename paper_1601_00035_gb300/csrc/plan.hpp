@@ -155,6 +155,15 @@ struct RkPlan {
     bool if_owned[3] = {false, false, false};
     int scheme = 0;
     double at[4][4] = {};  // shifted tableau a~_{i,j}, 1-based
+    // lgf_rk_step as a replayed CUDA graph (use_graph): one per (u_in, u_out, u_inf),
+    // at most two (a loop alternates two buffers)
+    int use_graph = 0;
+    struct StepGraph {
+        const void *in, *out;
+        double uinf[3];
+        cudaGraphExec_t exec;
+    };
+    std::vector<StepGraph> graphs;
     lgf_plan *poisson = nullptr;
     lgf_plan *poisson3 = nullptr;  // vector Poisson supp -> xsoln (velocity refresh)
     int *d_nbr27 = nullptr;

@@ -55,6 +55,7 @@ lgf_status alloc_upload(T **d, const std::vector<T> &h, size_t &bytes)
 void free_rk(RkPlan *r)
 {
     if (!r) return;
+    for (auto &g : r->graphs) cudaGraphExecDestroy(g.exec);
     lgf_plan_destroy(r->poisson);
     lgf_plan_destroy(r->poisson3);
     for (int i = 0; i < 3; i++)
@@ -119,8 +120,7 @@ lgf_status lgf_rk_plan(const lgf_rk_desc *d, void *stream, lgf_plan **out)
     LGF_CHECK_ARG(d->dx > 0 && d->dt > 0 && d->re > 0, "lgf_rk_plan: dx, dt, re must be positive");
     LGF_CHECK_ARG(d->scheme >= 0 && d->scheme <= 2, "lgf_rk_plan: scheme %d not in {0 (A), 1 (B), 2 (C)}",
                   d->scheme);
-    for (int i = 0; i < 3; i++) LGF_CHECK_ARG(d->reserved[i] == 0, "lgf_rk_plan: reserved fields must be zero");
-    cudaStream_t s = (cudaStream_t)stream;
+    for (int i = 0; i < 2; i++) LGF_CHECK_ARG(d->reserved[i] == 0, "lgf_rk_plan: reserved fields must be zero");
     const int B = d->B;
     // blocks: soln as given, xsoln = soln dilated by one block, soln first
     std::unordered_map<int64_t, int> xi;
@@ -261,6 +261,7 @@ lgf_status lgf_rk_plan(const lgf_rk_desc *d, void *stream, lgf_plan **out)
         }
         for (int i = 0; i < 3; i++) c[i] = A[i][0] + A[i][1] + A[i][2];
         r->scheme = d->scheme;
+        r->use_graph = d->use_graph ? 1 : 0;
         for (int i = 1; i <= 3; i++)
             for (int j = 1; j <= i; j++) r->at[i][j] = i < 3 ? A[i][j - 1] : b[j - 1];
         const double ct[4] = {c[0], c[1], c[2], 1.0};  // c~_0 = c_1, c~_i = c_{i+1}, c~_3 = 1
@@ -304,7 +305,6 @@ lgf_status lgf_rk_plan(const lgf_rk_desc *d, void *stream, lgf_plan **out)
         return fail(LGF_ERR_OOM);
     }
     r->bytes += total * sizeof(float);
-    (void)s;
     lgf_plan *p = new (std::nothrow) lgf_plan();
     if (!p) return fail(LGF_ERR_OOM);
     p->kind = LGF_PLAN_RK;
@@ -345,13 +345,12 @@ lgf_status lgf_op_apply(lgf_plan *p, int op, const float *in, float *out, double
                      (cudaStream_t)stream);
 }
 
-lgf_status lgf_rk_step(lgf_plan *p, const float *u_in, float *u_out, const double uinf[3], void *stream)
+}  // extern "C"
+
+// the launch sequence of one step (no host synchronisation: capturable)
+static lgf_status rk_step_launches(lgf_plan *p, const float *u_in, float *u_out, const double uinf[3], cudaStream_t s)
 {
-    clear_error();
-    LGF_CHECK_ARG(p && u_in && u_out && uinf && u_in != u_out, "lgf_rk_step: NULL or aliasing argument");
-    LGF_CHECK_ARG(p->kind == LGF_PLAN_RK, "lgf_rk_step: needs a plan from lgf_rk_plan");
     RkPlan *r = p->rk;
-    cudaStream_t s = (cudaStream_t)stream;
     const double dt = r->dt;
     const double a11 = r->at[1][1], a21 = r->at[2][1], a22 = r->at[2][2];
     const double a31 = r->at[3][1], a32 = r->at[3][2], a33 = r->at[3][3];
@@ -407,6 +406,55 @@ lgf_status lgf_rk_step(lgf_plan *p, const float *u_in, float *u_out, const doubl
     } else {
         LGF_TRY(project(rv, u_out, nullptr, 0.0));
     }
+    return LGF_OK;
+}
+
+extern "C" {
+
+lgf_status lgf_rk_step(lgf_plan *p, const float *u_in, float *u_out, const double uinf[3], void *stream)
+{
+    clear_error();
+    LGF_CHECK_ARG(p && u_in && u_out && uinf && u_in != u_out, "lgf_rk_step: NULL or aliasing argument");
+    LGF_CHECK_ARG(p->kind == LGF_PLAN_RK, "lgf_rk_step: needs a plan from lgf_rk_plan");
+    RkPlan *r = p->rk;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!r->use_graph || p->prof.on) return rk_step_launches(p, u_in, u_out, uinf, s);
+    for (auto &g : r->graphs)
+        if (g.in == u_in && g.out == u_out && g.uinf[0] == uinf[0] && g.uinf[1] == uinf[1] && g.uinf[2] == uinf[2]) {
+            LGF_CUDA_TRY(cudaGraphLaunch(g.exec, s));
+            return LGF_OK;
+        }
+    // capture this buffer set's step on a private stream, then replay it on s
+    cudaStream_t cs;
+    LGF_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t gr = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    lgf_status st = LGF_OK;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        set_error("stream capture failed to start");
+        st = LGF_ERR_CUDA;
+    } else {
+        st = rk_step_launches(p, u_in, u_out, uinf, cs);
+        const cudaError_t e = cudaStreamEndCapture(cs, &gr);
+        if (st == LGF_OK && e != cudaSuccess) {
+            set_error("stream capture failed: %s", cudaGetErrorString(e));
+            st = LGF_ERR_CUDA;
+        }
+        if (st == LGF_OK && cudaGraphInstantiate(&ex, gr, 0) != cudaSuccess) {
+            set_error("graph instantiation failed");
+            st = LGF_ERR_CUDA;
+            ex = nullptr;
+        }
+    }
+    if (gr) cudaGraphDestroy(gr);
+    cudaStreamDestroy(cs);
+    if (st != LGF_OK) return st;
+    if (r->graphs.size() == 2) {
+        cudaGraphExecDestroy(r->graphs.front().exec);
+        r->graphs.erase(r->graphs.begin());
+    }
+    r->graphs.push_back({u_in, u_out, {uinf[0], uinf[1], uinf[2]}, ex});
+    LGF_CUDA_TRY(cudaGraphLaunch(ex, s));
     return LGF_OK;
 }
 

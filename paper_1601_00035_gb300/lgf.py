@@ -57,7 +57,8 @@ class _RkDesc(ctypes.Structure):
         ("dt", ctypes.c_double),
         ("re", ctypes.c_double),
         ("scheme", ctypes.c_int),
-        ("reserved", ctypes.c_int * 3),
+        ("use_graph", ctypes.c_int),
+        ("reserved", ctypes.c_int * 2),
     ]
 
 
@@ -309,13 +310,15 @@ SCHEME_A, SCHEME_B, SCHEME_C = 0, 1, 2
 class RKPlan:
     """One IF-HERK step (Scheme A, B or C) on a block set (lgf_rk_plan / lgf_rk_step)."""
 
-    def __init__(self, B: int, soln_blocks, dx: float, dt: float, re: float, stream=None, scheme: int = SCHEME_A):
+    def __init__(self, B: int, soln_blocks, dx: float, dt: float, re: float, stream=None, scheme: int = SCHEME_A,
+                 use_graph: bool = False):
         L = load()
         self._soln = np.ascontiguousarray(soln_blocks, dtype=np.int32).reshape(-1, 3)
         d = _RkDesc()
         d.B, d.n_soln = int(B), len(self._soln)
         d.soln_blocks = self._soln.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         d.dx, d.dt, d.re, d.scheme = float(dx), float(dt), float(re), int(scheme)
+        d.use_graph = int(bool(use_graph))
         h = ctypes.c_void_p()
         _check(L.lgf_rk_plan(ctypes.byref(d), _stream(stream), ctypes.byref(h)))
         self._h = h

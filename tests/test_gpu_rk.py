@@ -365,3 +365,29 @@ def test_ring_speed_approaches_saffman():
         speed = (ds[-1]["X"] - ds[0]["X"]) @ ih / ((len(ds) - 1) * dt) - uinf @ ih
         rel.append(speed / ((math.log(8 / eps) - 0.557966) / (4 * math.pi)) - 1)
     assert abs(rel[1]) < 0.03 and abs(rel[1]) < abs(rel[0]), rel
+
+
+def test_step_graph_replay_bitwise():
+    """use_graph: lgf_rk_step captured and replayed per (u_in, u_out, u_inf) gives bitwise
+    the eager step's result, over alternating buffers, a repeated buffer set and a new u_inf."""
+    lgf = built()
+    cs = small_case(B=8, amp=3.0)
+    B, org = cs["B"], cs["origin"]
+    for scheme in (0, 2):
+        rk, xs = _plan(lgf, cs, 0.5, 10.0, scheme=scheme)
+        rkg = lgf.RKPlan(B, cs["soln"], cs["dx"], 0.5, 10.0, scheme=scheme, use_graph=True)
+        u0 = torch.from_numpy(to_blocks_dense(cs["u0"], B, xs, org)).cuda()
+        outs = []
+        for plan in (rk, rkg):
+            a, b = u0.clone(), torch.zeros_like(u0)
+            seq = []
+            for uinf in [(0.05, -0.02, 0.1)] * 3 + [(0.0, 0.0, -0.1)]:
+                plan.step(a, b, uinf)
+                a, b = b, a
+                seq.append(a.clone())
+            plan.step(u0, b, (0.05, -0.02, 0.1))   # a buffer set seen before
+            seq.append(b.clone())
+            torch.cuda.synchronize()
+            outs.append(seq)
+        for x, y in zip(*outs):
+            assert torch.equal(x, y)
