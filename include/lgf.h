@@ -137,7 +137,11 @@ lgf_status lgf_plan_workspace_bytes(const lgf_plan *p, size_t *bytes);
 
 /* Poisson: for every solve i, dst[i] (device, [n_dst][ncomp][B^3] FP32,
  * overwritten on every target point) = scale * dx^2 * G * src[i] (device,
- * [n_src][ncomp][B^3] FP32).  Asynchronous on `stream`; no allocation. */
+ * [n_src][ncomp][B^3] FP32).  Asynchronous on `stream`; no allocation.  A
+ * plan with more than one (solve, component) unit runs the units on its own
+ * worker streams, forked from and joined back to `stream` with events; with
+ * opts->use_graph the whole sequence is captured once per set of buffers
+ * and replayed. */
 lgf_status lgf_conv_execute(lgf_plan *p, const float *const *src, float *const *dst, void *stream);
 
 /* FP64 variant for plans built with opts->precision = 1: src[i], dst[i] are
@@ -146,8 +150,10 @@ lgf_status lgf_conv_execute_f64(lgf_plan *p, const double *const *src, double *c
 
 /* Same as lgf_conv_execute with HOST buffers: copies every src[i] to
  * plan-owned device staging, executes, copies the results to dst[i] and
- * synchronises `stream` before returning.  Host buffers should be pinned
- * for full copy bandwidth. */
+ * synchronises `stream` before returning.  Each unit copies its own
+ * component slice in and out on its worker stream, so copies overlap the
+ * other units' passes.  Host buffers should be pinned for full copy
+ * bandwidth. */
 lgf_status lgf_conv_execute_host(lgf_plan *p, const float *const *src, float *const *dst, void *stream);
 
 /* IF plan (table of kind LGF_KERNEL_IFACTOR, one solve): y = M E_Q(alpha) M x
