@@ -326,6 +326,20 @@ __host__ __device__ constexpr double cos48(int j)
 }
 __host__ __device__ constexpr double sin48(int j) { return cos48(j - 12); }
 
+// scalar helpers shared by the FP32, FP64 and packed transforms
+template <typename T>
+__device__ __forceinline__ T cst(double c) { return (T)c; }
+template <>
+__device__ __forceinline__ f32x2 cst<f32x2>(double c) { return bc2((float)c); }
+template <typename T>
+__device__ __forceinline__ T neg(T a) { return -a; }
+template <>
+__device__ __forceinline__ f32x2 neg<f32x2>(f32x2 a) { return bc2(0.f) - a; }
+template <typename T>
+__device__ __forceinline__ T fmaT(T a, T b, T c) { return ::fma(a, b, c); }
+template <>
+__device__ __forceinline__ f32x2 fmaT<f32x2>(f32x2 a, f32x2 b, f32x2 c) { return fma(a, b, c); }
+
 // v times w_R^j = exp(-2 pi i j / R) (its conjugate for the inverse); R divides
 // 48, j compile-time.  Quarter turns are swaps, the rest complex products with
 // literal constants.
@@ -334,12 +348,13 @@ __device__ __forceinline__ cx<T> twiddle48(cx<T> v, int j)
 {
     j %= R;
     if (j == 0) return v;
-    if (2 * j == R) return {-v.x, -v.y};
-    if (4 * j == R) return INV ? cx<T>{-v.y, v.x} : cx<T>{v.y, -v.x};
-    if (4 * j == 3 * R) return INV ? cx<T>{v.y, -v.x} : cx<T>{-v.y, v.x};
+    if (2 * j == R) return {neg(v.x), neg(v.y)};
+    if (4 * j == R) return INV ? cx<T>{neg(v.y), v.x} : cx<T>{v.y, neg(v.x)};
+    if (4 * j == 3 * R) return INV ? cx<T>{v.y, neg(v.x)} : cx<T>{neg(v.y), v.x};
     const int q = j * (48 / R);
-    const T c = (T)cos48(q), sn = INV ? (T)sin48(q) : -(T)sin48(q);  // w = c + i sn
-    return {::fma(v.x, c, -v.y * sn), ::fma(v.x, sn, v.y * c)};
+    const double sd = INV ? sin48(q) : -sin48(q);  // w = c + i sn
+    const T c = cst<T>(cos48(q)), sn = cst<T>(sd), nsn = cst<T>(-sd);
+    return {fmaT(v.x, c, v.y * nsn), fmaT(v.x, sn, v.y * c)};
 }
 
 // In-register DFT of length R = 3 M (M a power of two), natural order in and
@@ -364,7 +379,7 @@ __device__ __forceinline__ void dft_reg3(cx<T> *a)
             levels<M, INV, T, 0, HALF>(y[r]);
         }
     }
-    const T h = (T)0.5, s3 = (T)0.86602540378443864676;  // cos(pi/3), sin(pi/3)
+    const T nh = cst<T>(-0.5), s3 = cst<T>(0.86602540378443864676);  // -cos(pi/3), sin(pi/3)
 #pragma unroll
     for (int k = 0; k < M; k++) {
         const cx<T> b0 = y[0][k];
@@ -372,7 +387,7 @@ __device__ __forceinline__ void dft_reg3(cx<T> *a)
         const cx<T> b2 = twiddle48<INV, R>(y[2][k], 2 * k);
         // length-3 DFT: X0 = b0 + b1 + b2, X1,2 = b0 - (b1 + b2)/2 -+ i sqrt3/2 (b1 - b2) (forward)
         const cx<T> t1 = b1 + b2;
-        const cx<T> t2 = {::fma(-h, t1.x, b0.x), ::fma(-h, t1.y, b0.y)};
+        const cx<T> t2 = {fmaT(nh, t1.x, b0.x), fmaT(nh, t1.y, b0.y)};
         const cx<T> t3 = {s3 * (b1.x - b2.x), s3 * (b1.y - b2.y)};
         a[OFF + k] = b0 + t1;
         if (!INV) {

@@ -302,19 +302,22 @@ __global__ void __launch_bounds__(TileY<N, T>::threads, TileY<N, T>::minb(MODE))
     }
 }
 
-// z pass on line pairs (FP32, plans with 16 elements per lane): lanes of a
-// packed value carry lines 2q and 2q+1, so the forward transform, the spectral
-// multiply and the inverse transform of both lines run as one stream of
-// .f32x2 instructions (a third fewer instructions than k_line<N, 1, float>).
+// z pass on line pairs (FP32, N = 128, 256 with 16 elements per lane and
+// N = 384 with 24): lanes of a packed value carry lines 2q and
+// 2q+1, so the forward transform, the spectral multiply and the inverse
+// transform of both lines run as one stream of .f32x2 instructions (a third
+// fewer instructions than k_line<N, 1, float>).
 // Same arrays and results as k_line<N, 1, float>; a 16-byte access moves one
 // element of both lines.  The twiddle table holds pairs (w, w) so that a
 // stage twiddle is one 128-bit shared load.
 template <int N>
 struct TileZ2 {
     static constexpr int G = Plan<N>::G;
-    static constexpr int LS = 128 / G;  // line pairs per block
+    // line pairs per block: 24-element lanes take 64-thread blocks, so that the
+    // exchange rows (N x LS x 16 bytes) stay within the static shared memory
+    static constexpr int LS = (Plan<N>::E > 16 ? 64 : 128) / G;
     static constexpr int threads = LS * G;
-    static constexpr int minb = 4;      // 128 registers per thread
+    static constexpr int minb = Plan<N>::E > 16 ? 6 : 4;  // 170 / 128 registers per thread
 };
 
 template <int N>
@@ -326,7 +329,7 @@ __global__ void __launch_bounds__(TileZ2<N>::threads, TileZ2<N>::minb)
     constexpr int E = Plan<N>::E;
     constexpr int G = Plan<N>::G;
     constexpr int KZ = N / 2 + 1;
-    static_assert(E == 16, "packed z pass: 16 elements per lane");
+    static_assert(E == 16 || E == 24, "packed z pass: 16 or 24 elements per lane");
     using SM = fft::Smem<N, true>;
     // line-fast exchange rows of LS 16-byte entries: every 8-thread phase of a
     // 128-bit access touches one contiguous 128-byte row, so no padding
@@ -512,9 +515,13 @@ lgf_status launch_zmid2(const Geom &g, const cx<float> *in, cx<float> *out, cuda
     LGF_CUDA_TRY(launch_pdl(k_zmid2<N>, grid, dim3(TL::threads), s, g, in, out, tw_table<float>()));
     return LGF_OK;
 }
-// the packed z pass covers the FP32 plans with 16 elements per lane
+// the packed z pass covers the FP32 plans with 16 elements per lane and 384
+// (measured faster there; 96 and 192 keep the scalar pass)
 template <int N, typename T>
-constexpr bool use_zmid2() { return sizeof(T) == 4 && Plan<N>::E == 16 && Plan<N>::G > 1 && fft::tw_stage_tables<N>(); }
+constexpr bool use_zmid2()
+{
+    return sizeof(T) == 4 && (Plan<N>::E == 16 || N == 384) && Plan<N>::G > 1 && fft::tw_stage_tables<N>();
+}
 template <int N, typename T>
 lgf_status launch_x_inv(const Geom &g, const cx<T> *in, T *dst, cudaStream_t s)
 {
