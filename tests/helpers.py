@@ -43,3 +43,24 @@ def block_values_at(blocks_vals, coords, B, pts, comp=0):
         i = lut[(x // B, y // B, z // B)]
         out[j] = blocks_vals[i, comp, z % B, y % B, x % B]
     return out
+
+
+def golden(name: str):
+    """A value printed in the paper (tests/golden/paper_values.txt, which gives the
+    passage of each).  Numbers come back as float; comma lists as lists of floats;
+    the entries may use fractions and sqrt3."""
+    import math
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_values.txt")
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        key, val = line.split()[:2]
+        if key != name:
+            continue
+
+        def num(t):
+            return float(eval(t.replace("sqrt3", "math.sqrt(3)"), {"math": math}))
+        parts = val.split(",")
+        return [num(t) for t in parts] if len(parts) > 1 else num(val)
+    raise KeyError(name)

@@ -14,11 +14,13 @@ import pytest
 import oracle as O
 
 
-@pytest.mark.parametrize("alpha,expected", [(0.1, 7), (1.0, 13)])
-def test_footnote_decay(alpha, expected):
+@pytest.mark.parametrize("alpha", [0.1, 1.0])
+def test_footnote_decay(alpha):
+    from tests.helpers import golden
+    expected = golden("ifactor_decay_n_alpha_%.1f" % alpha)
     g = O.bessel_scaled(alpha, 40)
     ratio = g / g[0]  # [G_E](n,0,0) / [G_E](0) = g(n) g(0)^2 / g(0)^3
-    first = int(np.argmax(ratio < 1e-10))
+    first = int(np.argmax(ratio < golden("ifactor_decay_threshold")))
     assert first == expected
 
 
