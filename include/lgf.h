@@ -293,6 +293,11 @@ const char *lgf_last_error(void);
 /* Library version string. */
 const char *lgf_version(void);
 
+/* The FFT length a Poisson plan takes for an axis that needs at least `need`
+ * points (the size rule of lgf_conv_plan): the smallest supported length
+ * >= need, 0 if none.  Host only; no CUDA call. */
+int lgf_fft_length(int need);
+
 #ifdef __cplusplus
 }
 #endif

@@ -255,6 +255,8 @@ const char *lgf_last_error(void) { return g_err; }
 
 const char *lgf_version(void) { return "lgf 0.1 (sm_103a)"; }
 
+int lgf_fft_length(int need) { return need <= 0 ? 16 : lgf::poisson_pick_n(need); }
+
 lgf_status lgf_table_build(lgf_kernel kind, double alpha, int max_offset, void *stream, lgf_table **out)
 {
     clear_error();

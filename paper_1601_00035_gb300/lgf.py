@@ -117,6 +117,7 @@ _SIGS = {
     "lgf_plan_destroy": (None, [ctypes.c_void_p]),
     "lgf_last_error": (ctypes.c_char_p, []),
     "lgf_version": (ctypes.c_char_p, []),
+    "lgf_fft_length": (ctypes.c_int, [ctypes.c_int]),
 }
 
 

@@ -54,3 +54,14 @@ def test_required_max_offset():
         assert lgf.required_max_offset(c, c, 8) == n // 2 - 1, e
     assert [lgf.fft_length(v) for v in (1, 17, 65, 97, 129, 193, 257, 385, 513, 1025)] == \
         [16, 32, 96, 128, 192, 256, 384, 512, 1024, 0]
+
+
+def test_size_rule_matches_the_library():
+    """lgf.fft_length (used by required_max_offset on the host) and the library's
+    own size rule agree for every need up to past the largest length."""
+    if not os.path.exists("/usr/local/cuda/bin/nvcc") and not os.environ.get("NVCC"):
+        pytest.skip("no CUDA toolkit")
+    from paper_1601_00035_gb300 import lgf
+    L = lgf.load()
+    for need in range(1, 1100):
+        assert L.lgf_fft_length(need) == lgf.fft_length(need), need
