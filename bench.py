@@ -221,7 +221,8 @@ def calibrate(run, target_seconds: float) -> int:
     """Sample size whose run takes about target_seconds: grow the sample until
     the fixed cost of a call is amortised, then scale."""
     n, t = 24, run(24)
-    while t < target_seconds / 16 and n < 1 << 22:
+    enough = min(target_seconds / 2, max(target_seconds / 16, 0.25))
+    while t < enough and n < 1 << 22:
         n *= 4
         t = run(n)
     return max(24, int(n * target_seconds / max(t, 1e-3)))
