@@ -76,21 +76,23 @@ def test_ifactor_holed_set(alpha):
         assert rel_linf(got, ref) < 1e-5
 
 
-def test_ifactor_velocity_128_sampled():
-    """3-component 128^3 two-ring velocity, dense block set, alpha = 1.0."""
+@pytest.mark.parametrize("alpha", [0.05, 0.2, 1.0])
+def test_ifactor_velocity_128_sampled(alpha):
+    """3-component 128^3 two-ring velocity, dense block set, alpha in {0.05, 0.2, 1.0}
+    (R = 7, 9, 15): the integrating-factor configuration of the benchmark."""
     lgf = built()
     B = 16
     u = inputs.two_ring_velocity()
     blocks = inputs.block_grid(u.shape[1:], B)
     xb = inputs.to_blocks(u, B, blocks)
-    t = lgf.Table(lgf.IFACTOR, alpha=1.0)
+    t = lgf.Table(lgf.IFACTOR, alpha=alpha)
     plan = lgf.Plan(t, [lgf.Solve(B, 3, blocks, None)])
     dx = torch.from_numpy(xb).cuda()
     dy = torch.zeros_like(dx)
     plan.ifactor(dx, dy)
     torch.cuda.synchronize()
     y = dy.cpu().numpy()
-    g = O.ifactor_taps(1.0)
+    g = O.ifactor_taps(alpha)
     rng = np.random.default_rng(4)
     pts = rng.integers(0, 128, size=(3000, 3)).astype(np.int32)
     lut = {tuple(c): i for i, c in enumerate(blocks.tolist())}

@@ -393,3 +393,39 @@ def test_step_graph_replay_bitwise():
             outs.append(seq)
         for x, y in zip(*outs):
             assert torch.equal(x, y)
+
+
+def test_full_size_graph_step_divergence_free():
+    """The benchmarked configuration at full size: the Re = 500 ring on its 256^3 bounding
+    box (542 supp / 1186 xsoln blocks), Scheme A, the step replayed as a CUDA graph.
+    After two steps G^T u on the D_supp cells is at FP32 roundoff (a property that holds
+    at any size, eq. ifherk_linsys), and the impulse is unchanged."""
+    from paper_1601_00035_gb300 import inputs
+    lgf = built()
+    B, n, R0c, dcells = 16, 256, 50.0, 10.0
+    dx = 1.0 / R0c
+    dt, re = golden("ring_dt_gamma0_over_R0sq"), 500.0
+    uinf = (0.0, 0.0, golden("ring_uinf_z_R0_over_gamma0"))
+    axis = inputs.random_axis_tilted(inputs.rng_for(4))
+    w = inputs.vortex_ring_edges(n, R0c, dcells, axis) / dx ** 2
+    supp = inputs.active_blocks(w, B, 1e-6)
+    rk = lgf.RKPlan(B, supp, dx, dt, re, scheme=0, use_graph=True)
+    xs = rk.blocks(0)
+    assert (len(supp), len(xs)) == (542, 1186)
+    t = lgf.Table(lgf.LAPLACE7, max_offset=lgf.required_max_offset(supp, xs, B))
+    pv = lgf.Plan(t, [lgf.Solve(B, 3, supp, xs, dx=dx, scale=-1.0)])
+    a = torch.zeros((len(xs), 3, B, B, B), device="cuda")
+    pv.execute([torch.from_numpy(inputs.to_blocks(w, B, supp)).cuda()], [a])
+    u = torch.zeros_like(a)
+    rk.op(lgf.OP_CURL_T, a, u)
+    v = torch.zeros_like(u)
+    I0 = rk.diagnostics(u)["I"]
+    for _ in range(2):
+        rk.step(u, v, uinf)
+        u, v = v, u
+    div = torch.zeros((len(xs), 1, B, B, B), device="cuda")
+    rk.op(lgf.OP_DIV_T, u, div)
+    d = div[:len(supp)].abs().max().item()
+    assert d < 1e-5 * u.abs().max().item() / dx, d
+    I1 = rk.diagnostics(u)["I"]
+    assert np.abs(I1 - I0).max() < 1e-5 * np.linalg.norm(I0)
