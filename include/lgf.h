@@ -80,7 +80,8 @@ typedef struct {
 } lgf_solve_desc;
 
 typedef struct {
-    int use_graph;   /* 1: capture the execute launch sequence in a CUDA graph on first use */
+    int use_graph;   /* 1: lgf_conv_execute captures its launch sequence in a CUDA graph on first
+                        use per set of buffers (FP32 plans; FP64 plans launch directly) */
     int precision;   /* 0: FP32 data and transforms (lgf_conv_execute);
                         1: FP64 data and transforms, FP64 spectrum (lgf_conv_execute_f64 only;
                            FFT lengths up to 512) */
