@@ -176,8 +176,10 @@ lgf_status ifactor_apply(lgf_plan *p, const float *x, float *y, void *stream);
  * staging is static too.  Every call shares that storage and keeps the last
  * call's contents (each call overwrites all it reads), so calls that overlap
  * on the GPU, or that run concurrently from several host threads, race.
- * The first call on a device looks up the array's device address and should
- * come before any stream capture.  B in {8, 16}; radius R_alpha <= min(B, 16).
+ * The first call on a device looks up the array's device address.  The call
+ * must not be made while `stream` is being captured into a CUDA graph (it
+ * copies its tables from static host staging that the next call overwrites):
+ * it returns LGF_ERR_ARG if it is.  B in {8, 16}; radius R_alpha <= min(B, 16).
  * Asynchronous on `stream` except for a host-to-device copy of the tables
  * from pageable memory. */
 lgf_status ifactor_apply_noalloc(double alpha, int B, int ncomp, int n_blocks, const int32_t *blocks,

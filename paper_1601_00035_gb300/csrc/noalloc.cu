@@ -12,8 +12,10 @@
 // Every call shares the array (and the host staging): calls that overlap on
 // the GPU, or run concurrently from several host threads, race.  Each call
 // rewrites everything it reads, so nothing needs clearing between calls.
-// The first call on a device resolves the array's device address there, so
-// that first call should come before any stream capture.
+// The first call on a device resolves the array's device address there.  No
+// call may be made while its stream is being captured: each call copies its
+// tables from static host staging that the next call overwrites, so a
+// captured copy would replay stale tables (checked: LGF_ERR_ARG).
 #include <cmath>
 #include <cstring>
 
@@ -128,8 +130,11 @@ extern "C" lgf_status ifactor_apply_noalloc(double alpha, int B, int ncomp, int 
             hi[a] = blocks[3 * i + a] > hi[a] ? blocks[3 * i + a] : hi[a];
         }
     const long dx = hi[0] - lo[0] + 3, dy = hi[1] - lo[1] + 3, dz = hi[2] - lo[2] + 3;
-    LGF_CHECK_ARG(dx * dy * dz <= kMaxBBox, "ifactor_apply_noalloc: bounding box of %ld cells exceeds %d",
-                  dx * dy * dz, kMaxBBox);
+    // each extent is bounded first, so that the product below cannot overflow
+    LGF_CHECK_ARG(dx <= kMaxBBox && dy <= kMaxBBox && dz <= kMaxBBox,
+                  "ifactor_apply_noalloc: bounding box extent (%ld, %ld, %ld) exceeds %d blocks", dx, dy, dz, kMaxBBox);
+    LGF_CHECK_ARG(dx * dy <= kMaxBBox && dx * dy * dz <= kMaxBBox,
+                  "ifactor_apply_noalloc: bounding box of %ld cells exceeds %d", dx * dy * dz, kMaxBBox);
     const long ncell = dx * dy * dz;
     auto cell = [&](int bx, int by, int bz) -> long {
         return ((long)(bz - lo[2] + 1) * dy + (by - lo[1] + 1)) * dx + (bx - lo[0] + 1);
@@ -192,9 +197,17 @@ extern "C" lgf_status ifactor_apply_noalloc(double alpha, int B, int ncomp, int 
     LGF_CHECK_ARG(tab_bytes + y1_bytes + y2_bytes <= kScratchBytes,
                   "ifactor_apply_noalloc: needs %zu bytes of scratch, the static limit is %zu",
                   tab_bytes + y1_bytes + y2_bytes, kScratchBytes);
+    cudaStream_t s = (cudaStream_t)stream;
+    {
+        // the tables are copied from static host staging that the next call overwrites, so a
+        // captured call would replay stale tables: refuse capture outright
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        LGF_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
+        LGF_CHECK_ARG(cap == cudaStreamCaptureStatusNone,
+                      "ifactor_apply_noalloc: must not be called while the stream is being captured");
+    }
     unsigned char *base = nullptr;
     LGF_TRY(scratch_base(&base));
-    cudaStream_t s = (cudaStream_t)stream;
     LGF_CUDA_TRY(cudaMemcpyAsync(base, g_nb, sizeof(int32_t) * 3 * (size_t)(n1 + n2 + n_blocks),
                                  cudaMemcpyHostToDevice, s));
     IfPlan ip;

@@ -400,6 +400,10 @@ def ifactor_apply_noalloc(alpha: float, B: int, ncomp: int, blocks, x, y, stream
     """y = M E_Q(alpha) M x without any device allocation (static 64 MiB scratch
     inside the library; for callers that cannot allocate device memory)."""
     b = np.ascontiguousarray(blocks, dtype=np.int32).reshape(-1, 3)
+    need = len(b) * int(ncomp) * int(B) ** 3
+    if x.numel() != need or y.numel() != need:
+        raise ValueError("ifactor_apply_noalloc: x and y must hold len(blocks) * ncomp * B^3 = %d floats "
+                         "(got %d and %d)" % (need, x.numel(), y.numel()))
     _check(load().ifactor_apply_noalloc(float(alpha), int(B), int(ncomp), len(b),
                                         b.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _ptr(x), _ptr(y),
                                         _stream(stream)))

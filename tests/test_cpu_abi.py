@@ -65,3 +65,34 @@ def test_size_rule_matches_the_library():
     L = lgf.load()
     for need in range(1, 1100):
         assert L.lgf_fft_length(need) == lgf.fft_length(need), need
+
+
+def _noalloc_status(blocks, B=16, ncomp=1, alpha=0.2):
+    """Call ifactor_apply_noalloc with placeholder device pointers: the argument
+    checks under test all run on the host before any CUDA call."""
+    import numpy as np
+    from paper_1601_00035_gb300 import lgf
+    L = lgf.load()
+    b = np.ascontiguousarray(blocks, dtype=np.int32).reshape(-1, 3)
+    st = L.ifactor_apply_noalloc(alpha, B, ncomp, len(b), b.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                 ctypes.c_void_p(256), ctypes.c_void_p(512), None)
+    return st, L.lgf_last_error().decode()
+
+
+def test_noalloc_rejects_bad_block_sets_on_the_host():
+    if not os.path.exists("/usr/local/cuda/bin/nvcc") and not os.environ.get("NVCC"):
+        pytest.skip("no CUDA toolkit")
+    from paper_1601_00035_gb300 import lgf
+    m = (1 << 20) - 1
+    # two far corners: each extent is 2^21 + 2 blocks; the product would overflow a 64-bit long
+    st, msg = _noalloc_status([[-m, -m, -m], [m, m, m]])
+    assert st == lgf.LGF_ERR_ARG and "extent" in msg
+    # extents within range but the box too large
+    st, msg = _noalloc_status([[0, 0, 0], [200, 200, 200]])
+    assert st == lgf.LGF_ERR_ARG and "bounding box" in msg
+    # duplicate blocks
+    st, msg = _noalloc_status([[0, 0, 0], [1, 0, 0], [0, 0, 0]])
+    assert st == lgf.LGF_ERR_ARG and "duplicate" in msg
+    # coordinates outside +-2^20
+    st, msg = _noalloc_status([[1 << 20, 0, 0]])
+    assert st == lgf.LGF_ERR_ARG and "coordinate" in msg

@@ -25,9 +25,9 @@ def _holed_set(seed, n):
 
 def test_noalloc_matches_planned_ifactor_twice():
     lgf = built()
-    B = 16
-    cases = [(0.2, 2, _holed_set(1, 3)), (1.0, 3, _holed_set(2, 4))]  # two calls in a row
-    for alpha, ncomp, blocks in cases:
+    # calls in a row on the shared scratch: B = 16 at R = 9 and 15, B = 8 at R = 7
+    cases = [(16, 0.2, 2, _holed_set(1, 3)), (16, 1.0, 3, _holed_set(2, 4)), (8, 0.05, 1, _holed_set(3, 4))]
+    for B, alpha, ncomp, blocks in cases:
         rng = np.random.default_rng(int(alpha * 10) + ncomp)
         x = torch.from_numpy(rng.standard_normal((len(blocks), ncomp, B, B, B)).astype(np.float32)).cuda()
         y_ref = torch.zeros_like(x)
@@ -39,7 +39,16 @@ def test_noalloc_matches_planned_ifactor_twice():
         torch.cuda.synchronize()
         a, b = y.cpu().numpy(), y_ref.cpu().numpy()
         assert np.isfinite(a).all()
-        assert rel_l2(a, b) < 1e-6
+        assert rel_l2(a, b) < 1e-6, (B, alpha)
+
+
+def test_noalloc_binding_checks_sizes():
+    lgf = built()
+    blocks = _holed_set(1, 2)
+    x = torch.zeros((len(blocks), 1, 16, 16, 16), device="cuda")
+    y = torch.zeros((len(blocks) - 1, 1, 16, 16, 16), device="cuda")
+    with pytest.raises(ValueError):
+        lgf.ifactor_apply_noalloc(0.2, 16, 1, blocks, x, y)
 
 
 def test_noalloc_rejects_oversize():
