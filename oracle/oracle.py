@@ -435,7 +435,7 @@ def ring_diagnostics(u, dx, origin_cells, xs_mask, int_mask):
     return {"I": I, "K": K, "E": E, "J": J, "X": X}
 
 
-def regrid_weights(u, uinf, dx, xs_mask, B, blocks, origin_blocks):
+def regrid_weights(u, uinf, dx, xs_mask, B, blocks, origin_blocks, parts=False):
     """Block weights of Sec. 5 eq. weight_fun on D_xsoln: W = max(mu / mu_global,
     nu / nu_global), mu = max |C u| and nu = max |G^T N~(u + u_inf)| over the block,
     from w = M C M u and q = -M G^T M N~(M (u + u_inf)) (algorithm summary, step 1).
@@ -444,7 +444,7 @@ def regrid_weights(u, uinf, dx, xs_mask, B, blocks, origin_blocks):
     last cell layer; N~ and G^T each reach one cell further, so q carries that error
     3 cells deep.
     blocks: [n][3] block coordinates (the dense box's block (0,0,0) at origin_blocks);
-    returns W per listed block."""
+    returns W per listed block (with parts=True: W, mu, nu)."""
     xs = xs_mask
     w = op_C(u * xs, dx) * xs
     uf = (u + np.asarray(uinf, dtype=float).reshape(3, 1, 1, 1)) * xs
@@ -464,7 +464,8 @@ def regrid_weights(u, uinf, dx, xs_mask, B, blocks, origin_blocks):
         mu.append(np.abs(w[(slice(None),) + sl]).max())
         nu.append(np.abs(q[sl]).max())
     mu, nu = np.array(mu), np.array(nu)
-    return np.maximum(mu / mu.max(), nu / nu.max() if nu.max() > 0 else 0.0 * nu)
+    W = np.maximum(mu / mu.max(), nu / nu.max() if nu.max() > 0 else 0.0 * nu)
+    return (W, mu, nu) if parts else W
 
 
 def vor2vel(u, masks, cube, dx):
