@@ -237,45 +237,33 @@ def cpu_oracle_rate(f, src_c, target_seconds: float, rng_seed: int = 11):
     return n * nc / dt / 1e6, n * nc, dt, thr
 
 
-def cpu_fft_rate(f, src_c, dst_c, N, u_gpu, reps: int = 2):
-    """The same solve on the host as an FP64 zero-padded FFT convolution
-    (scipy.fft on every core), the fast-CPU reference point beside the oracle's
-    direct sum.  G comes from the oracle's table.  Returns (Mpoints/s, seconds
-    per solve, threads, relative L2 difference to the GPU result at 4096
-    sampled targets)."""
-    import scipy.fft as sf
+def cpu_fft_rate(f, src_c, dst_c, u_gpu, reps: int = 2):
+    """The same solve on the host by the oracle's FP64 zero-padded FFT convolution
+    (oracle.fft_conv: scipy.fft on every core, G from the oracle's table), the
+    fast-CPU reference point beside the direct sum.  Returns (Mpoints/s, seconds
+    per solve, threads, relative L2 difference to the GPU result at 4096 sampled
+    targets)."""
     import oracle as O
     from paper_1601_00035_gb300 import inputs
     nc = f.shape[1]
-    cube = O.lgf_cube(max(N) // 2 - 1)
-    axes = []
-    for n in N:  # wrapped offsets |j| (j < n/2) or n - j; the index n/2 is never reached
-        j = np.arange(n)
-        axes.append(np.where(j == n // 2, 0, np.minimum(j, n - j)))
-    kern = cube[axes[2]][:, axes[1]][:, :, axes[0]].copy()
-    for a, n in enumerate(N):
-        sl = [slice(None)] * 3
-        sl[2 - a] = n // 2
-        kern[tuple(sl)] = 0.0
+    s, t = np.asarray(src_c), np.asarray(dst_c)
+    s0, s1 = s.min(0) * B, (s.max(0) + 1) * B
+    t0, t1 = t.min(0) * B, (t.max(0) + 1) * B
     workers = os.cpu_count() or 1
-    khat = sf.rfftn(kern, workers=workers)
-    s0 = np.asarray(src_c).min(0) * B
-    tgt = inputs.block_points(dst_c, B)
-    rng = np.random.default_rng(5)
-    sel = rng.choice(len(tgt), 4096, replace=False)
-    tz, ty, tx = [(tgt[sel, a] - s0[a]) % N[a] for a in (2, 1, 0)]
-    times, diff = [], 0.0
+    times = []
     for _ in range(reps):
-        t0 = time.perf_counter()
-        out = []
-        for c in range(nc):
-            F = np.zeros((N[2], N[1], N[0]))
-            for b, (bx, by, bz) in enumerate(np.asarray(src_c) * B - s0):
-                F[bz:bz + B, by:by + B, bx:bx + B] = f[b, c]
-            out.append(-sf.irfftn(sf.rfftn(F, workers=workers) * khat, s=F.shape, workers=workers))
-        times.append(time.perf_counter() - t0)
+        a = time.perf_counter()
+        F = np.zeros((nc, *(s1 - s0)[::-1]))
+        for b, (bx, by, bz) in enumerate(s * B - s0):
+            F[:, bz:bz + B, by:by + B, bx:bx + B] = f[b]
+        U = -O.fft_conv(F, s0, t0, tuple((t1 - t0)[::-1]), workers=workers)
+        times.append(time.perf_counter() - a)
+    tgt = inputs.block_points(dst_c, B)
+    sel = np.random.default_rng(5).choice(len(tgt), 4096, replace=False)
+    tx, ty, tz = [tgt[sel, a] - t0[a] for a in range(3)]
+    diff = 0.0
     for c in range(nc):
-        ref = out[c][tz, ty, tx]
+        ref = U[c][tz, ty, tx]
         got = u_gpu[(sel // B ** 3), c].reshape(-1, B ** 3)[np.arange(len(sel)), sel % B ** 3]
         diff = max(diff, float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
     dt = min(times)
@@ -427,9 +415,10 @@ def bench_gpu(args):
         rate, pts, dt, thr = cpu_oracle_rate(f, src_c, args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
                "sample": "FP64 direct sum (oracle) at %d random target points x 3 components, %.1f s" % (pts // 3, dt)}
-        frate, fdt, fthr, fdiff = cpu_fft_rate(f, src_c, dst_c, geom["N"], d_dst.cpu().numpy())
+        frate, fdt, fthr, fdiff = cpu_fft_rate(f, src_c, dst_c, d_dst.cpu().numpy())
         cpu_fft = {"value": round(frate, 2), "unit": UNIT, "cores": fthr,
-                   "kind": "FP64 zero-padded FFT convolution on the host (scipy.fft, G from the oracle's table)",
+                   "kind": "FP64 zero-padded FFT convolution on the host (oracle.fft_conv: scipy.fft, G from the "
+                           "oracle's table)",
                    "sample": "the full solve, best of 2: %.2f s" % fdt, "rel_l2_vs_gpu": fdiff}
     cfg = dict(cfg)
     cfg.update({"fft_grid": geom["N"], "execution": "one stream per component, launch sequence replayed as a CUDA graph",

@@ -31,7 +31,7 @@ __all__ = [
     "op_Dbar", "op_L", "op_N", "residual_L", "WATSON_W", "num_threads", "SCHEME_A", "SCHEME_B", "SCHEME_C",
     "SCHEMES", "shifted_tableau",
     "block_mask", "ifactor_masked", "poisson_masked", "if_herk_step", "lgf_points", "ifactor_tail", "rk_qmax",
-    "vor2vel", "ring_diagnostics", "regrid_weights",
+    "vor2vel", "ring_diagnostics", "regrid_weights", "fft_conv",
 ]
 
 # Watson's integral for the simple cubic lattice, closed form (Watson 1939):
@@ -189,6 +189,44 @@ def direct_conv_box(cube: np.ndarray, f: np.ndarray, tgt_xyz: np.ndarray, origin
     z, y, x = np.nonzero(f)
     src = np.stack([x, y, z], axis=1).astype(np.int32) + np.asarray(origin, dtype=np.int32)
     return direct_conv(cube, src, f[z, y, x], tgt_xyz)
+
+
+def fft_conv(f: np.ndarray, src_origin, tgt_origin, tgt_shape, workers: int | None = None) -> np.ndarray:
+    """u(n) = sum_m G(n - m) f(m) (eq. dpoisson_conv on the unit lattice) for every n of
+    the box tgt_origin + [0, tgt_shape), by one FP64 linear convolution through
+    zero-padded FFTs (the FFT is a library step; G comes from lgf_cube over every offset
+    the two boxes produce, so nothing wraps).
+
+    f: dense [z, y, x] sources whose point (0, 0, 0) is src_origin (x, y, z), or
+    [c, z, y, x] for c independent components (the kernel is transformed once);
+    tgt_shape: (nz, ny, nx).  Returns u[z, y, x] (or [c, z, y, x]).  Pinned against
+    direct_conv."""
+    import scipy.fft as sf
+    f = np.asarray(f, dtype=np.float64)
+    if f.ndim == 4:
+        return np.stack(list(_fft_conv_many(f, src_origin, tgt_origin, tgt_shape, workers)))
+    return next(_fft_conv_many(f[None], src_origin, tgt_origin, tgt_shape, workers))
+
+
+def _fft_conv_many(fs, src_origin, tgt_origin, tgt_shape, workers):
+    import scipy.fft as sf
+    f = fs[0]
+    S0 = np.asarray(src_origin, dtype=np.int64)
+    T0 = np.asarray(tgt_origin, dtype=np.int64)
+    Sn = np.array(f.shape[::-1], dtype=np.int64)          # (x, y, z) extents
+    Tn = np.array(tuple(tgt_shape)[::-1], dtype=np.int64)
+    dmin = T0 - (S0 + Sn - 1)                              # smallest offset n - m per axis
+    dmax = T0 + Tn - 1 - S0                                # largest
+    cube = lgf_cube(int(max(np.abs(dmin).max(), np.abs(dmax).max())))
+    ax = [np.abs(np.arange(dmin[a], dmax[a] + 1)) for a in range(3)]
+    k = cube[np.ix_(ax[2], ax[1], ax[0])]                  # k[i] = G(dmin + i), [z, y, x]
+    L = [f.shape[i] + k.shape[i] - 1 for i in range(3)]     # full linear convolution
+    w = workers or os.cpu_count() or 1
+    kh = sf.rfftn(k, L, workers=w)
+    st = (Sn - 1)[::-1]                                    # index of n = T0: n - S0 - dmin
+    for fc in fs:
+        U = sf.irfftn(sf.rfftn(fc, L, workers=w) * kh, L, workers=w)
+        yield U[st[0]:st[0] + tgt_shape[0], st[1]:st[1] + tgt_shape[1], st[2]:st[2] + tgt_shape[2]].copy()
 
 
 def ifactor_direct(g: np.ndarray, x: np.ndarray, tgt_xyz: np.ndarray) -> np.ndarray:

@@ -166,6 +166,22 @@ def two_ring_velocity(cfg: int = 3, n: int = 128):
     return u
 
 
+def two_rings_vorticity(cfg: int = 3, n: int = 128, sigma: float = 3.0):
+    """Edge-sampled vorticity of the two seeded Gaussian-core rings of the 128^3
+    integrating-factor workload (circulation 1 each, centres within 16 cells of the
+    box centre, R ~ U[16, 28], sigma = 3, tilted as in the 128^3 ring case): w[q, z, y, x].
+    The velocity u = C^T a, a = -L^{-1} w, is left to the caller (it needs the Poisson
+    solve)."""
+    rng = rng_for(cfg)
+    w = np.zeros((3, n, n, n))
+    for _ in range(2):
+        c = n / 2 + rng.uniform(-16, 16, size=3)
+        R = rng.uniform(16, 28)
+        axis = random_axis_tilted(rng)
+        w += vortex_ring_edges(n, R, sigma, axis, centre=c)
+    return w
+
+
 def ragged_ring_sources(nsolve: int = 64, emin: int = 24, emax: int = 192, cfg: int = 5):
     """Ragged batch: per solve an edge e ~ round(exp(U[ln emin, ln emax])), a ring with
     R ~ U[4, min(40, (e/2 - 2)/1.75)], sigma = R/8, axis uniform on S^2, centred in the box;

@@ -16,7 +16,6 @@ def test_cpu_fft_matches_direct_sum():
     from paper_1601_00035_gb300 import inputs
     f, src_c, dst_c, _ = bench.workload()
     B = bench.B
-    geom = bench.geometry(src_c, dst_c, 3)
     # the direct sum at the targets cpu_fft_rate samples, in the place of the GPU field
     tgt = inputs.block_points(dst_c, B)
     sel = np.random.default_rng(5).choice(len(tgt), 4096, replace=False)
@@ -28,5 +27,5 @@ def test_cpu_fft_matches_direct_sum():
         nz = v != 0
         flat = u[:, c].reshape(len(dst_c), -1)
         flat[sel // B ** 3, sel % B ** 3] = O.direct_conv(cube, pts[nz], -v[nz], tgt[sel].astype(np.int32))
-    rate, dt, threads, diff = bench.cpu_fft_rate(f, src_c, dst_c, geom["N"], u, reps=1)
+    rate, dt, threads, diff = bench.cpu_fft_rate(f, src_c, dst_c, u, reps=1)
     assert diff < 1e-13 and rate > 0
