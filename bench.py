@@ -13,8 +13,11 @@ between steps, outside the events.  Barrier + synchronize on both sides; the
 max over ranks is reported.  Under torchrun every rank runs its own replica of
 the solve (weak scaling, no data-path collective).
 
-Extra keys: roofline (dominant kernel, bytes moved by that pass / its mean
-event time, against the measured HBM copy bandwidth), cpu_baseline (the FP64
+Extra keys: roofline (dominant kernel: the path's algorithmic 8 B per target
+point and component of one launch / its mean event time, against the measured
+HBM copy bandwidth; the whole step on the same rule), compute_roofline (the
+dominant pass's algorithmic flops against the FP32 FMA rate measured in the
+run by lgf_measure_peak), cpu_baseline (the FP64
 oracle's direct sum on a bounded sample of target points, host cores),
 e2e (the same solve through lgf_conv_execute_host with pinned host buffers,
 copies included), gpu_launches, clocks (nvidia-smi sampled during the run).
@@ -26,11 +29,9 @@ of target points.
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import math
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -164,32 +165,21 @@ def geometry(src_c, dst_c, ncomp):
     return {"Es": Es, "Et": Et, "N": N, "ncomp": ncomp, "nsrc": len(s), "ndst": len(t)}
 
 
-KERNEL_SOURCES = ("poisson.cu", "fft.cuh", "common.cuh")
+def pass_flops(plan_geom):
+    """Algorithmic flops of each FFT pass of one launch: 5 n log2 n per complex
+    n-point transform (a real n-point transform counts as half of one), two
+    transforms per z line plus 2 flops per point of the real spectral multiply."""
+    g = plan_geom
+    nc, N, Es, Et = g["ncomp"], g["N"], g["Es"], g["Et"]
+    KX = N[0] // 2 + 1
 
-
-def kernel_source_sha() -> str:
-    """sha256 prefix over the sources the FFT passes are compiled from."""
-    h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1601_00035_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
-
-
-def ncu_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
-    summary was taken on the current kernel sources (sha256 prefix recorded)."""
-    path = os.path.join(ROOT, "profiles", "poisson_ring128_ncu.md")
-    try:
-        txt = open(path).read()
-        sha = kernel_source_sha()
-    except OSError:
-        return None
-    m = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
-    if not m or m.group(1) != sha:
-        return None
-    m = re.search(r"traffic\[%s\]:\s*([0-9.e+]+)" % re.escape(kernel), txt)
-    return float(m.group(1)) if m else None
+    def c(n):
+        return 5.0 * n * math.log2(n)
+    return {"x_fwd_gather_r2c": nc * Es[2] * Es[1] * c(N[0]) / 2,
+            "y_fwd": nc * Es[2] * KX * c(N[1]),
+            "z_fwd_mul_inv": nc * N[1] * KX * (2 * c(N[2]) + 2 * N[2]),
+            "y_inv": nc * Et[2] * KX * c(N[1]),
+            "x_inv_c2r_scatter": nc * Et[2] * Et[1] * c(N[0]) / 2}
 
 
 def oracle_sampler(f, src_c, rng_seed: int = 11):
@@ -325,6 +315,9 @@ def bench_gpu(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     pts_per_step = len(dst_c) * B ** 3 * 3
 
+    # measured arithmetic peaks (compute roofline of the FFT passes), before the timed region
+    peaks_tf = {k: round(lgf.measure_peak(v, 200.0), 2) for k, v in
+                (("fp32_fma", lgf.PEAK_FP32), ("fp32x2_fma", lgf.PEAK_FP32X2), ("fp64_fma", lgf.PEAK_FP64))}
     sampler = clock_sampler(torch.cuda.current_device()) if r == 0 else None
     time.sleep(0.5)
     for _ in range(args.warmup):
@@ -393,22 +386,44 @@ def bench_gpu(args):
 
     value = job_rate(pts_per_step, args.steps, ws, dev_ms / 1e3)
     e2e_value = job_rate(pts_per_step, e2e_steps, ws, e2e_s)
-    # roofline of the dominant kernel
-    pb = pass_bytes(geometry(src_c, dst_c, 1))  # one launch moves one component
+    # roofline of the dominant kernel, on the algorithmic bytes of the path: 8 B per target
+    # point (4 B FP32 source in, 4 B result out); one launch of a pass is one component
+    g1 = geometry(src_c, dst_c, 1)
+    pb = pass_bytes(g1)
+    pf = pass_flops(g1)
     dom = max(kt, key=lambda k: kt[k][1])
     launches, tot_ms = kt[dom]
     per_launch_ms = tot_ms / launches
     hbm, src_kind = peaks()
-    achieved = pb[dom] / (per_launch_ms / 1e3) / 1e9
-    traffic = ncu_traffic(dom)
+    alg_bytes = 8 * len(dst_c) * B ** 3            # one component
+    achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
+    step_gbs = 8 * pts_per_step / (dev_ms / args.steps / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(achieved / hbm, 4), "traffic": traffic,
-            "algorithmic_bytes_per_launch": pb[dom], "mean_launch_ms": round(per_launch_ms, 5),
+            "frac": round(achieved / hbm, 4), "traffic": None,
+            "algorithmic_bytes_per_launch": alg_bytes, "mean_launch_ms": round(per_launch_ms, 5),
+            "bytes_rule": "8 B per target point and component (FP32 source read + result write), one component "
+                          "per launch",
+            "step": {"achieved": round(step_gbs, 1), "frac": round(step_gbs / hbm, 4),
+                     "rule": "8 B per target point and component over the whole timed step"},
+            "pass_workspace": {"bytes_per_launch": pb[dom],
+                               "achieved": round(pb[dom] / (per_launch_ms / 1e3) / 1e9, 1),
+                               "frac": round(pb[dom] / (per_launch_ms / 1e3) / 1e9 / hbm, 4),
+                               "rule": "the pass's own input and output arrays (complex FP32 workspaces, "
+                                       "kernel spectrum): bytes of this algorithm, not of the path"},
+            "traffic_note": "DRAM bytes per launch (ncu) are in profiles/poisson_ring128_ncu.md",
             "launch_timing": "CUDA events around each launch (one pass of one component) in K profiled steps "
                              "after the timed ones; profiling runs the components one after another",
             "peak_source": src_kind + " (MEASURED_PEAKS.json hbm_gbs)" if src_kind == "measured" else src_kind}
+    comp_tf = pf[dom] / (per_launch_ms / 1e3) / 1e12
+    compute = {"bound": "fp32", "kernel": dom, "achieved": round(comp_tf, 2), "peak": peaks_tf["fp32_fma"],
+               "unit": "TFLOP/s", "frac": round(comp_tf / peaks_tf["fp32_fma"], 4),
+               "flops_per_launch": pf[dom],
+               "flop_rule": "5 n log2 n per complex n-point transform (real: half), 2 per spectral-multiply point",
+               "peaks_measured_tflops": peaks_tf,
+               "peak_source": "lgf_measure_peak: FMA chains on every SM, CUDA events, measured in this run"}
     shares = {k: {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / sum(x[1] for x in kt.values()), 4),
-                  "gbs": round(pb[k] * v[0] / (v[1] / 1e3) / 1e9, 1)} for k, v in kt.items()}
+                  "workspace_gbs": round(pb[k] * v[0] / (v[1] / 1e3) / 1e9, 1),
+                  "tflops": round(pf[k] * v[0] / (v[1] / 1e3) / 1e12, 2)} for k, v in kt.items()}
     # CPU baseline: oracle on a bounded sample (rank 0, N=1 only)
     cpu = cpu_fft = None
     if ws == 1 and not args.no_cpu_baseline:
@@ -430,7 +445,7 @@ def bench_gpu(args):
     line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(dev_ms / args.steps, 5), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
-            "roofline": roof, "kernels": shares, "cpu_baseline": cpu, "cpu_fft_baseline": cpu_fft,
+            "roofline": roof, "compute_roofline": compute, "kernels": shares, "cpu_baseline": cpu, "cpu_fft_baseline": cpu_fft,
             "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": int(f.nbytes),
                     "d2h_bytes_per_step": int(h_dst.numel() * 4)},
             "gpu_launches": int(sum(v[0] for v in kt.values())), "clocks": clocks,

@@ -205,6 +205,16 @@ lgf_status lgf_plan_kernel_count(lgf_plan *p, int *count);
  * until the plan is destroyed), launches and summed device milliseconds. */
 lgf_status lgf_plan_kernel_times(lgf_plan *p, int i, const char **name, long long *launches, double *total_ms);
 
+/* Measured arithmetic rate of the current GPU, the compute roofline of the FFT,
+ * spectral-multiply and integrating-factor passes (the paper has no counterpart:
+ * a measurement helper).  kind 0: FP32 fused multiply-add (2 flops each);
+ * 1: paired FP32 fused multiply-add, fma.rn.f32x2 (4 flops each); 2: FP64 fused
+ * multiply-add (2 flops each).  Eight independent register-resident FMA chains
+ * per thread on 8 x 256-thread blocks per SM run for about `ms` milliseconds
+ * (0 < ms <= 10000), timed with CUDA events on `stream`; *tflops receives the
+ * rate in TFLOP/s.  Allocates a small device buffer; synchronises `stream`. */
+lgf_status lgf_measure_peak(int kind, double ms, double *tflops, void *stream);
+
 /* ---------------------------------------------------------------------------
  * One time step of the IF-HERK scheme on a finite block set (Sec. 3.2
  * algorithm, Sec. 3.3 eq. proj_final, Sec. 5 xIF-HERK masks), Scheme A of

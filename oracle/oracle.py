@@ -220,7 +220,8 @@ def _fft_conv_many(fs, src_origin, tgt_origin, tgt_shape, workers):
     cube = lgf_cube(int(max(np.abs(dmin).max(), np.abs(dmax).max())))
     ax = [np.abs(np.arange(dmin[a], dmax[a] + 1)) for a in range(3)]
     k = cube[np.ix_(ax[2], ax[1], ax[0])]                  # k[i] = G(dmin + i), [z, y, x]
-    L = [f.shape[i] + k.shape[i] - 1 for i in range(3)]     # full linear convolution
+    # full linear convolution; lengths rounded up to fast FFT sizes (extra zeros change nothing)
+    L = [sf.next_fast_len(f.shape[i] + k.shape[i] - 1, real=True) for i in range(3)]
     w = workers or os.cpu_count() or 1
     kh = sf.rfftn(k, L, workers=w)
     st = (Sn - 1)[::-1]                                    # index of n = T0: n - S0 - dmin

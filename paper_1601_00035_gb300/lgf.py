@@ -118,6 +118,8 @@ _SIGS = {
     "lgf_last_error": (ctypes.c_char_p, []),
     "lgf_version": (ctypes.c_char_p, []),
     "lgf_fft_length": (ctypes.c_int, [ctypes.c_int]),
+    "lgf_measure_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.c_void_p]),
 }
 
 
@@ -407,6 +409,16 @@ def ifactor_apply_noalloc(alpha: float, B: int, ncomp: int, blocks, x, y, stream
     _check(load().ifactor_apply_noalloc(float(alpha), int(B), int(ncomp), len(b),
                                         b.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _ptr(x), _ptr(y),
                                         _stream(stream)))
+
+
+PEAK_FP32, PEAK_FP32X2, PEAK_FP64 = 0, 1, 2
+
+
+def measure_peak(kind: int, ms: float = 200.0, stream=None) -> float:
+    """Measured FMA rate of the current GPU in TFLOP/s (lgf_measure_peak)."""
+    out = ctypes.c_double()
+    _check(load().lgf_measure_peak(int(kind), float(ms), ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 def version() -> str:

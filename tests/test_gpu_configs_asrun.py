@@ -188,7 +188,7 @@ def test_stage_operators_full_size_sampled():
     centres = pts_all[rng.choice(len(pts_all), 1024, replace=False)].astype(np.int64)
     win, mask = _windows(f, xs, B, centres, 2)
     soln = set(map(tuple, np.asarray(supp).tolist()))
-    in_soln = np.array([tuple(p // B) in soln for p in centres.tolist()])
+    in_soln = np.array([tuple(p) in soln for p in (centres // B).tolist()])
     uinf = (0.0, 0.0, -0.18686)
     coef = -0.37
     cases = [(lgf.OP_CURL, 3, lambda v, m: O.op_C(v * m, dx)),
