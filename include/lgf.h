@@ -80,12 +80,23 @@ typedef struct {
 } lgf_solve_desc;
 
 typedef struct {
-    int use_graph;   /* 1: lgf_conv_execute captures its launch sequence in a CUDA graph on first
-                        use per set of buffers (FP32 plans; FP64 plans launch directly) */
-    int precision;   /* 0: FP32 data and transforms (lgf_conv_execute);
-                        1: FP64 data and transforms, FP64 spectrum (lgf_conv_execute_f64 only;
-                           FFT lengths up to 512) */
-    int reserved[6]; /* must be zero */
+    int use_graph;      /* 1: lgf_conv_execute captures its launch sequence in a CUDA graph on first
+                           use per set of buffers (FP32 plans; FP64 plans launch directly) */
+    int precision;      /* 0: FP32 data and transforms (lgf_conv_execute);
+                           1: FP64 data and transforms, FP64 spectrum (lgf_conv_execute_f64 only;
+                              FFT lengths up to 512; method 0 only) */
+    int method;         /* 0: whole-box zero-padded FFT convolution (exact up to rounding);
+                           1: block-sparse split solve (Sec. 2.2 "to tolerance eps"): the LGF
+                              split as G = G_near + G_far at split time a of its Bessel form,
+                              G_near convolved block pair by block pair (16^3 blocks, offsets
+                              up to 2 blocks), G_far on the coarse lattice of spacing 2 through
+                              8-point Lagrange interpolation and anterpolation; one solve, B = 16;
+                              cost follows the active blocks; relative L2 error ~1e-7..1e-6;
+                           2: autotune: plan both and keep the faster (one timed execution each) */
+    int far_precision;  /* method 1: 0 FP32 interpolation; 1 reserved */
+    double split_alpha; /* method 1: the split time a; 0 takes 20 (the error and the near radius
+                           it sets are stated in DESIGN) */
+    int reserved[2];    /* must be zero */
 } lgf_plan_opts;
 
 /* ---------------------------------------------------------------------------
@@ -132,6 +143,11 @@ void lgf_table_destroy(lgf_table *t);
  * ------------------------------------------------------------------------- */
 lgf_status lgf_conv_plan(const lgf_table *t, const lgf_solve_desc *solves, int n_solves,
                          const lgf_plan_opts *opts, void *stream, lgf_plan **out);
+
+/* The method a Poisson plan executes (0 whole box, 1 block-sparse split; -1 for NULL).  For
+ * an autotuned plan (opts->method = 2), *ms_whole_box and *ms_split receive the device times
+ * of the two candidates measured at plan time (-1 where not timed); either pointer may be NULL. */
+int lgf_plan_method(const lgf_plan *p, double *ms_whole_box, double *ms_split);
 
 /* Device bytes held by the plan (workspaces + spectra + lookups). */
 lgf_status lgf_plan_workspace_bytes(const lgf_plan *p, size_t *bytes);

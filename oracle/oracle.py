@@ -113,9 +113,11 @@ def lgf_octant(K: int, t_lo: float = QUAD_DEFAULT["t_lo"], T: float = QUAD_DEFAU
 
 
 @functools.lru_cache(maxsize=4)
-def lgf_cube(K: int) -> np.ndarray:
-    """Dense table D[|dz|, |dy|, |dx|] = G(dx, dy, dz), 0..K on each axis."""
-    oct_ = np.ascontiguousarray(lgf_octant(K))
+def lgf_cube(K: int, t_lo: float = QUAD_DEFAULT["t_lo"]) -> np.ndarray:
+    """Dense table D[|dz|, |dy|, |dx|] = G(dx, dy, dz), 0..K on each axis.  With t_lo above
+    its default the Bessel-form integral starts there: -int_{t_lo}^inf prod_i i_{n_i}(t) dt
+    (the far part of a split of G at time t_lo)."""
+    oct_ = np.ascontiguousarray(lgf_octant(K, t_lo=t_lo))
     cube = np.zeros((K + 1, K + 1, K + 1))
     lib().oracle_octant_to_cube(int(K), _d(oct_), _d(cube))
     cube.setflags(write=False)

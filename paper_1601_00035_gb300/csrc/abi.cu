@@ -109,6 +109,8 @@ void free_plan(lgf_plan *p)
     cudaFree(p->ifp.y2);
     if (p->graph) cudaGraphExecDestroy(p->graph);
     if (p->rk) free_rk(p->rk);
+    if (p->split) free_split(p->split);
+    if (p->sub) free_plan(p->sub);
     delete p;
 }
 
@@ -642,6 +644,132 @@ static lgf_status plan_ifactor(lgf_plan *p, const lgf_table *t, const lgf_solve_
     return LGF_OK;
 }
 
+// A split plan keeps one PoissonSolve with the target neighbour tables of the FP64
+// residual check, and host staging buffers for lgf_conv_execute_host.
+static lgf_status plan_split_extras(lgf_plan *p, const lgf_solve_desc &d, cudaStream_t s)
+{
+    PoissonSolve ps;
+    std::memset(&ps.g, 0, sizeof(ps.g));
+    ps.g.B = d.B;
+    ps.g.ncomp = d.ncomp;
+    ps.g.nc = d.ncomp;
+    ps.nsrc = d.n_src;
+    ps.ndst = d.n_dst;
+    ps.dx = d.dx;
+    ps.scale = d.scale;
+    ps.src_coords.assign(d.src_blocks, d.src_blocks + 3 * d.n_src);
+    ps.dst_coords.assign(d.dst_blocks, d.dst_blocks + 3 * d.n_dst);
+    std::vector<int> nbr = neighbour_table(d.dst_blocks, d.n_dst);
+    std::vector<int> d2s(d.n_dst, -1);
+    {
+        std::unordered_map<int64_t, int> m;
+        for (int b = 0; b < d.n_src; b++) m[pack(d.src_blocks[3 * b], d.src_blocks[3 * b + 1], d.src_blocks[3 * b + 2])] = b;
+        for (int b = 0; b < d.n_dst; b++) {
+            auto it = m.find(pack(d.dst_blocks[3 * b], d.dst_blocks[3 * b + 1], d.dst_blocks[3 * b + 2]));
+            if (it != m.end()) d2s[b] = it->second;
+        }
+    }
+    p->solves.push_back(ps);
+    PoissonSolve &q = p->solves.back();
+    LGF_TRY(dalloc(&q.d_dst_nbr, nbr.size(), p->bytes));
+    LGF_TRY(dalloc(&q.d_dst2src, d2s.size(), p->bytes));
+    LGF_TRY(upload(q.d_dst_nbr, nbr, s));
+    LGF_TRY(upload(q.d_dst2src, d2s, s));
+    LGF_TRY(dalloc(&p->d_acc, 2, p->bytes));
+    const size_t B3 = (size_t)d.B * d.B * d.B;
+    LGF_TRY(dalloc(&p->split->d_stage_src, (size_t)d.n_src * d.ncomp * B3, p->bytes));
+    LGF_TRY(dalloc(&p->split->d_stage_dst, (size_t)d.n_dst * d.ncomp * B3, p->bytes));
+    LGF_CUDA_TRY(cudaStreamSynchronize(s));
+    return LGF_OK;
+}
+
+static lgf_status check_split_solve(const lgf_solve_desc &d)
+{
+    LGF_CHECK_ARG(d.ncomp >= 1 && d.ncomp <= 3 && d.n_src >= 1 && d.n_dst >= 1 && d.src_blocks && d.dst_blocks &&
+                      d.dx > 0.0 && std::isfinite(d.dx) && std::isfinite(d.scale),
+                  "lgf_conv_plan: bad solve description");
+    LGF_CHECK_ARG(coords_ok(d.src_blocks, d.n_src) && coords_ok(d.dst_blocks, d.n_dst),
+                  "lgf_conv_plan: block coordinate out of range");
+    LGF_CHECK_ARG(!has_duplicates(d.src_blocks, d.n_src) && !has_duplicates(d.dst_blocks, d.n_dst),
+                  "lgf_conv_plan: duplicate block");
+    return LGF_OK;
+}
+
+// Mean device time of a few executions of plan q (after one untimed run) on scratch buffers.
+static lgf_status time_plan(lgf_plan *q, const lgf_solve_desc &d, cudaStream_t s, double *ms)
+{
+    const size_t B3 = (size_t)d.B * d.B * d.B;
+    float *x = nullptr, *y = nullptr;
+    LGF_CUDA_TRY(cudaMalloc(&x, (size_t)d.n_src * d.ncomp * B3 * sizeof(float)));
+    if (cudaMalloc(&y, (size_t)d.n_dst * d.ncomp * B3 * sizeof(float)) != cudaSuccess) {
+        cudaFree(x);
+        set_error("autotune scratch allocation failed");
+        return LGF_ERR_OOM;
+    }
+    cudaEvent_t a = nullptr, b = nullptr;
+    lgf_status st = LGF_OK;
+    if (cudaMemsetAsync(x, 0, (size_t)d.n_src * d.ncomp * B3 * sizeof(float), s) != cudaSuccess ||
+        cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+        st = LGF_ERR_CUDA;
+    const float *src[1] = {x};
+    float *dst[1] = {y};
+    if (st == LGF_OK) st = lgf_conv_execute(q, src, dst, s);
+    const int reps = 3;
+    if (st == LGF_OK) {
+        cudaEventRecord(a, s);
+        for (int r = 0; r < reps && st == LGF_OK; r++) st = lgf_conv_execute(q, src, dst, s);
+        cudaEventRecord(b, s);
+        float t = 0.f;
+        if (st == LGF_OK && (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&t, a, b) != cudaSuccess))
+            st = LGF_ERR_CUDA;
+        *ms = t / reps;
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFree(x);
+    cudaFree(y);
+    if (st == LGF_ERR_CUDA) set_error("autotune timing failed");
+    return st;
+}
+
+// method 2: plan the whole-box and the split solve, time one of each, keep the faster
+// as the plan's executing sub-plan.  A solve the split method does not take (B != 16)
+// keeps the whole-box plan.
+static lgf_status autotune_plan(lgf_plan *p, const lgf_table *t, const lgf_solve_desc *solves, const lgf_plan_opts *opts,
+                                cudaStream_t s)
+{
+    lgf_plan_opts o = *opts;
+    o.method = 0;
+    lgf_plan *a = nullptr, *b = nullptr;
+    LGF_TRY(lgf_conv_plan(t, solves, 1, &o, (void *)s, &a));
+    p->auto_ms[0] = p->auto_ms[1] = -1.0;
+    lgf_status st = time_plan(a, solves[0], s, &p->auto_ms[0]);
+    if (st != LGF_OK) {
+        lgf_plan_destroy(a);
+        return st;
+    }
+    if (solves[0].B == 16) {
+        o.method = 1;
+        st = lgf_conv_plan(t, solves, 1, &o, (void *)s, &b);
+        if (st == LGF_OK) st = time_plan(b, solves[0], s, &p->auto_ms[1]);
+        if (st != LGF_OK) {  // the split plan does not fit (e.g. its coarse box): keep the whole box
+            lgf_plan_destroy(b);
+            b = nullptr;
+            clear_error();
+        }
+    }
+    if (b && p->auto_ms[1] < p->auto_ms[0]) {
+        lgf_plan_destroy(a);
+        p->sub = b;
+    } else {
+        lgf_plan_destroy(b);
+        p->sub = a;
+    }
+    p->method = p->sub->method;
+    p->bytes = p->sub->bytes;
+    return LGF_OK;
+}
+
 lgf_status lgf_conv_plan(const lgf_table *t, const lgf_solve_desc *solves, int n_solves, const lgf_plan_opts *opts,
                          void *stream, lgf_plan **out)
 {
@@ -650,8 +778,14 @@ lgf_status lgf_conv_plan(const lgf_table *t, const lgf_solve_desc *solves, int n
     *out = nullptr;
     LGF_CHECK_ARG(t != nullptr && solves != nullptr && n_solves >= 1, "lgf_conv_plan: bad table/solves/n_solves");
     if (opts) {
-        for (int i = 0; i < 6; i++) LGF_CHECK_ARG(opts->reserved[i] == 0, "lgf_conv_plan: reserved option fields must be zero");
+        for (int i = 0; i < 2; i++) LGF_CHECK_ARG(opts->reserved[i] == 0, "lgf_conv_plan: reserved option fields must be zero");
         LGF_CHECK_ARG(opts->precision == 0 || opts->precision == 1, "lgf_conv_plan: precision must be 0 or 1");
+        LGF_CHECK_ARG(opts->method >= 0 && opts->method <= 2, "lgf_conv_plan: method must be 0, 1 or 2");
+        LGF_CHECK_ARG(opts->far_precision == 0, "lgf_conv_plan: far_precision must be 0");
+        LGF_CHECK_ARG(opts->method == 0 || (opts->precision == 0 && t->kind == LGF_KERNEL_LAPLACE7 && n_solves == 1),
+                      "lgf_conv_plan: methods 1 and 2 take one FP32 Poisson solve");
+        LGF_CHECK_ARG(opts->split_alpha == 0.0 || (opts->split_alpha >= 1.0 && opts->split_alpha <= 64.0),
+                      "lgf_conv_plan: split_alpha must be 0 or in [1, 64]");
     }
     const int dev = current_device();
     if (dev != t->device) {
@@ -670,14 +804,35 @@ lgf_status lgf_conv_plan(const lgf_table *t, const lgf_solve_desc *solves, int n
     p->table = t;
     p->use_graph = opts ? opts->use_graph : 0;
     p->precision = opts ? opts->precision : 0;
-    lgf_status st = t->kind == LGF_KERNEL_LAPLACE7 ? plan_poisson(p, t, solves, n_solves, s)
-                                                   : plan_ifactor(p, t, solves, n_solves, s);
+    const int method = opts ? opts->method : 0;
+    const double alpha = opts && opts->split_alpha > 0.0 ? opts->split_alpha : 20.0;
+    lgf_status st;
+    if (t->kind != LGF_KERNEL_LAPLACE7) {
+        st = plan_ifactor(p, t, solves, n_solves, s);
+    } else if (method == 1) {
+        st = check_split_solve(solves[0]);
+        p->method = 1;
+        if (st == LGF_OK) st = plan_split(p, solves[0], alpha, s);
+        if (st == LGF_OK) st = plan_split_extras(p, solves[0], s);
+    } else if (method == 2) {
+        st = autotune_plan(p, t, solves, opts, s);
+    } else {
+        st = plan_poisson(p, t, solves, n_solves, s);
+    }
     if (st != LGF_OK) {
         free_plan(p);
         return st;
     }
     *out = p;
     return LGF_OK;
+}
+
+int lgf_plan_method(const lgf_plan *p, double *ms_whole_box, double *ms_split)
+{
+    if (!p) return -1;
+    if (ms_whole_box) *ms_whole_box = p->auto_ms[0];
+    if (ms_split) *ms_split = p->auto_ms[1];
+    return p->method;
 }
 
 lgf_status lgf_plan_workspace_bytes(const lgf_plan *p, size_t *bytes)
@@ -781,6 +936,13 @@ lgf_status lgf_conv_execute_f64(lgf_plan *p, const double *const *src, double *c
     return LGF_OK;
 }
 
+// FP32 execution of a whole-box or split plan (capturing: inside a stream capture)
+static lgf_status run_fp32(lgf_plan *p, const float *const *src, float *const *dst, cudaStream_t s, bool capturing)
+{
+    if (p->split) return run_split(p, src[0], dst[0], s, capturing ? nullptr : &p->prof);
+    return run_poisson(p, src, dst, s, capturing);
+}
+
 lgf_status lgf_conv_execute(lgf_plan *p, const float *const *src, float *const *dst, void *stream)
 {
     clear_error();
@@ -793,13 +955,15 @@ lgf_status lgf_conv_execute(lgf_plan *p, const float *const *src, float *const *
         set_error("lgf_conv_execute: FP64 plan (use lgf_conv_execute_f64)");
         return LGF_ERR_STATE;
     }
-    for (size_t i = 0; i < p->solves.size(); i++)
+    if (p->sub) return lgf_conv_execute(p->sub, src, dst, stream);
+    const size_t nsol = p->split ? 1 : p->solves.size();
+    for (size_t i = 0; i < nsol; i++)
         LGF_CHECK_ARG(src[i] && dst[i], "lgf_conv_execute: NULL buffer for solve %zu", i);
     cudaStream_t s = (cudaStream_t)stream;
-    if (!p->use_graph || p->prof.on) return run_poisson(p, src, dst, s);
+    if (!p->use_graph || p->prof.on) return run_fp32(p, src, dst, s, false);
     // graph path: one captured launch sequence per distinct set of buffers
     std::vector<const void *> key;
-    for (size_t i = 0; i < p->solves.size(); i++) {
+    for (size_t i = 0; i < nsol; i++) {
         key.push_back(src[i]);
         key.push_back(dst[i]);
     }
@@ -816,7 +980,7 @@ lgf_status lgf_conv_execute(lgf_plan *p, const float *const *src, float *const *
             set_error("stream capture failed to start");
             st = LGF_ERR_CUDA;
         } else {
-            st = run_poisson(p, src, dst, cs, true);
+            st = run_fp32(p, src, dst, cs, true);
             cudaError_t e = cudaStreamEndCapture(cs, &gr);
             if (st == LGF_OK && e != cudaSuccess) {
                 set_error("stream capture failed: %s", cudaGetErrorString(e));
@@ -845,7 +1009,19 @@ lgf_status lgf_conv_execute_host(lgf_plan *p, const float *const *src, float *co
         set_error("lgf_conv_execute_host: plan is not a Poisson plan");
         return LGF_ERR_STATE;
     }
+    if (p->sub) return lgf_conv_execute_host(p->sub, src, dst, stream);
     cudaStream_t s = (cudaStream_t)stream;
+    if (p->split) {
+        SplitPlan *sp = p->split;
+        LGF_CHECK_ARG(src[0] && dst[0], "lgf_conv_execute_host: NULL buffer");
+        const size_t B3 = 16 * 16 * 16;
+        const size_t ns = (size_t)sp->nsrc * sp->ncomp * B3, nd = (size_t)sp->ndst * sp->ncomp * B3;
+        LGF_CUDA_TRY(cudaMemcpyAsync(sp->d_stage_src, src[0], ns * sizeof(float), cudaMemcpyHostToDevice, s));
+        LGF_TRY(run_split(p, sp->d_stage_src, sp->d_stage_dst, s, &p->prof));
+        LGF_CUDA_TRY(cudaMemcpyAsync(dst[0], sp->d_stage_dst, nd * sizeof(float), cudaMemcpyDeviceToHost, s));
+        LGF_CUDA_TRY(cudaStreamSynchronize(s));
+        return LGF_OK;
+    }
     std::vector<const float *> ds(p->solves.size());
     std::vector<float *> dd(p->solves.size());
     for (size_t i = 0; i < p->solves.size(); i++) {
@@ -893,6 +1069,7 @@ lgf_status lgf_residual_fp64(lgf_plan *p, int solve, const float *src, const flo
 {
     clear_error();
     LGF_CHECK_ARG(p && src && dst && rel_residual, "lgf_residual_fp64: NULL argument");
+    if (p->sub) return lgf_residual_fp64(p->sub, solve, src, dst, rel_residual, stream);
     if (p->kind != LGF_KERNEL_LAPLACE7) {
         set_error("lgf_residual_fp64: not a Poisson plan");
         return LGF_ERR_STATE;
@@ -912,6 +1089,7 @@ lgf_status lgf_plan_set_profiling(lgf_plan *p, int enable)
 {
     clear_error();
     LGF_CHECK_ARG(p != nullptr && enable >= 0 && enable <= 2, "lgf_plan_set_profiling: bad argument");
+    if (p->sub) return lgf_plan_set_profiling(p->sub, enable);
     if (enable == 2) p->prof.clear();
     p->prof.on = enable != 0;
     if (p->rk) {  // an RK plan also times the kernels of its Poisson and IF sub-plans
@@ -946,6 +1124,7 @@ lgf_status lgf_plan_kernel_count(lgf_plan *p, int *count)
 {
     clear_error();
     LGF_CHECK_ARG(p && count, "lgf_plan_kernel_count: NULL argument");
+    if (p->sub) return lgf_plan_kernel_count(p->sub, count);
     LGF_TRY(merge_sub_profiles(p));
     *count = (int)p->prof.recs.size();
     return LGF_OK;
@@ -955,6 +1134,7 @@ lgf_status lgf_plan_kernel_times(lgf_plan *p, int i, const char **name, long lon
 {
     clear_error();
     LGF_CHECK_ARG(p != nullptr, "lgf_plan_kernel_times: NULL plan");
+    if (p->sub) return lgf_plan_kernel_times(p->sub, i, name, launches, total_ms);
     LGF_TRY(merge_sub_profiles(p));
     LGF_CHECK_ARG(i >= 0 && i < (int)p->prof.recs.size(), "lgf_plan_kernel_times: index %d out of range", i);
     if (name) *name = p->prof.recs[i].name.c_str();

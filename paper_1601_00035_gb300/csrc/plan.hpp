@@ -89,6 +89,8 @@ lgf_status build_spectrum(const double *d_octant, int K, const int N[3], float *
 
 // tables (table.cu)
 lgf_status build_lgf_octant(int K, double *d_out, cudaStream_t s);
+// -int_{t0}^{t1} of the Bessel form at offsets stride * (a, b, c) (t0 = 0: from 0; t1 = 0: to infinity)
+lgf_status build_lgf_octant_part(int K, int stride, double t0, double t1, double *d_out, cudaStream_t s);
 lgf_status build_if_taps(double alpha, double tol, double *d_taps, int max_r, int *R_out, cudaStream_t s);
 
 // integrating factor (ifactor.cu): block lists of the three passes
@@ -180,6 +182,39 @@ struct RkPlan {
 void free_rk(RkPlan *r);
 constexpr int LGF_PLAN_RK = 2;
 
+// block-sparse split solve (split.cu): G = G_near + G_far, near field by block-pair
+// spectra, far field on the coarse lattice through Lagrange interpolation
+struct SplitPlan {
+    double alpha = 0, dx = 0, scale = 0;
+    int ncomp = 0, nsrc = 0, ndst = 0;
+    int noff = 0;
+    std::vector<int> offs;       // [noff][3] kept near offsets d (target - source)
+    int64_t npairs = 0;
+    float2 *d_W = nullptr;       // window spectra [chunk][noff][32]
+    float2 *d_S = nullptr;       // source spectra [nc][chunk][nsrc][32]
+    float2 *d_U = nullptr;       // target spectra [nc][chunk][ndst][32]
+    int *d_off = nullptr;        // [ndst + 1]
+    int2 *d_pairs = nullptr;     // (offset index, source block)
+    // far field
+    int ncsrc = 0, ncdst = 0;
+    struct lgf_table *far_table = nullptr;  // G_far at even offsets (coarse octant)
+    lgf_plan *coarse = nullptr;             // whole-box plan on the coarse blocks
+    float *d_Q = nullptr;        // per source block anterpolated windows [nsrc][nc][16^3]
+    float *d_q = nullptr;        // coarse charges [ncsrc][nc][16^3]
+    float *d_v = nullptr;        // coarse potential [ncdst][nc][16^3]
+    int *d_ccoords = nullptr;    // coarse source block coordinates
+    int *d_flut = nullptr;       // fine source block lookup
+    int *d_tcoords = nullptr;    // fine target block coordinates
+    int *d_clut = nullptr;       // coarse target block lookup
+    int3 fmin, fext, cmin, cext;
+    float *d_stage_src = nullptr, *d_stage_dst = nullptr;  // lgf_conv_execute_host staging
+    cudaStream_t far_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_far = nullptr;
+};
+void free_split(SplitPlan *sp);
+lgf_status plan_split(lgf_plan *p, const lgf_solve_desc &d, double alpha, cudaStream_t s);
+lgf_status run_split(lgf_plan *p, const float *src, float *dst, cudaStream_t s, Profiler *prof);
+
 // residual (residual.cu)
 lgf_status residual_launch(const PoissonSolve &ps, const float *src, const float *dst, double *d_acc,
                            cudaStream_t s);
@@ -233,5 +268,9 @@ struct lgf_plan {
     std::vector<const void *> graph_key;
     lgf::Profiler prof;
     lgf::RkPlan *rk = nullptr;  // kind == LGF_PLAN_RK
+    int method = 0;                 // 0 whole-box FFT, 1 block-sparse split
+    lgf::SplitPlan *split = nullptr;
+    lgf_plan *sub = nullptr;        // autotuned plan: the executing plan it chose
+    double auto_ms[2] = {-1.0, -1.0};  // autotune times: whole box, split (-1: not timed)
     size_t bytes = 0;
 };

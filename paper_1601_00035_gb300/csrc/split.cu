@@ -1,0 +1,844 @@
+// Block-sparse Poisson solve: the LGF split into a compact near part and a smooth
+// far part, the near part convolved block pair by block pair and the far part on a
+// coarse lattice through Lagrange interpolation (the near-field / far-field
+// structure of the LGF-FMM the paper uses, Sec. 2.2 "evaluated to tolerance eps").
+//
+// Split.  In the Bessel form of App. B, G(n) = -int_0^inf prod_i i_{n_i}(t) dt with
+// i_n(t) = e^{-2t} I_n(2t).  With a split time a:
+//     G_near(n) = -int_0^a  prod_i i_{n_i}(t) dt,   G_far(n) = -int_a^inf prod_i i_{n_i}(t) dt,
+// G = G_near + G_far exactly.  G_far = e^{a L} G (the semigroup of Sec. 2.3), so it is
+// smooth on the scale sqrt(2a); G_near decays like the heat kernel at time a.
+//
+// Near field.  Blocks of 16^3 cells.  For a target block t and a source block
+// s = t - d, the pair's offsets n - m = 16 d + j, |j_i| <= 15, fit a circular
+// convolution of length 32: the source block zero-padded to 32^3 (R2C, kept
+// spectrum 32 x 32 x 17) times the spectrum of the window w_d(j) = G_near(16 d + j)
+// (computed once per plan in FP64).  Per target, the spectra of all kept offsets d
+// in [-2, 2]^3 are summed (spectral multiply-accumulate), then one C2R returns the
+// 16^3 result.  Spectra are stored frequency-major in chunks of 32 frequencies,
+// [chunk][block][32], so that the multiply-accumulate reads 256-byte rows.
+//
+// Far field.  Coarse lattice nodes c at fine positions 2c.  Interpolation phi_c(n):
+// an even fine index takes its node; an odd index n = 2j + 1 takes the 10-point
+// Lagrange midpoint rule on nodes j-4 .. j+5.  Then
+//     u_far(n) ~ sum_c phi_c(n) v(c),  v(c) = sum_c' G_far(2 (c - c')) q(c'),
+//     q(c') = sum_m phi_c'(m) f(m)            (anterpolation, the transpose),
+// i.e. G_far(x - y) is replaced by its tensor-product interpolant in x and y.  The
+// coarse convolution v = G_far(2 .) * q runs as a whole-box zero-padded FFT
+// convolution (the exact embedding of the library's plain plans) on coarse blocks of
+// 16^3 nodes.  Per fine block of 16 cells the 1-D interpolation touches the 17 nodes
+// 8b - 4 .. 8b + 12 (its window), so interpolation and anterpolation are 16 x 17
+// matrices applied along x, y and z.
+//
+// u = scale dx^2 (u_near + u_far).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <unordered_map>
+#include <vector>
+
+#include "fft.cuh"
+#include "plan.hpp"
+
+namespace lgf {
+namespace {
+
+constexpr int BN = 16;                 // near-field block edge
+constexpr int NF = 32;                 // near-field FFT length
+constexpr int KXN = NF / 2 + 1;        // kept x frequencies
+constexpr int NFREQ = NF * NF * KXN;   // 17408
+constexpr int CH = 32;                 // frequencies per chunk
+constexpr int NCHUNK = NFREQ / CH;     // 544
+constexpr int RNEAR = 2;               // near offsets d in [-RNEAR, RNEAR]^3
+constexpr int KNEAR = RNEAR * BN + BN - 1;  // largest |offset| a near window samples (47)
+constexpr int PINT = 10;               // interpolation points per axis (Lagrange order PINT - 1)
+constexpr int WOFF = PINT / 2 - 1;     // a block's window starts at node 8 b - WOFF
+constexpr int W = BN / 2 - 1 + PINT;   // nodes per window and axis (17)
+constexpr int W3 = W * W * W;
+
+__host__ __device__ inline int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+__device__ __forceinline__ int64_t oct_index(int a, int b, int c)
+{
+    int t;
+    if (a < b) { t = a; a = b; b = t; }
+    if (b < c) { t = b; b = c; c = t; }
+    if (a < b) { t = a; a = b; b = t; }
+    return (int64_t)a * (a + 1) * (a + 2) / 6 + (int64_t)b * (b + 1) / 2 + c;
+}
+
+// ---------------------------------------------------------------------------
+// Plan-time kernels (FP64): windows of G_near and their DFTs.
+// ---------------------------------------------------------------------------
+// win[d][z][y][x] = G_near(16 d + j) at circular index (x, y, z) = j mod 32, |j_i| <= 15;
+// index 16 (j = +-16) stays zero.
+__global__ void k_near_windows(const double *__restrict__ oct, const int *__restrict__ offs, int noff,
+                               double *__restrict__ win)
+{
+    const int64_t total = (int64_t)noff * NF * NF * NF;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % NF), y = (int)((i / NF) % NF), z = (int)((i / (NF * NF)) % NF);
+        const int d = (int)(i / (NF * NF * NF));
+        double v = 0.0;
+        if (x != NF / 2 && y != NF / 2 && z != NF / 2) {
+            const int jx = x < NF / 2 ? x : x - NF, jy = y < NF / 2 ? y : y - NF, jz = z < NF / 2 ? z : z - NF;
+            const int nx = abs(BN * offs[3 * d] + jx), ny = abs(BN * offs[3 * d + 1] + jy),
+                      nz = abs(BN * offs[3 * d + 2] + jz);
+            v = oct[oct_index(nx, ny, nz)];
+        }
+        win[i] = v;
+    }
+}
+
+// DFT along x of real windows: out[d][z][y][kx] (kx < 17), complex FP64
+__global__ void k_near_dft_x(const double *__restrict__ win, int noff, double2 *__restrict__ out,
+                             const double2 *__restrict__ tw)
+{
+    const int64_t total = (int64_t)noff * NF * NF * KXN;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int kx = (int)(i % KXN);
+        const int64_t row = i / KXN;
+        const double *r = win + row * NF;
+        double re = 0.0, im = 0.0;
+        for (int x = 0; x < NF; x++) {
+            const double2 w = tw[(kx * x) % NF];
+            re = fma(r[x], w.x, re);
+            im = fma(r[x], w.y, im);
+        }
+        out[i] = make_double2(re, im);
+    }
+}
+
+// complex DFT along y (axis 1) or z (axis 2) of [d][z][y][kx] arrays
+__global__ void k_near_dft_yz(const double2 *__restrict__ in, int noff, int axis, double2 *__restrict__ out,
+                              const double2 *__restrict__ tw)
+{
+    const int64_t total = (int64_t)noff * NF * NF * KXN;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int kx = (int)(i % KXN), y = (int)((i / KXN) % NF), z = (int)((i / (KXN * NF)) % NF);
+        const int64_t d = i / ((int64_t)KXN * NF * NF);
+        const int k = axis == 1 ? y : z;
+        const int64_t stride = axis == 1 ? KXN : (int64_t)KXN * NF;
+        const int64_t base = d * NF * NF * KXN + (axis == 1 ? (int64_t)z * NF * KXN + kx : (int64_t)y * KXN + kx);
+        double re = 0.0, im = 0.0;
+        for (int m = 0; m < NF; m++) {
+            const double2 w = tw[(k * m) % NF];
+            const double2 v = in[base + m * stride];
+            re += v.x * w.x - v.y * w.y;
+            im += v.x * w.y + v.y * w.x;
+        }
+        out[i] = make_double2(re, im);
+    }
+}
+
+// [d][kz][ky][kx] FP64 -> chunked FP32 [chunk][d][32], frequency f = (kz * 32 + ky) * 17 + kx
+__global__ void k_near_pack(const double2 *__restrict__ in, int noff, float2 *__restrict__ out)
+{
+    const int64_t total = (int64_t)noff * NFREQ;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int f = (int)(i % NFREQ);
+        const int d = (int)(i / NFREQ);
+        const double2 v = in[i];
+        out[((int64_t)(f / CH) * noff + d) * CH + (f % CH)] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Near field, per execution.
+// ---------------------------------------------------------------------------
+constexpr int SM_S1 = BN * BN * KXN;       // [z < 16][y < 16][kx]
+constexpr int SM_S2 = BN * NF * KXN;       // [z < 16][ky < 32][kx]
+constexpr size_t NEAR_SMEM = (size_t)(SM_S1 + SM_S2) * sizeof(float2);
+
+// Forward: one thread block per (source block, component).  R2C of the 16^3 block
+// zero-padded to 32^3: x (two real rows per complex line), y, z; the spectrum is
+// written chunked: S[((c * NCHUNK + chunk) * nsrc + b) * 32 + j].
+__global__ void __launch_bounds__(256) k_near_fwd(const float *__restrict__ src, int ncomp, int c0, int nsrc,
+                                                   float2 *__restrict__ S)
+{
+    extern __shared__ float2 sm[];
+    float2 *S1 = sm;
+    float2 *S2 = sm + SM_S1;
+    const int b = blockIdx.x, c = blockIdx.y;
+    const int t = threadIdx.x;
+    const float *f = src + ((size_t)b * ncomp + c0 + c) * (BN * BN * BN);
+    pdl_wait();
+    if (t < 128) {
+        cx<float> a[NF];
+        const float4 *r0 = reinterpret_cast<const float4 *>(f + (2 * t) * BN);
+        const float4 *r1 = reinterpret_cast<const float4 *>(f + (2 * t + 1) * BN);
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const float4 u = r0[i], v = r1[i];
+            a[4 * i + 0] = {u.x, v.x};
+            a[4 * i + 1] = {u.y, v.y};
+            a[4 * i + 2] = {u.z, v.z};
+            a[4 * i + 3] = {u.w, v.w};
+        }
+#pragma unroll
+        for (int i = BN; i < NF; i++) a[i] = {0.f, 0.f};
+        fft::dft_reg<NF, false, float, 0, true>(a);
+        // rows 2t (real part) and 2t + 1 (imaginary part) from Z = X0 + i X1
+#pragma unroll
+        for (int k = 0; k < KXN; k++) {
+            const cx<float> zk = a[k], zm = a[(NF - k) & (NF - 1)];
+            S1[(2 * t) * KXN + k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+            S1[(2 * t + 1) * KXN + k] = make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
+        }
+    }
+    __syncthreads();
+    for (int l = t; l < BN * KXN; l += 256) {  // y lines (z, kx)
+        const int z = l / KXN, kx = l % KXN;
+        cx<float> a[NF];
+#pragma unroll
+        for (int y = 0; y < BN; y++) {
+            const float2 v = S1[(z * BN + y) * KXN + kx];
+            a[y] = {v.x, v.y};
+        }
+#pragma unroll
+        for (int y = BN; y < NF; y++) a[y] = {0.f, 0.f};
+        fft::dft_reg<NF, false, float, 0, true>(a);
+#pragma unroll
+        for (int ky = 0; ky < NF; ky++) S2[(z * NF + ky) * KXN + kx] = make_float2(a[ky].x, a[ky].y);
+    }
+    __syncthreads();
+    pdl_trigger();
+    float2 *out = S + (size_t)c * NCHUNK * nsrc * CH;
+    for (int l = t; l < NF * KXN; l += 256) {  // z lines (ky, kx), l = ky * 17 + kx
+        cx<float> a[NF];
+#pragma unroll
+        for (int z = 0; z < BN; z++) {
+            const float2 v = S2[z * NF * KXN + l];
+            a[z] = {v.x, v.y};
+        }
+#pragma unroll
+        for (int z = BN; z < NF; z++) a[z] = {0.f, 0.f};
+        fft::dft_reg<NF, false, float, 0, true>(a);
+#pragma unroll
+        for (int kz = 0; kz < NF; kz++) {
+            const int fq = kz * (NF * KXN) + l;
+            out[((size_t)(fq / CH) * nsrc + b) * CH + (fq % CH)] = make_float2(a[kz].x, a[kz].y);
+        }
+    }
+}
+
+// Spectral multiply-accumulate: U_t(k) = sum_d W_d(k) S_{t-d}(k) over the kept offsets
+// present for target t.  One thread block per (chunk, group of 64 targets, component);
+// a warp per target, lane = frequency in the chunk.  pairs[off[t] .. off[t+1]) lists
+// (d, s) for target t.
+__global__ void __launch_bounds__(256) k_near_mac(const float2 *__restrict__ W, int noff, const float2 *__restrict__ S,
+                                                   int nsrc, const int *__restrict__ off, const int2 *__restrict__ pairs,
+                                                   int ndst, float2 *__restrict__ U)
+{
+    extern __shared__ float2 Kc[];  // [noff][32]
+    const int chunk = blockIdx.x, c = blockIdx.z;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < noff * CH; i += 256) Kc[i] = W[(size_t)chunk * noff * CH + i];
+    __syncthreads();
+    pdl_wait();
+    const float2 *Sc = S + ((size_t)c * NCHUNK + chunk) * nsrc * CH;
+    float2 *Uc = U + ((size_t)c * NCHUNK + chunk) * ndst * CH;
+    for (int i = 0; i < 8; i++) {
+        const int t = blockIdx.y * 64 + warp * 8 + i;
+        if (t >= ndst) break;
+        const int beg = off[t], end = off[t + 1];
+        float ar = 0.f, ai = 0.f;
+        for (int base = beg; base < end; base += 32) {
+            const int2 my = base + lane < end ? pairs[base + lane] : make_int2(0, 0);
+            const int n = min(32, end - base);
+            for (int k = 0; k < n; k++) {
+                const int d = __shfl_sync(0xffffffffu, my.x, k);
+                const int s = __shfl_sync(0xffffffffu, my.y, k);
+                const float2 sv = Sc[(size_t)s * CH + lane];
+                const float2 kv = Kc[d * CH + lane];
+                ar = fmaf(kv.x, sv.x, ar);
+                ar = fmaf(-kv.y, sv.y, ar);
+                ai = fmaf(kv.x, sv.y, ai);
+                ai = fmaf(kv.y, sv.x, ai);
+            }
+        }
+        Uc[(size_t)t * CH + lane] = make_float2(ar, ai);
+    }
+    pdl_trigger();
+}
+
+// Inverse: one thread block per (target block, component): z, y (keeping the first
+// 16 outputs of each), then C2R in x with two rows per complex line; writes
+// dst = mul * result (the target window of the circular convolution).
+__global__ void __launch_bounds__(256) k_near_inv(const float2 *__restrict__ U, int ndst, float *__restrict__ dst,
+                                                   int ncomp, int c0, float mul)
+{
+    extern __shared__ float2 sm[];
+    float2 *S1 = sm;          // [z][y][kx]
+    float2 *S2 = sm + SM_S1;  // [z][ky][kx]
+    const int b = blockIdx.x, c = blockIdx.y;
+    const int t = threadIdx.x;
+    const float2 *in = U + (size_t)c * NCHUNK * ndst * CH;
+    pdl_wait();
+    for (int l = t; l < NF * KXN; l += 256) {  // z lines (ky, kx)
+        cx<float> a[NF];
+#pragma unroll
+        for (int kz = 0; kz < NF; kz++) {
+            const int fq = kz * (NF * KXN) + l;
+            const float2 v = in[((size_t)(fq / CH) * ndst + b) * CH + (fq % CH)];
+            a[kz] = {v.x, v.y};
+        }
+        fft::dft_reg<NF, true, float, 0, false>(a);
+#pragma unroll
+        for (int z = 0; z < BN; z++) S2[z * NF * KXN + l] = make_float2(a[z].x, a[z].y);
+    }
+    __syncthreads();
+    for (int l = t; l < BN * KXN; l += 256) {  // y lines (z, kx)
+        const int z = l / KXN, kx = l % KXN;
+        cx<float> a[NF];
+#pragma unroll
+        for (int ky = 0; ky < NF; ky++) {
+            const float2 v = S2[(z * NF + ky) * KXN + kx];
+            a[ky] = {v.x, v.y};
+        }
+        fft::dft_reg<NF, true, float, 0, false>(a);
+#pragma unroll
+        for (int y = 0; y < BN; y++) S1[(z * BN + y) * KXN + kx] = make_float2(a[y].x, a[y].y);
+    }
+    __syncthreads();
+    pdl_trigger();
+    if (t < 128) {  // x: rows 2t, 2t + 1 as Z = X0 + i X1 with the Hermitian halves filled in
+        cx<float> a[NF];
+#pragma unroll
+        for (int k = 0; k < KXN; k++) {
+            const float2 p = S1[(2 * t) * KXN + k], q = S1[(2 * t + 1) * KXN + k];
+            a[k] = {p.x - q.y, p.y + q.x};
+        }
+#pragma unroll
+        for (int k = KXN; k < NF; k++) {
+            const float2 p = S1[(2 * t) * KXN + (NF - k)], q = S1[(2 * t + 1) * KXN + (NF - k)];
+            a[k] = {p.x + q.y, q.x - p.y};  // conj(p) + i conj(q)
+        }
+        fft::dft_reg<NF, true, float, 0, false>(a);
+        float *o = dst + ((size_t)b * ncomp + c0 + c) * (BN * BN * BN);
+        float4 *w0 = reinterpret_cast<float4 *>(o + (2 * t) * BN);
+        float4 *w1 = reinterpret_cast<float4 *>(o + (2 * t + 1) * BN);
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            w0[i] = make_float4(mul * a[4 * i].x, mul * a[4 * i + 1].x, mul * a[4 * i + 2].x, mul * a[4 * i + 3].x);
+            w1[i] = make_float4(mul * a[4 * i].y, mul * a[4 * i + 1].y, mul * a[4 * i + 2].y, mul * a[4 * i + 3].y);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Far field: anterpolation, coarse charge gather, interpolation (SIMT).
+// The 1-D matrix P[i][l] (fine i < 16 of a block, node l < 17 of its window
+// 8b - 4 + l) is in constant memory.
+// ---------------------------------------------------------------------------
+__constant__ float c_P[BN * W];
+
+// Q_b[lz][ly][lx] = sum_i P[iz][lz] P[iy][ly] P[ix][lx] f_b[iz][iy][ix] (a W^3 window), per
+// (source block, component)
+__global__ void __launch_bounds__(256) k_far_anterp(const float *__restrict__ src, int ncomp, int c0,
+                                                     float *__restrict__ Q, int ncq)
+{
+    __shared__ float A[W3];
+    __shared__ float T[W3];
+    const int b = blockIdx.x, c = blockIdx.y, t = threadIdx.x;
+    const float *f = src + ((size_t)b * ncomp + c0 + c) * (BN * BN * BN);
+    pdl_wait();
+    for (int i = t; i < BN * BN * BN; i += 256) A[i] = f[i];
+    __syncthreads();
+    // x: T[z][y][lx] = sum_x P[x][lx] A[z][y][x]      (16 x 16 x W)
+    for (int i = t; i < BN * BN * W; i += 256) {
+        const int lx = i % W, row = i / W;
+        float acc = 0.f;
+#pragma unroll
+        for (int x = 0; x < BN; x++) acc = fmaf(c_P[x * W + lx], A[row * BN + x], acc);
+        T[i] = acc;
+    }
+    __syncthreads();
+    // y: A[z][ly][lx] = sum_y P[y][ly] T[z][y][lx]    (16 x W x W)
+    for (int i = t; i < BN * W * W; i += 256) {
+        const int lx = i % W, ly = (i / W) % W, z = i / (W * W);
+        float acc = 0.f;
+#pragma unroll
+        for (int y = 0; y < BN; y++) acc = fmaf(c_P[y * W + ly], T[(z * BN + y) * W + lx], acc);
+        A[i] = acc;
+    }
+    __syncthreads();
+    // z: Q[lz][ly][lx] = sum_z P[z][lz] A[z][ly][lx]  (W^3)
+    float *out = Q + ((size_t)b * ncq + c) * W3;
+    for (int i = t; i < W3; i += 256) {
+        const int r = i % (W * W), lz = i / (W * W);
+        float acc = 0.f;
+#pragma unroll
+        for (int z = 0; z < BN; z++) acc = fmaf(c_P[z * W + lz], A[z * W * W + r], acc);
+        out[i] = acc;
+    }
+    pdl_trigger();
+}
+
+// Coarse charges q on coarse block C: node n = 16 C + l receives Q_b[n - (8 b - 4)] from
+// each source block b whose window holds n (up to three per axis, fixed order).
+// flut: dense lookup of the fine source blocks over [fmin, fmin + fext).
+__global__ void __launch_bounds__(256) k_far_gather(const float *__restrict__ Q, int ncq,
+                                                     const int *__restrict__ ccoords, const int *__restrict__ flut,
+                                                     int3 fmin, int3 fext, float *__restrict__ q)
+{
+    const int C = blockIdx.x, c = blockIdx.y;
+    const int Cx = ccoords[3 * C], Cy = ccoords[3 * C + 1], Cz = ccoords[3 * C + 2];
+    float *out = q + ((size_t)C * ncq + c) * (BN * BN * BN);
+    pdl_wait();
+    for (int i = threadIdx.x; i < BN * BN * BN; i += 256) {
+        const int nx = 16 * Cx + i % BN, ny = 16 * Cy + (i / BN) % BN, nz = 16 * Cz + i / (BN * BN);
+        const int bx1 = floordiv(nx + WOFF, 8), by1 = floordiv(ny + WOFF, 8), bz1 = floordiv(nz + WOFF, 8);
+        float acc = 0.f;
+        for (int dz = -2; dz <= 0; dz++) {
+            const int bz = bz1 + dz, lz = nz - (8 * bz - WOFF);
+            if (lz >= W || bz - fmin.z < 0 || bz - fmin.z >= fext.z) continue;
+            for (int dy = -2; dy <= 0; dy++) {
+                const int by = by1 + dy, ly = ny - (8 * by - WOFF);
+                if (ly >= W || by - fmin.y < 0 || by - fmin.y >= fext.y) continue;
+                for (int dx = -2; dx <= 0; dx++) {
+                    const int bx = bx1 + dx, lx = nx - (8 * bx - WOFF);
+                    if (lx >= W || bx - fmin.x < 0 || bx - fmin.x >= fext.x) continue;
+                    const int s = flut[((size_t)(bz - fmin.z) * fext.y + (by - fmin.y)) * fext.x + (bx - fmin.x)];
+                    if (s < 0) continue;
+                    acc += Q[((size_t)s * ncq + c) * W3 + (lz * W + ly) * W + lx];
+                }
+            }
+        }
+        out[i] = acc;
+    }
+    pdl_trigger();
+}
+
+// dst_b += mul * sum_l P[iz][lz] P[iy][ly] P[ix][lx] v(8 b - 4 + l), per (target block, component);
+// v on coarse blocks through clut (dense lookup over [cmin, cmin + cext)), ncv components.
+__global__ void __launch_bounds__(256) k_far_interp(const float *__restrict__ v, int ncv, const int *__restrict__ tcoords,
+                                                     const int *__restrict__ clut, int3 cmin, int3 cext,
+                                                     float *__restrict__ dst, int ncomp, int c0, float mul)
+{
+    __shared__ float A[W3];
+    __shared__ float T[W3];
+    const int b = blockIdx.x, c = blockIdx.y, t = threadIdx.x;
+    const int bx = tcoords[3 * b], by = tcoords[3 * b + 1], bz = tcoords[3 * b + 2];
+    pdl_wait();
+    for (int i = t; i < W3; i += 256) {
+        const int nx = 8 * bx - WOFF + i % W, ny = 8 * by - WOFF + (i / W) % W, nz = 8 * bz - WOFF + i / (W * W);
+        const int Cx = floordiv(nx, 16) - cmin.x, Cy = floordiv(ny, 16) - cmin.y, Cz = floordiv(nz, 16) - cmin.z;
+        float val = 0.f;
+        if (Cx >= 0 && Cy >= 0 && Cz >= 0 && Cx < cext.x && Cy < cext.y && Cz < cext.z) {
+            const int C = clut[((size_t)Cz * cext.y + Cy) * cext.x + Cx];
+            if (C >= 0) {
+                const int lx = nx - 16 * (Cx + cmin.x), ly = ny - 16 * (Cy + cmin.y), lz = nz - 16 * (Cz + cmin.z);
+                val = v[((size_t)C * ncv + c) * (BN * BN * BN) + (lz * BN + ly) * BN + lx];
+            }
+        }
+        A[i] = val;
+    }
+    __syncthreads();
+    // x: T[lz][ly][ix] = sum_lx P[ix][lx] A[lz][ly][lx]   (W x W x 16)
+    for (int i = t; i < W * W * BN; i += 256) {
+        const int ix = i % BN, row = i / BN;
+        float acc = 0.f;
+#pragma unroll
+        for (int l = 0; l < W; l++) acc = fmaf(c_P[ix * W + l], A[row * W + l], acc);
+        T[i] = acc;
+    }
+    __syncthreads();
+    for (int i = t; i < W * BN * BN; i += 256) {  // y: A[lz][iy][ix]   (W x 16 x 16)
+        const int ix = i % BN, iy = (i / BN) % BN, lz = i / (BN * BN);
+        float acc = 0.f;
+#pragma unroll
+        for (int l = 0; l < W; l++) acc = fmaf(c_P[iy * W + l], T[(lz * W + l) * BN + ix], acc);
+        A[i] = acc;
+    }
+    __syncthreads();
+    float *o = dst + ((size_t)b * ncomp + c0 + c) * (BN * BN * BN);
+    for (int i = t; i < BN * BN * BN; i += 256) {  // z, added to the near field
+        const int r = i % (BN * BN), iz = i / (BN * BN);
+        float acc = 0.f;
+#pragma unroll
+        for (int l = 0; l < W; l++) acc = fmaf(c_P[iz * W + l], A[l * BN * BN + r], acc);
+        o[i] += mul * acc;
+    }
+    pdl_trigger();
+}
+
+// ---------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------
+template <typename T>
+lgf_status dalloc_n(T **p, size_t n, size_t &bytes)
+{
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc(p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        set_error("device allocation of %zu bytes failed: %s", n * sizeof(T), cudaGetErrorString(e));
+        return LGF_ERR_OOM;
+    }
+    bytes += n * sizeof(T);
+    return LGF_OK;
+}
+template <typename T>
+lgf_status upload_v(T *d, const std::vector<T> &h, cudaStream_t s)
+{
+    if (h.empty()) return LGF_OK;
+    LGF_CUDA_TRY(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return LGF_OK;
+}
+
+inline int64_t key3(int x, int y, int z)
+{
+    const int64_t off = 1 << 20, m = (1 << 21) - 1;
+    return (((int64_t)x + off) & m) << 42 | (((int64_t)y + off) & m) << 21 | (((int64_t)z + off) & m);
+}
+
+// PINT-point Lagrange weights at the midpoint of nodes PINT/2 - 1 and PINT/2 of 0 .. PINT-1
+void midpoint_weights(double w[PINT])
+{
+    for (int k = 0; k < PINT; k++) {
+        double v = 1.0;
+        for (int m = 0; m < PINT; m++)
+            if (m != k) v *= (0.5 * (PINT - 1) - m) / (double)(k - m);
+        w[k] = v;
+    }
+}
+
+// the 1-D interpolation matrix P[i][l]: fine i of a block, node l of its window 8b - WOFF + l.
+// Even i: its own node i/2; odd i = 2j + 1: nodes j - (PINT/2 - 1) .. j + PINT/2.
+void interp_matrix(float P[BN * W])
+{
+    double w[PINT];
+    midpoint_weights(w);
+    for (int i = 0; i < BN * W; i++) P[i] = 0.f;
+    for (int i = 0; i < BN; i++) {
+        if (i % 2 == 0) {
+            P[i * W + i / 2 + WOFF] = 1.f;
+        } else {
+            const int j = i / 2;
+            for (int k = 0; k < PINT; k++) P[i * W + j - (PINT / 2 - 1) + k + WOFF] = (float)w[k];
+        }
+    }
+}
+
+}  // namespace
+
+void free_split(SplitPlan *sp)
+{
+    if (!sp) return;
+    cudaFree(sp->d_W);
+    cudaFree(sp->d_S);
+    cudaFree(sp->d_U);
+    cudaFree(sp->d_off);
+    cudaFree(sp->d_pairs);
+    cudaFree(sp->d_Q);
+    cudaFree(sp->d_q);
+    cudaFree(sp->d_v);
+    cudaFree(sp->d_ccoords);
+    cudaFree(sp->d_flut);
+    cudaFree(sp->d_tcoords);
+    cudaFree(sp->d_clut);
+    cudaFree(sp->d_stage_src);
+    cudaFree(sp->d_stage_dst);
+    if (sp->coarse) lgf_plan_destroy(sp->coarse);
+    if (sp->far_table) lgf_table_destroy(sp->far_table);
+    if (sp->far_stream) cudaStreamDestroy(sp->far_stream);
+    if (sp->ev_fork) cudaEventDestroy(sp->ev_fork);
+    if (sp->ev_far) cudaEventDestroy(sp->ev_far);
+    delete sp;
+}
+
+lgf_status plan_split(lgf_plan *p, const lgf_solve_desc &d, double alpha, cudaStream_t s)
+{
+    LGF_CHECK_ARG(d.B == BN, "block-sparse method: B=%d (the near-field blocks are 16^3)", d.B);
+    LGF_CHECK_ARG(alpha >= 1.0 && alpha <= 64.0, "block-sparse method: split time %g outside [1, 64]", alpha);
+    SplitPlan *sp = new (std::nothrow) SplitPlan();
+    if (!sp) {
+        set_error("host allocation failed");
+        return LGF_ERR_OOM;
+    }
+    p->split = sp;
+    sp->alpha = alpha;
+    sp->ncomp = d.ncomp;
+    sp->nsrc = d.n_src;
+    sp->ndst = d.n_dst;
+    sp->dx = d.dx;
+    sp->scale = d.scale;
+    size_t &bytes = p->bytes;
+    LGF_CUDA_TRY(fft::upload_tw64());
+
+    // --- near field: G_near table, kept offsets, window spectra ---
+    double *d_near = nullptr;
+    const int64_t noct = (int64_t)(KNEAR + 1) * (KNEAR + 2) * (KNEAR + 3) / 6;
+    LGF_TRY(dalloc_n(&d_near, (size_t)noct, bytes));
+    lgf_status st = build_lgf_octant_part(KNEAR, 1, 0.0, alpha, d_near, s);
+    std::vector<double> h_near(noct);
+    if (st == LGF_OK && cudaMemcpy(h_near.data(), d_near, noct * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+        st = LGF_ERR_CUDA;
+    if (st != LGF_OK) {
+        cudaFree(d_near);
+        bytes -= noct * sizeof(double);
+        return st == LGF_ERR_CUDA ? (set_error("near table download failed"), st) : st;
+    }
+    // keep an offset when its window holds a value above 1e-12 |G(0)| (|G(0)| ~ 0.2527)
+    auto oct_h = [&](int a, int b, int c) {
+        a = std::abs(a), b = std::abs(b), c = std::abs(c);
+        if (a < b) std::swap(a, b);
+        if (b < c) std::swap(b, c);
+        if (a < b) std::swap(a, b);
+        return h_near[(int64_t)a * (a + 1) * (a + 2) / 6 + (int64_t)b * (b + 1) / 2 + c];
+    };
+    std::vector<int> offs;
+    for (int dz = -RNEAR; dz <= RNEAR; dz++)
+        for (int dy = -RNEAR; dy <= RNEAR; dy++)
+            for (int dxo = -RNEAR; dxo <= RNEAR; dxo++) {
+                // the window's largest |G_near| sits at its point nearest the origin
+                auto nearest = [](int o) { return o == 0 ? 0 : (o > 0 ? BN * o - (BN - 1) : BN * o + (BN - 1)); };
+                const double g = std::fabs(oct_h(nearest(dxo), nearest(dy), nearest(dz)));
+                if (g >= 1e-12 * 0.2527) {
+                    offs.push_back(dxo);
+                    offs.push_back(dy);
+                    offs.push_back(dz);
+                }
+            }
+    sp->noff = (int)offs.size() / 3;
+    sp->offs = offs;
+    {
+        int *d_offs = nullptr;
+        double *d_win = nullptr;
+        double2 *d_a = nullptr, *d_b = nullptr, *d_tw = nullptr;
+        size_t tmp = 0;
+        const size_t nwin = (size_t)sp->noff * NF * NF * NF, nspec = (size_t)sp->noff * NF * NF * KXN;
+        st = dalloc_n(&d_offs, offs.size(), tmp);
+        if (st == LGF_OK) st = dalloc_n(&d_win, nwin, tmp);
+        if (st == LGF_OK) st = dalloc_n(&d_a, nspec, tmp);
+        if (st == LGF_OK) st = dalloc_n(&d_b, nspec, tmp);
+        if (st == LGF_OK) st = dalloc_n(&d_tw, (size_t)NF, tmp);
+        if (st == LGF_OK) st = dalloc_n(&sp->d_W, (size_t)sp->noff * NFREQ, bytes);
+        std::vector<double2> tw(NF);
+        for (int j = 0; j < NF; j++) tw[j] = make_double2(std::cos(-2.0 * M_PI * j / NF), std::sin(-2.0 * M_PI * j / NF));
+        if (st == LGF_OK) st = upload_v(d_offs, offs, s);
+        if (st == LGF_OK) st = upload_v(d_tw, tw, s);
+        if (st == LGF_OK) {
+            k_near_windows<<<1024, 256, 0, s>>>(d_near, d_offs, sp->noff, d_win);
+            k_near_dft_x<<<1024, 256, 0, s>>>(d_win, sp->noff, d_a, d_tw);
+            k_near_dft_yz<<<1024, 256, 0, s>>>(d_a, sp->noff, 1, d_b, d_tw);
+            k_near_dft_yz<<<1024, 256, 0, s>>>(d_b, sp->noff, 2, d_a, d_tw);
+            k_near_pack<<<1024, 256, 0, s>>>(d_a, sp->noff, sp->d_W);
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) {
+                set_error("near-field spectra: %s", cudaGetErrorString(e));
+                st = LGF_ERR_CUDA;
+            }
+        }
+        cudaFree(d_offs);
+        cudaFree(d_win);
+        cudaFree(d_a);
+        cudaFree(d_b);
+        cudaFree(d_tw);
+    }
+    cudaFree(d_near);
+    bytes -= noct * sizeof(double);
+    if (st != LGF_OK) return st;
+
+    // target -> (offset, source) pairs
+    std::unordered_map<int64_t, int> smap;
+    for (int i = 0; i < d.n_src; i++) smap[key3(d.src_blocks[3 * i], d.src_blocks[3 * i + 1], d.src_blocks[3 * i + 2])] = i;
+    std::vector<int> off(d.n_dst + 1, 0);
+    std::vector<int2> pairs;
+    for (int t = 0; t < d.n_dst; t++) {
+        off[t] = (int)pairs.size();
+        for (int k = 0; k < sp->noff; k++) {
+            auto it = smap.find(key3(d.dst_blocks[3 * t] - offs[3 * k], d.dst_blocks[3 * t + 1] - offs[3 * k + 1],
+                                     d.dst_blocks[3 * t + 2] - offs[3 * k + 2]));
+            if (it != smap.end()) pairs.push_back(make_int2(k, it->second));
+        }
+    }
+    off[d.n_dst] = (int)pairs.size();
+    sp->npairs = (int64_t)pairs.size();
+    LGF_TRY(dalloc_n(&sp->d_off, off.size(), bytes));
+    LGF_TRY(dalloc_n(&sp->d_pairs, pairs.size(), bytes));
+    LGF_TRY(upload_v(sp->d_off, off, s));
+    LGF_TRY(upload_v(sp->d_pairs, pairs, s));
+    LGF_TRY(dalloc_n(&sp->d_S, (size_t)d.ncomp * NFREQ * d.n_src, bytes));
+    LGF_TRY(dalloc_n(&sp->d_U, (size_t)d.ncomp * NFREQ * d.n_dst, bytes));
+
+    // --- far field: coarse block sets, G_far table, coarse plan ---
+    float P[BN * W];
+    interp_matrix(P);
+    LGF_CUDA_TRY(cudaMemcpyToSymbol(c_P, P, sizeof(P)));
+    auto coarse_of = [&](const int32_t *bl, int n) {
+        std::map<int64_t, int> m;  // ordered: deterministic coarse block order
+        std::vector<int> out;
+        for (int i = 0; i < n; i++) {
+            int lo[3], hi[3];
+            for (int a = 0; a < 3; a++) {  // the block's window: nodes 8 b - WOFF .. 8 b - WOFF + W - 1
+                lo[a] = floordiv(8 * bl[3 * i + a] - WOFF, 16);
+                hi[a] = floordiv(8 * bl[3 * i + a] - WOFF + W - 1, 16);
+            }
+            for (int z = lo[2]; z <= hi[2]; z++)
+                for (int y = lo[1]; y <= hi[1]; y++)
+                    for (int x = lo[0]; x <= hi[0]; x++) m.emplace(key3(z, y, x), 0);
+        }
+        for (auto &kv : m) {
+            const int64_t k = kv.first, off20 = 1 << 20, msk = (1 << 21) - 1;
+            const int z = (int)(((k >> 42) & msk) - off20), y = (int)(((k >> 21) & msk) - off20), x = (int)((k & msk) - off20);
+            out.push_back(x);
+            out.push_back(y);
+            out.push_back(z);
+        }
+        return out;
+    };
+    std::vector<int> csrc = coarse_of(d.src_blocks, d.n_src), cdst = coarse_of(d.dst_blocks, d.n_dst);
+    sp->ncsrc = (int)csrc.size() / 3;
+    sp->ncdst = (int)cdst.size() / 3;
+    // the coarse plan's table must cover half its FFT length: same size rule as lgf_conv_plan
+    int Kc = 1;
+    for (int a = 0; a < 3; a++) {
+        int smin = 1 << 30, smax = -(1 << 30), tmin = 1 << 30, tmax = -(1 << 30);
+        for (int i = 0; i < sp->ncsrc; i++) smin = std::min(smin, csrc[3 * i + a]), smax = std::max(smax, csrc[3 * i + a]);
+        for (int i = 0; i < sp->ncdst; i++) tmin = std::min(tmin, cdst[3 * i + a]), tmax = std::max(tmax, cdst[3 * i + a]);
+        const long S0 = 16L * smin, S1 = 16L * (smax + 1) - 1, T0 = 16L * tmin, T1 = 16L * (tmax + 1) - 1;
+        const long m = std::max(std::labs(T0 - S1), std::labs(T1 - S0));
+        const int n = poisson_pick_n((int)std::min<long>(std::max(2 * m + 2, 2 * (S1 - S0 + 1)), 1 << 20));
+        LGF_CHECK_ARG(n > 0, "block-sparse method: the coarse far-field box needs an FFT longer than 1024 on axis %d", a);
+        Kc = std::max(Kc, n / 2 - 1);
+    }
+    lgf_table *ft = new (std::nothrow) lgf_table();
+    if (!ft) {
+        set_error("host allocation failed");
+        return LGF_ERR_OOM;
+    }
+    sp->far_table = ft;
+    ft->kind = LGF_KERNEL_LAPLACE7;
+    ft->alpha = 0.0;
+    ft->K = Kc;
+    ft->R = 0;
+    ft->device = p->device;
+    ft->n = (int64_t)(Kc + 1) * (Kc + 2) * (Kc + 3) / 6;
+    ft->d_vals = nullptr;
+    ft->d_taps32 = nullptr;
+    if (cudaMalloc(&ft->d_vals, ft->n * sizeof(double)) != cudaSuccess) {
+        set_error("far table allocation failed");
+        return LGF_ERR_OOM;
+    }
+    LGF_TRY(build_lgf_octant_part(Kc, 2, alpha, 0.0, ft->d_vals, s));
+    lgf_solve_desc cd;
+    std::memset(&cd, 0, sizeof(cd));
+    cd.B = BN;
+    cd.ncomp = d.ncomp;
+    cd.n_src = sp->ncsrc;
+    cd.n_dst = sp->ncdst;
+    cd.src_blocks = csrc.data();
+    cd.dst_blocks = cdst.data();
+    cd.dx = 1.0;
+    cd.scale = 1.0;
+    lgf_plan_opts co;
+    std::memset(&co, 0, sizeof(co));
+    LGF_TRY(lgf_conv_plan(ft, &cd, 1, &co, (void *)s, &sp->coarse));
+    bytes += sp->coarse->bytes;
+    // lookups: fine source blocks (dense over their box + 1), coarse target blocks
+    int fmin[3], fmax[3], cmin[3], cmax[3];
+    for (int a = 0; a < 3; a++) {
+        fmin[a] = 1 << 30, fmax[a] = -(1 << 30), cmin[a] = 1 << 30, cmax[a] = -(1 << 30);
+        for (int i = 0; i < d.n_src; i++) fmin[a] = std::min(fmin[a], d.src_blocks[3 * i + a]),
+                                           fmax[a] = std::max(fmax[a], d.src_blocks[3 * i + a]);
+        for (int i = 0; i < sp->ncdst; i++) cmin[a] = std::min(cmin[a], cdst[3 * i + a]), cmax[a] = std::max(cmax[a], cdst[3 * i + a]);
+    }
+    sp->fmin = make_int3(fmin[0], fmin[1], fmin[2]);
+    sp->fext = make_int3(fmax[0] - fmin[0] + 1, fmax[1] - fmin[1] + 1, fmax[2] - fmin[2] + 1);
+    sp->cmin = make_int3(cmin[0], cmin[1], cmin[2]);
+    sp->cext = make_int3(cmax[0] - cmin[0] + 1, cmax[1] - cmin[1] + 1, cmax[2] - cmin[2] + 1);
+    std::vector<int> flut((size_t)sp->fext.x * sp->fext.y * sp->fext.z, -1);
+    for (int i = 0; i < d.n_src; i++)
+        flut[((size_t)(d.src_blocks[3 * i + 2] - fmin[2]) * sp->fext.y + (d.src_blocks[3 * i + 1] - fmin[1])) * sp->fext.x +
+             (d.src_blocks[3 * i] - fmin[0])] = i;
+    std::vector<int> clut((size_t)sp->cext.x * sp->cext.y * sp->cext.z, -1);
+    for (int i = 0; i < sp->ncdst; i++)
+        clut[((size_t)(cdst[3 * i + 2] - cmin[2]) * sp->cext.y + (cdst[3 * i + 1] - cmin[1])) * sp->cext.x +
+             (cdst[3 * i] - cmin[0])] = i;
+    std::vector<int> tco(d.dst_blocks, d.dst_blocks + 3 * d.n_dst);
+    LGF_TRY(dalloc_n(&sp->d_flut, flut.size(), bytes));
+    LGF_TRY(dalloc_n(&sp->d_clut, clut.size(), bytes));
+    LGF_TRY(dalloc_n(&sp->d_ccoords, csrc.size(), bytes));
+    LGF_TRY(dalloc_n(&sp->d_tcoords, tco.size(), bytes));
+    LGF_TRY(upload_v(sp->d_flut, flut, s));
+    LGF_TRY(upload_v(sp->d_clut, clut, s));
+    LGF_TRY(upload_v(sp->d_ccoords, csrc, s));
+    LGF_TRY(upload_v(sp->d_tcoords, tco, s));
+    const size_t B3 = (size_t)BN * BN * BN;
+    LGF_TRY(dalloc_n(&sp->d_Q, (size_t)d.n_src * d.ncomp * W3, bytes));
+    LGF_TRY(dalloc_n(&sp->d_q, (size_t)sp->ncsrc * d.ncomp * B3, bytes));
+    LGF_TRY(dalloc_n(&sp->d_v, (size_t)sp->ncdst * d.ncomp * B3, bytes));
+    LGF_CUDA_TRY(cudaStreamCreateWithFlags(&sp->far_stream, cudaStreamNonBlocking));
+    LGF_CUDA_TRY(cudaEventCreateWithFlags(&sp->ev_fork, cudaEventDisableTiming));
+    LGF_CUDA_TRY(cudaEventCreateWithFlags(&sp->ev_far, cudaEventDisableTiming));
+    static bool attr_done[64] = {false};
+    if (p->device >= 0 && p->device < 64 && !attr_done[p->device]) {
+        LGF_CUDA_TRY(cudaFuncSetAttribute(k_near_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NEAR_SMEM));
+        LGF_CUDA_TRY(cudaFuncSetAttribute(k_near_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NEAR_SMEM));
+        attr_done[p->device] = true;
+    }
+    LGF_CUDA_TRY(cudaStreamSynchronize(s));
+    return LGF_OK;
+}
+
+// One split solve: near field on stream s, far field (anterpolation, coarse charges,
+// coarse convolution) on the plan's far stream, joined before the interpolation
+// adds the far field to the near result.  prof: per-kernel event timing (then all
+// launches go to s, one after another).
+lgf_status run_split(lgf_plan *p, const float *src, float *dst, cudaStream_t s, Profiler *prof)
+{
+    SplitPlan *sp = p->split;
+    const bool P = prof && prof->on;
+    const int nc = sp->ncomp;
+    const float mul_near = (float)(sp->scale * sp->dx * sp->dx / ((double)NF * NF * NF));
+    const float mul_far = (float)(sp->scale * sp->dx * sp->dx);
+    cudaStream_t fs = P ? s : sp->far_stream;
+    if (!P) {
+        LGF_CUDA_TRY(cudaEventRecord(sp->ev_fork, s));
+        LGF_CUDA_TRY(cudaStreamWaitEvent(fs, sp->ev_fork, 0));
+    }
+    // far field
+    if (P) prof->begin(fs);
+    k_far_anterp<<<dim3(sp->nsrc, nc), 256, 0, fs>>>(src, nc, 0, sp->d_Q, nc);
+    LGF_LAUNCH_CHECK("k_far_anterp");
+    if (P) prof->end("far_anterp", fs);
+    if (P) prof->begin(fs);
+    k_far_gather<<<dim3(sp->ncsrc, nc), 256, 0, fs>>>(sp->d_Q, nc, sp->d_ccoords, sp->d_flut, sp->fmin, sp->fext,
+                                                      sp->d_q);
+    LGF_LAUNCH_CHECK("k_far_gather");
+    if (P) prof->end("far_gather", fs);
+    {
+        const float *cs[1] = {sp->d_q};
+        float *cd[1] = {sp->d_v};
+        if (P) prof->begin(fs);
+        LGF_TRY(lgf_conv_execute(sp->coarse, cs, cd, (void *)fs));
+        if (P) prof->end("far_coarse_conv", fs);
+    }
+    if (!P) LGF_CUDA_TRY(cudaEventRecord(sp->ev_far, fs));
+    // near field
+    if (P) prof->begin(s);
+    LGF_CUDA_TRY(launch_pdl_smem(k_near_fwd, dim3(sp->nsrc, nc), dim3(256), NEAR_SMEM, s, src, nc, 0, sp->nsrc, sp->d_S));
+    if (P) prof->end("near_fwd", s);
+    if (P) prof->begin(s);
+    LGF_CUDA_TRY(launch_pdl_smem(k_near_mac, dim3(NCHUNK, (sp->ndst + 63) / 64, nc), dim3(256),
+                                 (size_t)sp->noff * CH * sizeof(float2), s, (const float2 *)sp->d_W, sp->noff,
+                                 (const float2 *)sp->d_S, sp->nsrc, (const int *)sp->d_off, (const int2 *)sp->d_pairs,
+                                 sp->ndst, sp->d_U));
+    if (P) prof->end("near_mac", s);
+    if (P) prof->begin(s);
+    LGF_CUDA_TRY(launch_pdl_smem(k_near_inv, dim3(sp->ndst, nc), dim3(256), NEAR_SMEM, s, (const float2 *)sp->d_U,
+                                 sp->ndst, dst, nc, 0, mul_near));
+    if (P) prof->end("near_inv", s);
+    if (!P) LGF_CUDA_TRY(cudaStreamWaitEvent(s, sp->ev_far, 0));
+    if (P) prof->begin(s);
+    k_far_interp<<<dim3(sp->ndst, nc), 256, 0, s>>>(sp->d_v, nc, sp->d_tcoords, sp->d_clut, sp->cmin, sp->cext, dst, nc,
+                                                    0, mul_far);
+    LGF_LAUNCH_CHECK("k_far_interp");
+    if (P) prof->end("far_interp", s);
+    return LGF_OK;
+}
+
+}  // namespace lgf

@@ -121,9 +121,11 @@ __global__ void k_nodes(const double *__restrict__ tq, int nq, int K, double *__
     scaled_bessel(2.0 * tq[q], K, bes + (size_t)q * (K + 1), 1);
 }
 
-// one block per leading index a; threads over the (b, c) pairs with a >= b >= c
-__global__ void k_octant(const double *__restrict__ bes, const double *__restrict__ wq, int nq, int K,
-                         double *__restrict__ out, double T_hi)
+// one block per leading index a; threads over the (b, c) pairs with a >= b >= c.
+// Entry (a, b, c) samples the lattice offset stride * (a, b, c): bes rows hold
+// i_n(t_q) for n = 0 .. nrow - 1.  tail: add the closed-form integral beyond T_hi.
+__global__ void k_octant(const double *__restrict__ bes, const double *__restrict__ wq, int nq, int nrow, int stride,
+                         double *__restrict__ out, double T_hi, int tail)
 {
     const int a = blockIdx.x;
     const int npairs = (a + 1) * (a + 2) / 2;
@@ -133,16 +135,20 @@ __global__ void k_octant(const double *__restrict__ bes, const double *__restric
         while ((b + 1) * (b + 2) / 2 <= p) b++;
         while (b * (b + 1) / 2 > p) b--;
         const int c = p - b * (b + 1) / 2;
-        const int K1 = K + 1;
+        const int na = stride * a, nb = stride * b, nc = stride * c;
         double acc = 0.0;
         for (int q = 0; q < nq; q++) {
-            const double *row = bes + (size_t)q * K1;
-            acc = fma(wq[q] * row[a], row[b] * row[c], acc);
+            const double *row = bes + (size_t)q * nrow;
+            acc = fma(wq[q] * row[na], row[nb] * row[nc], acc);
         }
-        const double c1 = ((4.0 * a * (double)a - 1.0) + (4.0 * b * (double)b - 1.0) + (4.0 * c * (double)c - 1.0)) / 16.0;
-        const double tail = c4 * (2.0 / sqrt(T_hi) - (2.0 / 3.0) * c1 / (T_hi * sqrt(T_hi)));
+        double tl = 0.0;
+        if (tail) {
+            const double c1 = ((4.0 * na * (double)na - 1.0) + (4.0 * nb * (double)nb - 1.0) +
+                               (4.0 * nc * (double)nc - 1.0)) / 16.0;
+            tl = c4 * (2.0 / sqrt(T_hi) - (2.0 / 3.0) * c1 / (T_hi * sqrt(T_hi)));
+        }
         const int64_t idx = (int64_t)a * (a + 1) * (a + 2) / 6 + (int64_t)b * (b + 1) / 2 + c;
-        out[idx] = -(acc + tail);
+        out[idx] = -(acc + tl);
     }
 }
 
@@ -162,9 +168,19 @@ __global__ void k_if_taps(double alpha, int maxr, double tol, double *__restrict
 
 lgf_status build_lgf_octant(int K, double *d_out, cudaStream_t s)
 {
+    return build_lgf_octant_part(K, 1, 0.0, 0.0, d_out, s);
+}
+
+// Part of the t-integral of the Bessel form: -int_{t0}^{t1} prod_i i_{n_i}(t) dt, with
+// t0 = 0 read as T_LO (the integrand is < T_LO below it) and t1 = 0 read as infinity
+// (Gauss-Legendre up to T_HI plus the closed-form tail), at the offsets stride * (a, b, c)
+// of the sorted octant K >= a >= b >= c >= 0.
+lgf_status build_lgf_octant_part(int K, int stride, double t0, double t1, double *d_out, cudaStream_t s)
+{
     std::vector<double> xg, wg;
     gauss_legendre_rule(NGL, xg, wg);
-    const double s0 = std::log(T_LO), s1 = std::log(T_HI);
+    const bool tail = !(t1 > 0.0);
+    const double s0 = std::log(t0 > T_LO ? t0 : T_LO), s1 = std::log(tail ? T_HI : t1);
     const int npan = (int)std::ceil((s1 - s0) / PANEL);
     const double h = (s1 - s0) / npan;
     const int nq = npan * NGL;
@@ -178,8 +194,9 @@ lgf_status build_lgf_octant(int K, double *d_out, cudaStream_t s)
         }
     double *d_t = nullptr, *d_w = nullptr, *d_bes = nullptr;
     lgf_status st = LGF_OK;
+    const int nrow = stride * K + 1;
     if (cudaMalloc(&d_t, nq * sizeof(double)) != cudaSuccess || cudaMalloc(&d_w, nq * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&d_bes, (size_t)nq * (K + 1) * sizeof(double)) != cudaSuccess) {
+        cudaMalloc(&d_bes, (size_t)nq * nrow * sizeof(double)) != cudaSuccess) {
         set_error("table workspace allocation failed");
         st = LGF_ERR_OOM;
     }
@@ -189,8 +206,8 @@ lgf_status build_lgf_octant(int K, double *d_out, cudaStream_t s)
         st = LGF_ERR_CUDA;
     }
     if (st == LGF_OK) {
-        k_nodes<<<(nq + 63) / 64, 64, 0, s>>>(d_t, nq, K, d_bes);
-        k_octant<<<K + 1, 256, 0, s>>>(d_bes, d_w, nq, K, d_out, T_HI);
+        k_nodes<<<(nq + 63) / 64, 64, 0, s>>>(d_t, nq, nrow - 1, d_bes);
+        k_octant<<<K + 1, 256, 0, s>>>(d_bes, d_w, nq, nrow, stride, d_out, T_HI, tail ? 1 : 0);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {

@@ -63,7 +63,11 @@ class _RkDesc(ctypes.Structure):
 
 
 class _PlanOpts(ctypes.Structure):
-    _fields_ = [("use_graph", ctypes.c_int), ("precision", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+    _fields_ = [("use_graph", ctypes.c_int), ("precision", ctypes.c_int), ("method", ctypes.c_int),
+                ("far_precision", ctypes.c_int), ("split_alpha", ctypes.c_double), ("reserved", ctypes.c_int * 2)]
+
+
+METHOD_WHOLE_BOX, METHOD_SPLIT, METHOD_AUTOTUNE = 0, 1, 2
 
 
 _lib = None
@@ -80,6 +84,8 @@ _SIGS = {
     "lgf_conv_plan": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_SolveDesc), ctypes.c_int,
                                      ctypes.POINTER(_PlanOpts), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "lgf_plan_workspace_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "lgf_plan_method": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]),
     "lgf_conv_execute": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
                                         ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
     "lgf_conv_execute_f64": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
@@ -207,7 +213,7 @@ class Plan:
     """lgf_conv_plan over one or more solves."""
 
     def __init__(self, table: Table, solves: Sequence[Solve], use_graph: bool = False, stream=None,
-                 precision: int = 0):
+                 precision: int = 0, method: int = 0, split_alpha: float = 0.0, far_precision: int = 0):
         L = load()
         self.table = table  # keep alive
         self.solves = list(solves)
@@ -224,9 +230,18 @@ class Plan:
         opts = _PlanOpts()
         opts.use_graph = 1 if use_graph else 0
         opts.precision = int(precision)
+        opts.method = int(method)
+        opts.split_alpha = float(split_alpha)
+        opts.far_precision = int(far_precision)
         h = ctypes.c_void_p()
         _check(L.lgf_conv_plan(table._h, descs, len(self.solves), ctypes.byref(opts), _stream(stream), ctypes.byref(h)))
         self._h = h
+
+    def method(self):
+        """(executed method, autotune ms of the whole-box plan, autotune ms of the split plan)."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        m = load().lgf_plan_method(self._h, ctypes.byref(a), ctypes.byref(b))
+        return m, a.value, b.value
 
     def workspace_bytes(self) -> int:
         b = ctypes.c_size_t()
