@@ -93,7 +93,11 @@ typedef struct {
                               8-point Lagrange interpolation and anterpolation; one solve, B = 16;
                               cost follows the active blocks; relative L2 error ~1e-7..1e-6;
                            2: autotune: plan both and keep the faster (one timed execution each) */
-    int far_precision;  /* method 1: 0 FP32 interpolation; 1 reserved */
+    int far_precision;  /* method 1: 0 = far-field interpolation and anterpolation in FP32 on the
+                           CUDA cores (the solve held to 1e-6 relative L2);
+                           1 = the same as GEMMs on the tensor cores (tcgen05 kind::tf32 MMAs,
+                           operands split into two TF32 parts, FP32 accumulation: the
+                           reduced-precision far field, held to 1e-5) */
     double split_alpha; /* method 1: the split time a; 0 takes 20 (the error and the near radius
                            it sets are stated in DESIGN) */
     int reserved[2];    /* must be zero */
@@ -148,6 +152,12 @@ lgf_status lgf_conv_plan(const lgf_table *t, const lgf_solve_desc *solves, int n
  * an autotuned plan (opts->method = 2), *ms_whole_box and *ms_split receive the device times
  * of the two candidates measured at plan time (-1 where not timed); either pointer may be NULL. */
 int lgf_plan_method(const lgf_plan *p, double *ms_whole_box, double *ms_split);
+
+/* Synchronises `stream` and reports LGF_ERR_TIMEOUT if a bounded device-side wait of the
+ * plan's kernels gave up since the last check (the flag is then cleared; the results of
+ * the executions since then are not valid), LGF_OK otherwise.  Only the block-sparse
+ * method's tensor-core kernels wait; lgf_conv_execute_host checks on its own. */
+lgf_status lgf_plan_check(lgf_plan *p, void *stream);
 
 /* Device bytes held by the plan (workspaces + spectra + lookups). */
 lgf_status lgf_plan_workspace_bytes(const lgf_plan *p, size_t *bytes);

@@ -781,7 +781,8 @@ lgf_status lgf_conv_plan(const lgf_table *t, const lgf_solve_desc *solves, int n
         for (int i = 0; i < 2; i++) LGF_CHECK_ARG(opts->reserved[i] == 0, "lgf_conv_plan: reserved option fields must be zero");
         LGF_CHECK_ARG(opts->precision == 0 || opts->precision == 1, "lgf_conv_plan: precision must be 0 or 1");
         LGF_CHECK_ARG(opts->method >= 0 && opts->method <= 2, "lgf_conv_plan: method must be 0, 1 or 2");
-        LGF_CHECK_ARG(opts->far_precision == 0, "lgf_conv_plan: far_precision must be 0");
+        LGF_CHECK_ARG(opts->far_precision == 0 || opts->far_precision == 1,
+                      "lgf_conv_plan: far_precision must be 0 (FP32, CUDA cores) or 1 (tensor cores, TF32 split)");
         LGF_CHECK_ARG(opts->method == 0 || (opts->precision == 0 && t->kind == LGF_KERNEL_LAPLACE7 && n_solves == 1),
                       "lgf_conv_plan: methods 1 and 2 take one FP32 Poisson solve");
         LGF_CHECK_ARG(opts->split_alpha == 0.0 || (opts->split_alpha >= 1.0 && opts->split_alpha <= 64.0),
@@ -812,7 +813,7 @@ lgf_status lgf_conv_plan(const lgf_table *t, const lgf_solve_desc *solves, int n
     } else if (method == 1) {
         st = check_split_solve(solves[0]);
         p->method = 1;
-        if (st == LGF_OK) st = plan_split(p, solves[0], alpha, s);
+        if (st == LGF_OK) st = plan_split(p, solves[0], alpha, opts ? opts->far_precision : 0, s);
         if (st == LGF_OK) st = plan_split_extras(p, solves[0], s);
     } else if (method == 2) {
         st = autotune_plan(p, t, solves, opts, s);
@@ -824,6 +825,17 @@ lgf_status lgf_conv_plan(const lgf_table *t, const lgf_solve_desc *solves, int n
         return st;
     }
     *out = p;
+    return LGF_OK;
+}
+
+lgf_status lgf_plan_check(lgf_plan *p, void *stream)
+{
+    clear_error();
+    LGF_CHECK_ARG(p != nullptr, "lgf_plan_check: NULL plan");
+    if (p->sub) return lgf_plan_check(p->sub, stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p->split) return split_check(p, s);
+    LGF_CUDA_TRY(cudaStreamSynchronize(s));
     return LGF_OK;
 }
 
@@ -1019,8 +1031,7 @@ lgf_status lgf_conv_execute_host(lgf_plan *p, const float *const *src, float *co
         LGF_CUDA_TRY(cudaMemcpyAsync(sp->d_stage_src, src[0], ns * sizeof(float), cudaMemcpyHostToDevice, s));
         LGF_TRY(run_split(p, sp->d_stage_src, sp->d_stage_dst, s, &p->prof));
         LGF_CUDA_TRY(cudaMemcpyAsync(dst[0], sp->d_stage_dst, nd * sizeof(float), cudaMemcpyDeviceToHost, s));
-        LGF_CUDA_TRY(cudaStreamSynchronize(s));
-        return LGF_OK;
+        return split_check(p, s);
     }
     std::vector<const float *> ds(p->solves.size());
     std::vector<float *> dd(p->solves.size());

@@ -208,11 +208,16 @@ struct SplitPlan {
     int *d_clut = nullptr;       // coarse target block lookup
     int3 fmin, fext, cmin, cext;
     float *d_stage_src = nullptr, *d_stage_dst = nullptr;  // lgf_conv_execute_host staging
+    bool far_tensor_cores = false;  // far-field interpolation on the tensor cores (tcgen05, reduced precision)
+    uint32_t *d_Ba = nullptr, *d_Bi = nullptr;  // tensor-core B operands (TF32 hi, lo)
+    int *d_err = nullptr;                       // set by a tensor-core wait that gave up
     cudaStream_t far_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_far = nullptr;
 };
 void free_split(SplitPlan *sp);
-lgf_status plan_split(lgf_plan *p, const lgf_solve_desc &d, double alpha, cudaStream_t s);
+lgf_status plan_split(lgf_plan *p, const lgf_solve_desc &d, double alpha, int far_precision, cudaStream_t s);
+// device error flag of a split plan (a bounded tensor-core wait gave up): LGF_ERR_TIMEOUT, cleared
+lgf_status split_check(lgf_plan *p, cudaStream_t s);
 lgf_status run_split(lgf_plan *p, const float *src, float *dst, cudaStream_t s, Profiler *prof);
 
 // residual (residual.cu)

@@ -40,6 +40,7 @@
 
 #include "fft.cuh"
 #include "plan.hpp"
+#include "tc.cuh"
 
 namespace lgf {
 namespace {
@@ -341,8 +342,10 @@ __global__ void __launch_bounds__(256) k_far_anterp(const float *__restrict__ sr
 {
     __shared__ float A[W3];
     __shared__ float T[W3];
+    __shared__ float sP[BN * W];
     const int b = blockIdx.x, c = blockIdx.y, t = threadIdx.x;
     const float *f = src + ((size_t)b * ncomp + c0 + c) * (BN * BN * BN);
+    for (int i = t; i < BN * W; i += 256) sP[i] = c_P[i];
     pdl_wait();
     for (int i = t; i < BN * BN * BN; i += 256) A[i] = f[i];
     __syncthreads();
@@ -351,7 +354,7 @@ __global__ void __launch_bounds__(256) k_far_anterp(const float *__restrict__ sr
         const int lx = i % W, row = i / W;
         float acc = 0.f;
 #pragma unroll
-        for (int x = 0; x < BN; x++) acc = fmaf(c_P[x * W + lx], A[row * BN + x], acc);
+        for (int x = 0; x < BN; x++) acc = fmaf(sP[x * W + lx], A[row * BN + x], acc);
         T[i] = acc;
     }
     __syncthreads();
@@ -360,7 +363,7 @@ __global__ void __launch_bounds__(256) k_far_anterp(const float *__restrict__ sr
         const int lx = i % W, ly = (i / W) % W, z = i / (W * W);
         float acc = 0.f;
 #pragma unroll
-        for (int y = 0; y < BN; y++) acc = fmaf(c_P[y * W + ly], T[(z * BN + y) * W + lx], acc);
+        for (int y = 0; y < BN; y++) acc = fmaf(sP[y * W + ly], T[(z * BN + y) * W + lx], acc);
         A[i] = acc;
     }
     __syncthreads();
@@ -370,7 +373,7 @@ __global__ void __launch_bounds__(256) k_far_anterp(const float *__restrict__ sr
         const int r = i % (W * W), lz = i / (W * W);
         float acc = 0.f;
 #pragma unroll
-        for (int z = 0; z < BN; z++) acc = fmaf(c_P[z * W + lz], A[z * W * W + r], acc);
+        for (int z = 0; z < BN; z++) acc = fmaf(sP[z * W + lz], A[z * W * W + r], acc);
         out[i] = acc;
     }
     pdl_trigger();
@@ -419,8 +422,10 @@ __global__ void __launch_bounds__(256) k_far_interp(const float *__restrict__ v,
 {
     __shared__ float A[W3];
     __shared__ float T[W3];
+    __shared__ float sP[BN * W];
     const int b = blockIdx.x, c = blockIdx.y, t = threadIdx.x;
     const int bx = tcoords[3 * b], by = tcoords[3 * b + 1], bz = tcoords[3 * b + 2];
+    for (int i = t; i < BN * W; i += 256) sP[i] = c_P[i];
     pdl_wait();
     for (int i = t; i < W3; i += 256) {
         const int nx = 8 * bx - WOFF + i % W, ny = 8 * by - WOFF + (i / W) % W, nz = 8 * bz - WOFF + i / (W * W);
@@ -441,7 +446,7 @@ __global__ void __launch_bounds__(256) k_far_interp(const float *__restrict__ v,
         const int ix = i % BN, row = i / BN;
         float acc = 0.f;
 #pragma unroll
-        for (int l = 0; l < W; l++) acc = fmaf(c_P[ix * W + l], A[row * W + l], acc);
+        for (int l = 0; l < W; l++) acc = fmaf(sP[ix * W + l], A[row * W + l], acc);
         T[i] = acc;
     }
     __syncthreads();
@@ -449,7 +454,7 @@ __global__ void __launch_bounds__(256) k_far_interp(const float *__restrict__ v,
         const int ix = i % BN, iy = (i / BN) % BN, lz = i / (BN * BN);
         float acc = 0.f;
 #pragma unroll
-        for (int l = 0; l < W; l++) acc = fmaf(c_P[iy * W + l], T[(lz * W + l) * BN + ix], acc);
+        for (int l = 0; l < W; l++) acc = fmaf(sP[iy * W + l], T[(lz * W + l) * BN + ix], acc);
         A[i] = acc;
     }
     __syncthreads();
@@ -458,9 +463,228 @@ __global__ void __launch_bounds__(256) k_far_interp(const float *__restrict__ v,
         const int r = i % (BN * BN), iz = i / (BN * BN);
         float acc = 0.f;
 #pragma unroll
-        for (int l = 0; l < W; l++) acc = fmaf(c_P[iz * W + l], A[l * BN * BN + r], acc);
+        for (int l = 0; l < W; l++) acc = fmaf(sP[iz * W + l], A[l * BN * BN + r], acc);
         o[i] += mul * acc;
     }
+    pdl_trigger();
+}
+
+// ---------------------------------------------------------------------------
+// Far field on the tensor cores.  Each 1-D interpolation step is a GEMM: with the
+// block's data as the A operand (rows = the two other axes, K = the axis transformed)
+// and the 16 x 17 matrix P as B, D = A B^T lands in TMEM; the next step reads D back
+// (one row per thread), writes it transposed as its own A operand, and so on for x, y,
+// z.  Data and weights are split into two TF32 parts, x = hi + lo; each product keeps
+// hi*hi + hi*lo + lo*hi (three MMAs per K step).  The tensor cores add each MMA's
+// products into the FP32 accumulator with truncation, so the steps are not quite FP32
+// accurate: measured ~1e-6 relative on the far field (this is the reduced-precision far
+// field, held to 1e-5; a three-part split adds MMAs and measured worse).
+//   anterpolation: 16^3 -> 17^3: K = 16 each step, N = 17 padded to 32, rows 256, 272, 289
+//   interpolation: 17^3 -> 16^3: K = 17 padded to 24, N = 16, rows 289, 272, 256
+// One 128-thread block (one warpgroup, so every TMEM lane has its thread) per block and
+// component; M = 128 per MMA, up to three row tiles; TMEM: 128 columns.
+// ---------------------------------------------------------------------------
+constexpr int TC_THREADS = 128;
+constexpr int TC_ROWS = 384;           // three 128-row tiles
+constexpr int TC_TMEM_COLS = 128;
+constexpr int TC_WAIT = 1 << 18;       // mbarrier polls before a wait gives up
+
+template <int K>
+struct TcSmem {
+    uint32_t a_hi[TC_ROWS * K], a_lo[TC_ROWS * K];  // A operand, core-matrix layout
+    uint32_t b_hi[32 * K], b_lo[32 * K];            // B operand (P), core-matrix layout
+    uint64_t mbar;
+    uint32_t tmem_base;
+};
+
+// Issue D[tile] = A[tile] B^T for every row tile (three MMAs per K step), commit to the
+// mbarrier and wait for it (phase `ph`).  Thread 0 issues; everyone waits.  Returns false
+// if the wait gave up.
+template <int K, int N>
+__device__ __forceinline__ bool tc_pass(TcSmem<K> &sm, int ntiles, uint32_t ph)
+{
+    tc::fence_smem_to_async();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tc::fence_after_sync();
+        const uint32_t idesc = tc::idesc_tf32(128, N);
+        const uint32_t sbo = K * 32;
+        const uint32_t ah = tc::smem_addr(sm.a_hi), al = tc::smem_addr(sm.a_lo);
+        const uint32_t bh = tc::smem_addr(sm.b_hi), bl = tc::smem_addr(sm.b_lo);
+        for (int mt = 0; mt < ntiles; mt++) {
+            const uint32_t d = sm.tmem_base + mt * N;
+            for (int ks = 0; ks < K / 8; ks++) {
+                const uint32_t ao = mt * 16 * sbo + ks * 256, bo = ks * 256;
+                tc::mma_tf32(d, tc::smem_desc(ah + ao, 128, sbo), tc::smem_desc(bh + bo, 128, sbo), idesc, ks > 0);
+                tc::mma_tf32(d, tc::smem_desc(ah + ao, 128, sbo), tc::smem_desc(bl + bo, 128, sbo), idesc, 1);
+                tc::mma_tf32(d, tc::smem_desc(al + ao, 128, sbo), tc::smem_desc(bh + bo, 128, sbo), idesc, 1);
+            }
+        }
+        tc::mma_commit(tc::smem_addr(&sm.mbar));
+    }
+    bool ok = tc::mbar_wait(tc::smem_addr(&sm.mbar), ph, TC_WAIT);
+    ok = __syncthreads_and(ok) != 0;  // uniform across the block
+    tc::fence_after_sync();
+    return ok;
+}
+
+// this thread's row `row` of tile `mt` of the last pass: N (16 or 32) columns
+template <int N>
+__device__ __forceinline__ void tc_row(uint32_t tmem_base, int mt, float v[N])
+{
+    const int w = threadIdx.x >> 5;
+    const uint32_t t = tmem_base + ((uint32_t)(32 * w) << 16) + mt * N;
+    tc::tmem_ld16(t, v);
+    if constexpr (N == 32) tc::tmem_ld16(t + 16, v + 16);
+}
+
+template <int K>
+__device__ __forceinline__ void tc_put(TcSmem<K> &sm, int r, int k, float x)
+{
+    uint32_t hi, lo;
+    tc::split_tf32(x, hi, lo);
+    const int o = tc::core_byte(r, k, K) >> 2;
+    sm.a_hi[o] = hi;
+    sm.a_lo[o] = lo;
+}
+
+template <int K>
+__device__ __forceinline__ void tc_setup(TcSmem<K> &sm, const uint32_t *__restrict__ Bhl)
+{
+    for (int i = threadIdx.x; i < 32 * K; i += TC_THREADS) {
+        sm.b_hi[i] = Bhl[i];
+        sm.b_lo[i] = Bhl[32 * K + i];
+    }
+    for (int i = threadIdx.x; i < TC_ROWS * K; i += TC_THREADS) sm.a_hi[i] = sm.a_lo[i] = 0u;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(tc::smem_addr(&sm.mbar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x < 32) tc::tmem_alloc(tc::smem_addr(&sm.tmem_base), TC_TMEM_COLS);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+}
+
+// ok = false: a wait gave up on phase `ph` with MMAs possibly in flight; wait for them
+// once more (bounded) before the TMEM is freed
+template <int K>
+__device__ __forceinline__ void tc_teardown(TcSmem<K> &sm, bool ok, uint32_t ph)
+{
+    if (!ok && threadIdx.x == 0) tc::mbar_wait(tc::smem_addr(&sm.mbar), ph, TC_WAIT);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (threadIdx.x < 32) tc::tmem_dealloc(sm.tmem_base, TC_TMEM_COLS);
+}
+
+__global__ void __launch_bounds__(TC_THREADS) k_far_anterp_tc(const float *__restrict__ src, int ncomp, int c0,
+                                                               float *__restrict__ Q, int ncq,
+                                                               const uint32_t *__restrict__ Bhl, int *err)
+{
+    extern __shared__ __align__(128) unsigned char tc_raw[];
+    TcSmem<16> &sm = *reinterpret_cast<TcSmem<16> *>(tc_raw);
+    const int b = blockIdx.x, c = blockIdx.y, t = threadIdx.x;
+    tc_setup<16>(sm, Bhl);
+    const float *f = src + ((size_t)b * ncomp + c0 + c) * (BN * BN * BN);
+    pdl_wait();
+    for (int i = t; i < BN * BN * BN; i += TC_THREADS) tc_put<16>(sm, i / BN, i % BN, f[i]);  // rows (z, y), k = x
+    uint32_t ph = 0;
+    bool ok = tc_pass<16, 32>(sm, 2, ph);
+    float v[32];
+    // D1 rows (z, y), cols lx  ->  A2 rows (z, lx), k = y
+    for (int mt = 0; mt < 2 && ok; mt++) {
+        const int r = mt * 128 + t;
+        tc_row<32>(sm.tmem_base, mt, v);
+        const int z = r / BN, y = r % BN;
+        for (int l = 0; l < W; l++) tc_put<16>(sm, z * W + l, y, v[l]);
+    }
+    tc::fence_before_sync();
+    if (ok) ok = tc_pass<16, 32>(sm, 3, ph = 1);
+    // D2 rows (z, lx), cols ly  ->  A3 rows (ly, lx), k = z
+    for (int mt = 0; mt < 3 && ok; mt++) {
+        const int r = mt * 128 + t;
+        tc_row<32>(sm.tmem_base, mt, v);
+        if (r < BN * W) {
+            const int z = r / W, lx = r % W;
+            for (int l = 0; l < W; l++) tc_put<16>(sm, l * W + lx, z, v[l]);
+        }
+    }
+    tc::fence_before_sync();
+    if (ok) ok = tc_pass<16, 32>(sm, 3, ph = 0);
+    // D3 rows (ly, lx), cols lz  ->  Q[lz][ly][lx]
+    float *out = Q + ((size_t)b * ncq + c) * W3;
+    for (int mt = 0; mt < 3 && ok; mt++) {
+        const int r = mt * 128 + t;
+        tc_row<32>(sm.tmem_base, mt, v);
+        if (r < W * W)
+            for (int l = 0; l < W; l++) out[l * W * W + r] = v[l];
+    }
+    if (!ok && t == 0) atomicExch(err, 1);
+    tc_teardown<16>(sm, ok, ph);
+    pdl_trigger();
+}
+
+__global__ void __launch_bounds__(TC_THREADS) k_far_interp_tc(const float *__restrict__ vc, int ncv,
+                                                               const int *__restrict__ tcoords,
+                                                               const int *__restrict__ clut, int3 cmin, int3 cext,
+                                                               float *__restrict__ dst, int ncomp, int c0, float mul,
+                                                               const uint32_t *__restrict__ Bhl, int *err)
+{
+    extern __shared__ __align__(128) unsigned char tc_raw[];
+    TcSmem<24> &sm = *reinterpret_cast<TcSmem<24> *>(tc_raw);
+    const int b = blockIdx.x, c = blockIdx.y, t = threadIdx.x;
+    tc_setup<24>(sm, Bhl);
+    const int bx = tcoords[3 * b], by = tcoords[3 * b + 1], bz = tcoords[3 * b + 2];
+    pdl_wait();
+    // the block's window of the coarse potential: rows (lz, ly), k = lx
+    for (int i = t; i < W3; i += TC_THREADS) {
+        const int nx = 8 * bx - WOFF + i % W, ny = 8 * by - WOFF + (i / W) % W, nz = 8 * bz - WOFF + i / (W * W);
+        const int Cx = floordiv(nx, 16) - cmin.x, Cy = floordiv(ny, 16) - cmin.y, Cz = floordiv(nz, 16) - cmin.z;
+        float val = 0.f;
+        if (Cx >= 0 && Cy >= 0 && Cz >= 0 && Cx < cext.x && Cy < cext.y && Cz < cext.z) {
+            const int C = clut[((size_t)Cz * cext.y + Cy) * cext.x + Cx];
+            if (C >= 0) {
+                const int lx = nx - 16 * (Cx + cmin.x), ly = ny - 16 * (Cy + cmin.y), lz = nz - 16 * (Cz + cmin.z);
+                val = vc[((size_t)C * ncv + c) * (BN * BN * BN) + (lz * BN + ly) * BN + lx];
+            }
+        }
+        tc_put<24>(sm, i / W, i % W, val);
+    }
+    uint32_t ph = 0;
+    bool ok = tc_pass<24, 16>(sm, 3, ph);
+    float v[16];
+    // D1 rows (lz, ly), cols ix  ->  A2 rows (lz, ix), k = ly
+    for (int mt = 0; mt < 3 && ok; mt++) {
+        const int r = mt * 128 + t;
+        tc_row<16>(sm.tmem_base, mt, v);
+        if (r < W * W) {
+            const int lz = r / W, ly = r % W;
+            for (int i = 0; i < BN; i++) tc_put<24>(sm, lz * BN + i, ly, v[i]);
+        }
+    }
+    tc::fence_before_sync();
+    if (ok) ok = tc_pass<24, 16>(sm, 3, ph = 1);
+    // D2 rows (lz, ix), cols iy  ->  A3 rows (iy, ix), k = lz
+    for (int mt = 0; mt < 3 && ok; mt++) {
+        const int r = mt * 128 + t;
+        tc_row<16>(sm.tmem_base, mt, v);
+        if (r < W * BN) {
+            const int lz = r / BN, ix = r % BN;
+            for (int i = 0; i < BN; i++) tc_put<24>(sm, i * BN + ix, lz, v[i]);
+        }
+    }
+    tc::fence_before_sync();
+    if (ok) ok = tc_pass<24, 16>(sm, 2, ph = 0);
+    // D3 rows (iy, ix), cols iz: added to the near field
+    float *o = dst + ((size_t)b * ncomp + c0 + c) * (BN * BN * BN);
+    for (int mt = 0; mt < 2 && ok; mt++) {
+        const int r = mt * 128 + t;
+        tc_row<16>(sm.tmem_base, mt, v);
+        for (int i = 0; i < BN; i++) o[i * BN * BN + r] += mul * v[i];
+    }
+    if (!ok && t == 0) atomicExch(err, 1);
+    tc_teardown<24>(sm, ok, ph);
     pdl_trigger();
 }
 
@@ -521,6 +745,34 @@ void interp_matrix(float P[BN * W])
     }
 }
 
+// B operands of the tensor-core steps, split into TF32 hi / lo parts, in the core-matrix
+// layout: anterpolation B[n = l][k = i] = P[i][l] (32 rows x K 16), interpolation
+// B[n = i][k = l] = P[i][l] (rows 16..31 zero, K 24).  out: [2][32 * K] (hi, then lo).
+void tc_weights(const float P[BN * W], bool anterp, std::vector<uint32_t> &out)
+{
+    const int K = anterp ? 16 : 24;
+    out.assign(2 * 32 * K, 0u);
+    for (int n = 0; n < 32; n++)
+        for (int k = 0; k < K; k++) {
+            float v = 0.f;
+            if (anterp && n < W) v = P[k * W + n];
+            if (!anterp && n < BN && k < W) v = P[n * W + k];
+            // TF32: round to nearest on the top 10 mantissa bits (ties away), as cvt.rna.tf32
+            auto tf32 = [](float x) {
+                uint32_t u;
+                std::memcpy(&u, &x, 4);
+                u = (u + 0x1000u) & 0xFFFFE000u;
+                float y;
+                std::memcpy(&y, &u, 4);
+                return y;
+            };
+            const float hi = tf32(v), lo = tf32(v - hi);
+            const int idx = ((n >> 3) * (K * 32) + (k >> 2) * 128 + (n & 7) * 16 + (k & 3) * 4) >> 2;
+            std::memcpy(&out[idx], &hi, 4);
+            std::memcpy(&out[32 * K + idx], &lo, 4);
+        }
+}
+
 }  // namespace
 
 void free_split(SplitPlan *sp)
@@ -540,6 +792,9 @@ void free_split(SplitPlan *sp)
     cudaFree(sp->d_clut);
     cudaFree(sp->d_stage_src);
     cudaFree(sp->d_stage_dst);
+    cudaFree(sp->d_Ba);
+    cudaFree(sp->d_Bi);
+    cudaFree(sp->d_err);
     if (sp->coarse) lgf_plan_destroy(sp->coarse);
     if (sp->far_table) lgf_table_destroy(sp->far_table);
     if (sp->far_stream) cudaStreamDestroy(sp->far_stream);
@@ -548,7 +803,7 @@ void free_split(SplitPlan *sp)
     delete sp;
 }
 
-lgf_status plan_split(lgf_plan *p, const lgf_solve_desc &d, double alpha, cudaStream_t s)
+lgf_status plan_split(lgf_plan *p, const lgf_solve_desc &d, double alpha, int far_precision, cudaStream_t s)
 {
     LGF_CHECK_ARG(d.B == BN, "block-sparse method: B=%d (the near-field blocks are 16^3)", d.B);
     LGF_CHECK_ARG(alpha >= 1.0 && alpha <= 64.0, "block-sparse method: split time %g outside [1, 64]", alpha);
@@ -559,6 +814,7 @@ lgf_status plan_split(lgf_plan *p, const lgf_solve_desc &d, double alpha, cudaSt
     }
     p->split = sp;
     sp->alpha = alpha;
+    sp->far_tensor_cores = far_precision == 1;
     sp->ncomp = d.ncomp;
     sp->nsrc = d.n_src;
     sp->ndst = d.n_dst;
@@ -668,6 +924,17 @@ lgf_status plan_split(lgf_plan *p, const lgf_solve_desc &d, double alpha, cudaSt
     float P[BN * W];
     interp_matrix(P);
     LGF_CUDA_TRY(cudaMemcpyToSymbol(c_P, P, sizeof(P)));
+    {
+        std::vector<uint32_t> ba, bi;
+        tc_weights(P, true, ba);
+        tc_weights(P, false, bi);
+        LGF_TRY(dalloc_n(&sp->d_Ba, ba.size(), bytes));
+        LGF_TRY(dalloc_n(&sp->d_Bi, bi.size(), bytes));
+        LGF_TRY(upload_v(sp->d_Ba, ba, s));
+        LGF_TRY(upload_v(sp->d_Bi, bi, s));
+        LGF_TRY(dalloc_n(&sp->d_err, 1, bytes));
+        LGF_CUDA_TRY(cudaMemsetAsync(sp->d_err, 0, sizeof(int), s));
+    }
     auto coarse_of = [&](const int32_t *bl, int n) {
         std::map<int64_t, int> m;  // ordered: deterministic coarse block order
         std::vector<int> out;
@@ -778,6 +1045,10 @@ lgf_status plan_split(lgf_plan *p, const lgf_solve_desc &d, double alpha, cudaSt
     if (p->device >= 0 && p->device < 64 && !attr_done[p->device]) {
         LGF_CUDA_TRY(cudaFuncSetAttribute(k_near_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NEAR_SMEM));
         LGF_CUDA_TRY(cudaFuncSetAttribute(k_near_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NEAR_SMEM));
+        LGF_CUDA_TRY(cudaFuncSetAttribute(k_far_anterp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sizeof(TcSmem<16>)));
+        LGF_CUDA_TRY(cudaFuncSetAttribute(k_far_interp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sizeof(TcSmem<24>)));
         attr_done[p->device] = true;
     }
     LGF_CUDA_TRY(cudaStreamSynchronize(s));
@@ -788,6 +1059,20 @@ lgf_status plan_split(lgf_plan *p, const lgf_solve_desc &d, double alpha, cudaSt
 // coarse convolution) on the plan's far stream, joined before the interpolation
 // adds the far field to the near result.  prof: per-kernel event timing (then all
 // launches go to s, one after another).
+lgf_status split_check(lgf_plan *p, cudaStream_t s)
+{
+    SplitPlan *sp = p->split;
+    int h = 0;
+    LGF_CUDA_TRY(cudaMemcpyAsync(&h, sp->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LGF_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h) {
+        LGF_CUDA_TRY(cudaMemsetAsync(sp->d_err, 0, sizeof(int), s));
+        set_error("a tensor-core wait of the far-field interpolation gave up (its result is not valid)");
+        return LGF_ERR_TIMEOUT;
+    }
+    return LGF_OK;
+}
+
 lgf_status run_split(lgf_plan *p, const float *src, float *dst, cudaStream_t s, Profiler *prof)
 {
     SplitPlan *sp = p->split;
@@ -802,8 +1087,13 @@ lgf_status run_split(lgf_plan *p, const float *src, float *dst, cudaStream_t s, 
     }
     // far field
     if (P) prof->begin(fs);
-    k_far_anterp<<<dim3(sp->nsrc, nc), 256, 0, fs>>>(src, nc, 0, sp->d_Q, nc);
-    LGF_LAUNCH_CHECK("k_far_anterp");
+    if (!sp->far_tensor_cores) {
+        k_far_anterp<<<dim3(sp->nsrc, nc), 256, 0, fs>>>(src, nc, 0, sp->d_Q, nc);
+        LGF_LAUNCH_CHECK("k_far_anterp");
+    } else {
+        LGF_CUDA_TRY(launch_pdl_smem(k_far_anterp_tc, dim3(sp->nsrc, nc), dim3(TC_THREADS), sizeof(TcSmem<16>), fs, src,
+                                     nc, 0, sp->d_Q, nc, (const uint32_t *)sp->d_Ba, sp->d_err));
+    }
     if (P) prof->end("far_anterp", fs);
     if (P) prof->begin(fs);
     k_far_gather<<<dim3(sp->ncsrc, nc), 256, 0, fs>>>(sp->d_Q, nc, sp->d_ccoords, sp->d_flut, sp->fmin, sp->fext,
@@ -834,9 +1124,15 @@ lgf_status run_split(lgf_plan *p, const float *src, float *dst, cudaStream_t s, 
     if (P) prof->end("near_inv", s);
     if (!P) LGF_CUDA_TRY(cudaStreamWaitEvent(s, sp->ev_far, 0));
     if (P) prof->begin(s);
-    k_far_interp<<<dim3(sp->ndst, nc), 256, 0, s>>>(sp->d_v, nc, sp->d_tcoords, sp->d_clut, sp->cmin, sp->cext, dst, nc,
-                                                    0, mul_far);
-    LGF_LAUNCH_CHECK("k_far_interp");
+    if (!sp->far_tensor_cores) {
+        k_far_interp<<<dim3(sp->ndst, nc), 256, 0, s>>>(sp->d_v, nc, sp->d_tcoords, sp->d_clut, sp->cmin, sp->cext, dst,
+                                                        nc, 0, mul_far);
+        LGF_LAUNCH_CHECK("k_far_interp");
+    } else {
+        LGF_CUDA_TRY(launch_pdl_smem(k_far_interp_tc, dim3(sp->ndst, nc), dim3(TC_THREADS), sizeof(TcSmem<24>), s,
+                                     (const float *)sp->d_v, nc, (const int *)sp->d_tcoords, (const int *)sp->d_clut,
+                                     sp->cmin, sp->cext, dst, nc, 0, mul_far, (const uint32_t *)sp->d_Bi, sp->d_err));
+    }
     if (P) prof->end("far_interp", s);
     return LGF_OK;
 }

@@ -86,6 +86,7 @@ _SIGS = {
     "lgf_plan_workspace_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     "lgf_plan_method": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)]),
+    "lgf_plan_check": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "lgf_conv_execute": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
                                         ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
     "lgf_conv_execute_f64": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
@@ -242,6 +243,10 @@ class Plan:
         a, b = ctypes.c_double(), ctypes.c_double()
         m = load().lgf_plan_method(self._h, ctypes.byref(a), ctypes.byref(b))
         return m, a.value, b.value
+
+    def check(self, stream=None):
+        """Synchronise and raise LGFError(LGF_ERR_TIMEOUT) if a bounded device wait gave up."""
+        _check(load().lgf_plan_check(self._h, _stream(stream)))
 
     def workspace_bytes(self) -> int:
         b = ctypes.c_size_t()

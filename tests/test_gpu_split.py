@@ -21,13 +21,13 @@ pytestmark = pytest.mark.gpu
 SPLIT = 1
 
 
-def _plan(lgf, src_c, dst_c, ncomp=1, scale=1.0, dx=1.0, method=SPLIT, use_graph=False):
+def _plan(lgf, src_c, dst_c, ncomp=1, scale=1.0, dx=1.0, method=SPLIT, use_graph=False, far_precision=0):
     # the split plan builds its own tables; the whole-box plan (methods 0 and 2) samples
     # this one up to half its FFT length (a box beyond the FFT limit gets the largest table)
     K = 31 if method == SPLIT else max(31, lgf.required_max_offset(src_c, dst_c, 16))
     t = lgf.Table(lgf.LAPLACE7, max_offset=min(K, 1024))
     return t, lgf.Plan(t, [lgf.Solve(16, ncomp, src_c, dst_c, dx=dx, scale=scale)], method=method,
-                       use_graph=use_graph)
+                       use_graph=use_graph, far_precision=far_precision)
 
 
 def _dilate(blocks, r=1):
@@ -66,6 +66,7 @@ def test_split_random_blocks_full(seed):
         err = rel_l2(out[:, c].reshape(-1), ref)
         assert err < 1e-6, (c, err)
     assert plan.method()[0] == SPLIT
+    plan.check()            # no bounded tensor-core wait gave up
 
 
 def test_split_ring128_whole_field():
@@ -195,3 +196,32 @@ def test_split_host_buffers_residual_and_autotune():
         assert torch.equal(a_dst, d_dst)
     else:
         assert rel_l2(a_dst.cpu().numpy(), d_dst.cpu().numpy()) < 2e-6
+
+
+def test_split_tensor_core_far_field():
+    """The reduced-precision far field (far_precision = 1): interpolation and anterpolation
+    as tcgen05 TF32 GEMMs on operands split into two TF32 parts.  On the 256^3 shell the
+    solve stays within the 1e-5 stated for it against the FP64 direct sum, and within 2e-6
+    of the FP32 CUDA-core far field; no bounded tensor-core wait gives up."""
+    lgf = built()
+    B, n = 16, 256
+    axis = inputs.random_axis_tilted(inputs.rng_for(4))
+    w = inputs.vortex_ring_edges(n, 50.0, 10.0, axis)[0]
+    src_c = inputs.active_blocks(w, B, 1e-6)
+    dst_c = _dilate(src_c)
+    f = inputs.to_blocks(w, B, src_c)
+    d_src = torch.from_numpy(f).cuda()
+    outs = []
+    for fp in (0, 1):
+        _, plan = _plan(lgf, src_c, dst_c, scale=-1.0, far_precision=fp)
+        d = torch.zeros((len(dst_c), 1, B, B, B), device="cuda")
+        plan.execute([d_src], [d])
+        plan.check()
+        outs.append(d.cpu().numpy())
+    assert rel_l2(outs[1], outs[0]) < 2e-6, rel_l2(outs[1], outs[0])
+    rng = np.random.default_rng(19)
+    pts_all = inputs.block_points(dst_c, B)
+    pts = pts_all[rng.choice(len(pts_all), 1024, replace=False)]
+    ref = oracle_poisson_blocks(f, src_c, B, pts, lgf.required_max_offset(src_c, dst_c, B), scale=-1.0)
+    err = rel_l2(block_values_at(outs[1], dst_c, B, pts), ref)
+    assert err < 1e-5, err
