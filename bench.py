@@ -308,7 +308,8 @@ def bench_gpu(args):
     table = lgf.Table(lgf.LAPLACE7, max_offset=K)
     # the library runs the three components on three streams (one launch per pass
     # and component); the launch sequence is captured in a CUDA graph on first use
-    plan = lgf.Plan(table, [lgf.Solve(B, 3, src_c, dst_c, scale=-1.0)], use_graph=True)
+    plan = lgf.Plan(table, [lgf.Solve(B, 3, src_c, dst_c, scale=-1.0)], use_graph=True, method=lgf.METHOD_AUTOTUNE)
+    chosen, auto_wb, auto_split = plan.method()
     stream = torch.cuda.current_stream()
     d_src = torch.from_numpy(f).cuda()
     d_dst = torch.zeros((len(dst_c), 3, B, B, B), device="cuda")
@@ -397,6 +398,8 @@ def bench_gpu(args):
     hbm, src_kind = peaks()
     alg_bytes = 8 * len(dst_c) * B ** 3            # one component
     achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
+    if dom not in pb:      # the autotuner chose the split solve: no per-pass workspace or flop model
+        pb[dom], pf[dom] = 0, 0.0
     step_gbs = 8 * pts_per_step / (dev_ms / args.steps / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4), "traffic": None,
@@ -422,8 +425,8 @@ def bench_gpu(args):
                "peaks_measured_tflops": peaks_tf,
                "peak_source": "lgf_measure_peak: FMA chains on every SM, CUDA events, measured in this run"}
     shares = {k: {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / sum(x[1] for x in kt.values()), 4),
-                  "workspace_gbs": round(pb[k] * v[0] / (v[1] / 1e3) / 1e9, 1),
-                  "tflops": round(pf[k] * v[0] / (v[1] / 1e3) / 1e12, 2)} for k, v in kt.items()}
+                  "workspace_gbs": round(pb.get(k, 0) * v[0] / (v[1] / 1e3) / 1e9, 1),
+                  "tflops": round(pf.get(k, 0.0) * v[0] / (v[1] / 1e3) / 1e12, 2)} for k, v in kt.items()}
     # CPU baseline: oracle on a bounded sample (rank 0, N=1 only)
     cpu = cpu_fft = None
     if ws == 1 and not args.no_cpu_baseline:
@@ -436,7 +439,10 @@ def bench_gpu(args):
                            "oracle's table)",
                    "sample": "the full solve, best of 2: %.2f s" % fdt, "rel_l2_vs_gpu": fdiff}
     cfg = dict(cfg)
-    cfg.update({"fft_grid": geom["N"], "execution": "one stream per component, launch sequence replayed as a CUDA graph",
+    cfg.update({"method": {"chosen": ["whole-box FFT convolution", "block-sparse split solve"][chosen],
+                           "autotune_ms": {"whole_box": round(auto_wb, 4), "split": round(auto_split, 4)},
+                           "rule": "lgf_conv_plan method 2: both planned, one timed execution each, the faster kept"},
+                "fft_grid": geom["N"], "execution": "one stream per component, launch sequence replayed as a CUDA graph",
                 "plain_ms": round(plain_ms, 4), "batched_over_plain": round(plain_ms / (dev_ms / args.steps), 3),
                 "plain": "one component per solve, three solves one after another on one stream, no graph",
                 "l2": "256 MiB buffer rewritten between timed steps (outside the events)",
@@ -608,6 +614,41 @@ def aux_workload(name, lgf, torch):
             "supp_blocks": int(len(supp)), "xsoln_blocks": int(len(xs)), "scalar_ms": round(ms1, 4),
             "vector_ms": round(ms3, 4), "vector_to_scalar_ratio": round(ms3 / ms1, 3),
             "points": "3 x D_xsoln points per vector solve"}, [t, p1]
+    if name in ("shell256", "shell256_split", "shell256_split_tc"):
+        # one scalar Poisson solve D_supp -> D_xsoln of the 256^3 Re = 500 ring shell, by the
+        # whole-box FFT convolution or by the block-sparse split solve (FP32 far field on the
+        # CUDA cores, or the reduced-precision far field on the tensor cores)
+        axis = inputs.random_axis_tilted(inputs.rng_for(4))
+        w = inputs.vortex_ring_edges(256, 50.0, 10.0, axis)[0]
+        supp = inputs.active_blocks(w, B, 1e-6)
+        xs = _dilate(supp)
+        method = 0 if name == "shell256" else 1
+        K = lgf.required_max_offset(supp, xs, B) if method == 0 else 31
+        t = lgf.Table(lgf.LAPLACE7, max_offset=K)
+        p = lgf.Plan(t, [lgf.Solve(B, 1, supp, xs, scale=-1.0)], method=method, use_graph=True,
+                     far_precision=1 if name.endswith("_tc") else 0)
+        f = torch.from_numpy(inputs.to_blocks(w, B, supp)).cuda()
+        o = torch.zeros((len(xs), 1, B, B, B), device="cuda")
+        return (lambda: p.execute([f], [o])), [p], len(xs) * B ** 3, {
+            "workload": "scalar Poisson solve D_supp -> D_xsoln of the 256^3 Re = 500 ring shell (w_x), "
+                        + {0: "whole-box FFT convolution", 1: "block-sparse split solve"}[method]
+                        + (", far field on the tensor cores (tcgen05, TF32 split)" if name.endswith("_tc") else ""),
+            "supp_blocks": int(len(supp)), "xsoln_blocks": int(len(xs)), "points": "D_xsoln points per solve"}, [t]
+    if name == "thinring_split":
+        # the thinnest ring of Sec. 6 (delta / R0 = 0.0125: R0 = 400 cells, core 5 cells), w_x on the
+        # blocks above 1e-6 max, targets their one-block dilation: its bounding box (about 750 cells
+        # across) is beyond the whole-box embedding's 1024-point FFTs; the split solve runs it
+        src_c, vals = inputs.thin_ring_blocks()
+        xs = _dilate(src_c)
+        t = lgf.Table(lgf.LAPLACE7, max_offset=31)
+        p = lgf.Plan(t, [lgf.Solve(B, 1, src_c, xs, scale=-1.0)], method=1, use_graph=True)
+        f = torch.from_numpy(vals).cuda()
+        o = torch.zeros((len(xs), 1, B, B, B), device="cuda")
+        ext = (src_c.max(0) - src_c.min(0) + 1) * B
+        return (lambda: p.execute([f], [o])), [p], len(xs) * B ** 3, {
+            "workload": "scalar Poisson solve of the delta/R0 = 0.0125 ring (R0 = 400 cells, core 5 cells), "
+                        "block-sparse split solve", "supp_blocks": int(len(src_c)), "xsoln_blocks": int(len(xs)),
+            "source_extent_cells": [int(e) for e in ext], "points": "D_xsoln points per solve"}, [t]
     if name == "ragged64":
         fs = inputs.ragged_ring_sources(nsolve=64)
         solves, srcs, dsts, pts = [], [], [], 0
@@ -724,7 +765,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="ring128",
                     choices=["ring128", "blobs32", "blobs32_f64", "if128", "rk256", "rk256_b", "rk256_c",
-                             "rk256_refresh", "vecscal256", "ragged64"],
+                             "rk256_refresh", "vecscal256", "ragged64", "shell256", "shell256_split",
+                             "shell256_split_tc", "thinring_split"],
                     help="ring128 is the headline workload; the others print their own throughput")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -182,6 +182,36 @@ def two_rings_vorticity(cfg: int = 3, n: int = 128, sigma: float = 3.0):
     return w
 
 
+def thin_ring_blocks(R: float = 400.0, sigma: float = 5.0, B: int = 16, rel_thresh: float = 1e-6, cfg: int = 6):
+    """A thin Gaussian-core ring of radius R cells and core sigma (delta/R0 = 0.0125 at the
+    defaults, the thinnest ring of Sec. 6) centred at the origin, axis tilted as in the 128^3
+    ring case; the scalar source is the x-component of its vorticity at edge(1) centres,
+    kept on the blocks whose |w| exceeds rel_thresh * max.  Only blocks near the torus are
+    sampled, so the box (about 2R + 12 sigma across) is never held densely.
+    Returns (block coordinates [n, 3], values [n, 1, B, B, B] float32)."""
+    rng = rng_for(cfg)
+    axis = random_axis_tilted(rng)
+    reach = 6.0 * sigma + B                       # torus half-thickness plus one block
+    span = int(math.ceil((R + reach) / B)) + 1
+    g = np.arange(-span, span)
+    bz, by, bx = np.meshgrid(g, g, g, indexing="ij")
+    cen = (np.stack([bx.ravel(), by.ravel(), bz.ravel()], 1) + 0.5) * B
+    Rm = _rotation(axis)
+    p = cen @ Rm
+    rho = np.hypot(p[:, 0], p[:, 1])
+    near = np.hypot(rho - R, p[:, 2]) < reach
+    cand = np.stack([bx.ravel(), by.ravel(), bz.ravel()], 1)[near].astype(np.int32)
+    k, j, i = np.meshgrid(np.arange(B), np.arange(B), np.arange(B), indexing="ij")
+    loc = np.stack([i.ravel(), j.ravel(), k.ravel()], 1).astype(float) + np.array([-0.5, 0.0, 0.0])  # edge(1)
+    vals = np.zeros((len(cand), 1, B, B, B), dtype=np.float32)
+    for n, c in enumerate(cand):
+        w = ring_vorticity(c * B + loc, np.zeros(3), axis, R, sigma)[:, 0]
+        vals[n, 0] = w.reshape(B, B, B)
+    mx = np.abs(vals).reshape(len(cand), -1).max(1)
+    keep = mx > rel_thresh * mx.max()
+    return cand[keep], vals[keep]
+
+
 def ragged_ring_sources(nsolve: int = 64, emin: int = 24, emax: int = 192, cfg: int = 5):
     """Ragged batch: per solve an edge e ~ round(exp(U[ln emin, ln emax])), a ring with
     R ~ U[4, min(40, (e/2 - 2)/1.75)], sigma = R/8, axis uniform on S^2, centred in the box;

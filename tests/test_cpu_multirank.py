@@ -76,3 +76,51 @@ def test_reference_arm_other_rank_does_no_work(monkeypatch):
     monkeypatch.setattr(bench, "oracle_sampler", boom)
     monkeypatch.setattr(bench, "workload", boom)
     assert bench.bench_reference(Args()) == 0
+
+
+def _replica_worker(rank, world, port, q):
+    """One rank of the replica path: the rank builds the benchmarked workload (seeded, the
+    same on every rank), runs its own replica of a small solve (the oracle's direct sum at a
+    few targets stands in for the GPU solve on this CPU-only box), times it, and the job
+    takes the slowest rank's time; no data crosses ranks."""
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    import time
+    import numpy as np
+    import torch.distributed as tdist
+    tdist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    import oracle as O
+    from paper_1601_00035_gb300 import inputs
+    f, src_c, dst_c, cfg = bench.workload()
+    pts = inputs.block_points(src_c, bench.B)
+    v = f[:, 0].reshape(-1).astype(np.float64)
+    nz = v != 0
+    tgt = inputs.block_points(dst_c, bench.B)[::4099][:64]
+    tdist.barrier()
+    t0 = time.perf_counter()
+    u = O.direct_conv(O.lgf_cube(127), pts[nz], -v[nz], tgt)
+    dt = time.perf_counter() - t0
+    tdist.barrier()
+    slowest = bench.max_over_ranks(dt)
+    q.put((rank, float(np.abs(u).sum()), dt, slowest, bench.job_rate(len(tgt), 1, world, slowest)))
+    tdist.destroy_process_group()
+
+
+def test_two_rank_replicas():
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_replica_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=300) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res[0][1] == res[1][1] > 0                      # identical replicas
+    assert res[0][3] == res[1][3] == max(res[0][2], res[1][2])   # the job's time is the slowest rank's
+    assert res[0][4] == pytest.approx(2 * 64 / res[0][3] / 1e6)  # both ranks' points over that time

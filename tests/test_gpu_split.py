@@ -225,3 +225,31 @@ def test_split_tensor_core_far_field():
     ref = oracle_poisson_blocks(f, src_c, B, pts, lgf.required_max_offset(src_c, dst_c, B), scale=-1.0)
     err = rel_l2(block_values_at(outs[1], dst_c, B, pts), ref)
     assert err < 1e-5, err
+
+
+def test_split_thin_ring_sampled():
+    """The thinnest ring of Sec. 6 (delta / R0 = 0.0125: R0 = 400 cells, 5-cell core, tilted),
+    whose bounding box (about 750 cells across) the whole-box embedding cannot take: the
+    split solve on its 1616 source blocks and their dilation, 512 sampled targets against
+    the direct sum."""
+    lgf = built()
+    B = 16
+    src_c, vals = inputs.thin_ring_blocks()
+    dst_c = _dilate(src_c)
+    with pytest.raises(lgf.LGFError):
+        _plan(lgf, src_c, dst_c, method=0)
+    _, plan = _plan(lgf, src_c, dst_c, scale=-1.0)
+    d_dst = torch.zeros((len(dst_c), 1, B, B, B), device="cuda")
+    plan.execute([torch.from_numpy(vals).cuda()], [d_dst])
+    plan.check()
+    out = d_dst.cpu().numpy()
+    rng = np.random.default_rng(400)
+    pts_all = inputs.block_points(dst_c, B)
+    pts = pts_all[rng.choice(len(pts_all), 512, replace=False)]
+    sp = inputs.block_points(src_c, B)
+    v = vals.reshape(-1).astype(np.float64)
+    nz = v != 0
+    offs_max = int(max(np.abs(pts.max(0) - sp.min(0)).max(), np.abs(sp.max(0) - pts.min(0)).max()))
+    ref = -O.direct_conv(O.lgf_cube(offs_max), sp[nz], v[nz], pts)
+    err = rel_l2(block_values_at(out, dst_c, B, pts), ref)
+    assert err < 1e-6, err
