@@ -542,7 +542,7 @@ def aux_workload(name, lgf, torch):
             "batched_over_plain": round(plain_ms / batched_ms, 3),
             "plain": "one component per integrating-factor application (9 applications) and the Poisson "
                      "solve, separate launches on one stream, no graph"}, tabs + [tp]
-    if name in ("rk256", "rk256_b", "rk256_c", "rk256_refresh"):
+    if name in ("rk256", "rk256_b", "rk256_c", "rk256_refresh", "rk256_vort"):
         n, R0c, dcells = 256, 50.0, 10.0
         dx = 1.0 / R0c                      # R0 = 1, Gamma = 1
         dt, re = 0.01721, 500.0             # Sec. 6.4: dt Gamma/R0^2 = 0.01721, Re = 500
@@ -550,7 +550,7 @@ def aux_workload(name, lgf, torch):
         axis = inputs.random_axis_tilted(inputs.rng_for(4))
         w = inputs.vortex_ring_edges(n, R0c, dcells, axis) / dx ** 2   # physical vorticity
         supp = inputs.active_blocks(w, B, 1e-6)
-        scheme = {"rk256": 0, "rk256_b": 1, "rk256_c": 2, "rk256_refresh": 0}[name]
+        scheme = {"rk256": 0, "rk256_b": 1, "rk256_c": 2, "rk256_refresh": 0, "rk256_vort": 0}[name]
         rk = lgf.RKPlan(B, supp, dx, dt, re, scheme=scheme, use_graph=True)
         xs = rk.blocks(0)
         # initial velocity by the method itself: a = -L^-1 w (vector, D_supp -> D_xsoln), u = C^T a
@@ -563,6 +563,16 @@ def aux_workload(name, lgf, torch):
         u0 = torch.zeros_like(a)
         rk.op(lgf.OP_CURL_T, a, u0)
         u1 = torch.zeros_like(u0)
+        if name == "rk256_vort":
+            # the vorticity formulation of Sec. 4.1: a vector Poisson solve per stage
+            w0 = torch.zeros_like(u0)
+            rk.op(lgf.OP_CURL, u0, w0)
+            w1 = torch.zeros_like(u0)
+            return (lambda: rk.step_vorticity(w0, w1, uinf)), [rk], len(xs) * B ** 3, {
+                "workload": "one Scheme-A step of the vorticity formulation (Sec. 4.1: curl of the momentum equation, "
+                            "velocity by a vector Poisson solve D_supp -> D_xsoln per stage), Re=500 ring, 256^3 box",
+                "supp_blocks": int(len(supp)), "xsoln_blocks": int(len(xs)), "points": "D_xsoln points per step",
+                "compare": "rk256: the primitive-variable step on the same blocks"}, [t, pv]
         if name == "rk256_refresh":
             return (lambda: rk.refresh(u0, u1)), [rk], len(xs) * B ** 3, {
                 "workload": "velocity refresh u = C^T(-L^-1 C u) (vector Poisson D_supp -> D_xsoln), Re=500 ring, "
@@ -766,7 +776,7 @@ def main():
     ap.add_argument("--workload", default="ring128",
                     choices=["ring128", "blobs32", "blobs32_f64", "if128", "rk256", "rk256_b", "rk256_c",
                              "rk256_refresh", "vecscal256", "ragged64", "shell256", "shell256_split",
-                             "shell256_split_tc", "thinring_split"],
+                             "shell256_split_tc", "thinring_split", "rk256_vort"],
                     help="ring128 is the headline workload; the others print their own throughput")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -277,6 +277,15 @@ lgf_status lgf_rk_blocks(const lgf_plan *p, int which, int32_t *coords, int n);
  * five integrating-factor applications (six for Scheme C, whose H^3 is not the identity), three
  * nonlinear terms.  Asynchronous; no allocation. */
 lgf_status lgf_rk_step(lgf_plan *p, const float *u_in, float *u_out, const double uinf[3], void *stream);
+/* One step of the vorticity formulation of Sec. 4.1 (the discrete curl of eq. dnstp,
+ * dw/dt = L w / Re - C N~(u + u_inf) with u = -C^T L^{-1} w, eq. vel_vor), integrated with the
+ * plan's IF-HERK tableau and integrating factors (Sec. 3.2; no constraint, so no projection).
+ * w_in, w_out: edge vorticity on D_xsoln, device [n_xsoln][3][B^3] (component q is the x_q-edge
+ * value), must not alias.  Each stage solves a VECTOR Poisson problem D_supp -> D_xsoln for the
+ * velocity (the cost the paper cites for not pursuing this form) and applies
+ * g^i = -a~_ii dt M^soln C M^soln N~(M^xsoln (u + u_inf)).  Algebraically the curl of lgf_rk_step.
+ * Asynchronous; no allocation. */
+lgf_status lgf_rk_step_vorticity(lgf_plan *p, const float *w_in, float *w_out, const double uinf[3], void *stream);
 /* Velocity refresh of Sec. 5 (eq. vel_refresh): u_out = M^xsoln C^T M^xsoln a with
  * a = -M^xsoln L^{-1} M^supp w and w = M^xsoln C M^xsoln u_in (a vector Poisson solve
  * D_supp -> D_xsoln).  u_in, u_out device [n_xsoln][3][B^3]; u_out may equal u_in.

@@ -31,7 +31,7 @@ __all__ = [
     "op_Dbar", "op_L", "op_N", "residual_L", "WATSON_W", "num_threads", "SCHEME_A", "SCHEME_B", "SCHEME_C",
     "SCHEMES", "shifted_tableau",
     "block_mask", "ifactor_masked", "poisson_masked", "if_herk_step", "lgf_points", "ifactor_tail", "rk_qmax",
-    "vor2vel", "ring_diagnostics", "regrid_weights", "fft_conv",
+    "vor2vel", "ring_diagnostics", "regrid_weights", "fft_conv", "vel_from_vort", "if_herk_step_vorticity",
 ]
 
 # Watson's integral for the simple cubic lattice, closed form (Watson 1939):
@@ -561,3 +561,50 @@ def if_herk_step(u, dt, re, dx, uinf, masks, cube, nonlinear=True, tab=SCHEME_A)
                 w[(i + 1, j)] = applyH(i, w[(i, j)])
         u_prev = u_i
     return u_prev
+
+
+def vel_from_vort(w, masks, cube, dx):
+    """u = M^xsoln C^T M^xsoln a, a = -M^xsoln L^{-1} M^supp w per component (Sec. 4.1 eq. vel_vor
+    with the masks of Sec. 5), for an edge field w on D_xsoln."""
+    xs = masks["xsoln"]
+    a = np.stack([-poisson_masked(cube, w[q], masks["supp"], xs, dx) for q in range(3)])
+    return op_Ct(a * xs, dx) * xs
+
+
+def if_herk_step_vorticity(w, dt, re, dx, uinf, masks, cube, tab=SCHEME_A):
+    """One step of the vorticity formulation of Sec. 4.1: the discrete curl of eq. dnstp,
+        dw/dt = (1/Re) L w - C N~(u + u_inf),   u = -C^T L^{-1} w   (eq. vel_vor),
+    integrated with the IF-HERK algorithm of Sec. 3.2 in the paper's q / w recursions; there is no
+    constraint, so each stage value is the integrating factor applied to r^i (no projection).
+    Masks (reading: Sec. 5 carried over): w lives on D_xsoln, the integrating factors are
+    M^xsoln E M^xsoln, the velocity takes its Poisson source on D_supp, and the stage term is
+    g^i = -a~_ii dt M^soln C M^soln N~(M^xsoln (u^{i-1} + u_inf))."""
+    at, ct, s = shifted_tableau(tab)
+    xs, so = masks["xsoln"], masks["soln"]
+    alpha = dt / (dx * dx * re)
+    H = {}
+    for i in range(1, s + 1):
+        a = (ct[i] - ct[i - 1]) * alpha
+        H[i] = None if a == 0.0 else ifactor_taps(a)
+
+    def applyH(i, f):
+        return f * xs if H[i] is None else ifactor_masked(H[i], f, xs)
+
+    uinf = np.asarray(uinf, dtype=float).reshape(3, 1, 1, 1)
+    q = {1: w.copy()}
+    z = {}
+    w_prev = w
+    for i in range(1, s + 1):
+        u = vel_from_vort(w_prev, masks, cube, dx)
+        g = -at[(i, i)] * dt * op_C(op_N((u + uinf) * xs, dx) * so, dx) * so
+        r = q[i] + g
+        for j in range(1, i):
+            r = r + dt * at[(i, j)] * z[(i, j)]
+        w_i = applyH(i, r * xs)
+        z[(i, i)] = g / (at[(i, i)] * dt)
+        if i < s:
+            q[i + 1] = applyH(i, q[i])
+            for j in range(1, i + 1):
+                z[(i + 1, j)] = applyH(i, z[(i, j)])
+        w_prev = w_i
+    return w_prev

@@ -1105,6 +1105,7 @@ lgf_status lgf_plan_set_profiling(lgf_plan *p, int enable)
     p->prof.on = enable != 0;
     if (p->rk) {  // an RK plan also times the kernels of its Poisson and IF sub-plans
         LGF_TRY(lgf_plan_set_profiling(p->rk->poisson, enable));
+        LGF_TRY(lgf_plan_set_profiling(p->rk->poisson3, enable));
         for (int i = 0; i < 3; i++)
             if (p->rk->if_owned[i]) LGF_TRY(lgf_plan_set_profiling(p->rk->ifp[i], enable));
     }
@@ -1116,7 +1117,7 @@ static lgf_status merge_sub_profiles(lgf_plan *p)
 {
     LGF_TRY(p->prof.collect());
     if (!p->rk) return LGF_OK;
-    std::vector<lgf_plan *> subs = {p->rk->poisson};
+    std::vector<lgf_plan *> subs = {p->rk->poisson, p->rk->poisson3};
     for (int i = 0; i < 3; i++)
         if (p->rk->if_owned[i]) subs.push_back(p->rk->ifp[i]);
     for (lgf_plan *sub : subs) {

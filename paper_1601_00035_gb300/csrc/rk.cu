@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <cmath>
 #include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "plan.hpp"
@@ -297,8 +298,9 @@ lgf_status lgf_rk_plan(const lgf_rk_desc *d, void *stream, lgf_plan **out)
     r->scal_x = (size_t)nx * B3;
     r->scal_s = (size_t)nsoln * B3;
     // 8 vectors (slot 5 holds a multi-step run's intermediate state), d^ on D_xsoln and
-    // D_supp, and w on D_supp (3 components) for the refresh
-    const size_t total = 8 * r->vec + r->scal_x + r->scal_s + 3 * r->scal_s;
+    // D_supp, w on D_supp (3 components) for the refresh, and 2 more vectors for the
+    // vorticity-formulation step
+    const size_t total = 8 * r->vec + r->scal_x + r->scal_s + 3 * r->scal_s + 2 * r->vec;
     if (cudaMalloc(&r->work, total * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         set_error("lgf_rk_plan: workspace allocation of %zu bytes failed", total * sizeof(float));
@@ -475,7 +477,87 @@ lgf_status rk_vor2vel_supp(lgf_plan *p, float *u_out, cudaStream_t s)
 }
 }  // namespace lgf
 
+namespace lgf {
+// One step of the vorticity formulation (Sec. 4.1): the curl of eq. dnstp,
+// dw/dt = L w / Re - C N~(u + u_inf) with u = -C^T L^{-1} w (eq. vel_vor), by the IF-HERK
+// recursion of Sec. 3.2 without a constraint.  Per stage: the velocity of the previous stage
+// value (a vector Poisson solve D_supp -> D_xsoln and C^T), g^i = -a~_ii dt M^soln C M^soln
+// N~(M^xsoln (u + u_inf)), and the integrating factors applied to q and to the w^{i,j}
+// (linearity gives the stage value from them); the last stage applies H^s to r^s.
+static lgf_status rk_step_vorticity_launches(lgf_plan *p, const float *w_in, float *w_out, const double uinf[3],
+                                             cudaStream_t s)
+{
+    RkPlan *r = p->rk;
+    const double dt = r->dt;
+    const size_t V = r->vec;
+    const int B = r->B, B3 = B * B * B;
+    // q, w^{i,1}, w^{i,2} and one spare buffer rotate through slots 2-5 (the integrating
+    // factor does not work in place)
+    float *g = r->work, *q = r->work + 2 * V, *z[2] = {r->work + 3 * V, r->work + 4 * V}, *spare = r->work + 5 * V;
+    float *u = r->work + 6 * V, *f = r->work + 7 * V;
+    float *ws = r->work + 8 * V + r->scal_x + r->scal_s;  // w on D_supp (Poisson source)
+    float *wi = ws + 3 * r->scal_s, *rv = wi + V;          // stage value, r^s
+    Profiler &pr = p->prof;
+    auto H = [&](int k, const float *x, float *y) -> lgf_status {
+        if (!r->ifp[k - 1])
+            return timed(pr, "lincomb", s, [&] {
+                return lincomb_launch(y, (int64_t)V, x, 1.0, nullptr, 0.0, nullptr, 0.0, nullptr, 0.0, s);
+            });
+        IfIO io;
+        io.x0 = x;
+        return ifactor_apply_io(r->ifp[k - 1], io, y, s);
+    };
+    auto LC = [&](float *o, const float *x0, double c0, const float *x1 = nullptr, double c1 = 0,
+                  const float *x2 = nullptr, double c2 = 0, const float *x3 = nullptr, double c3 = 0) {
+        return timed(pr, "lincomb", s, [&] { return lincomb_launch(o, (int64_t)V, x0, c0, x1, c1, x2, c2, x3, c3, s); });
+    };
+    const float *wprev = w_in;
+    for (int i = 1; i <= 3; i++) {
+        const double aii = r->at[i][i];
+        // velocity of the previous stage value (eq. vel_vor, source on D_supp)
+        LGF_TRY(timed(pr, "gather_supp", s, [&] { return gather_launch(wprev, ws, r->d_supp_idx, r->n_soln, 3 * B3, s); }));
+        LGF_TRY(rk_vor2vel_supp(p, u, s));
+        // g = -a~_ii dt M^soln C M^soln N~(M^xsoln (u + u_inf)); the D_soln blocks come first
+        LGF_TRY(timed(pr, "op_nonlinear", s, [&] {
+            return op_launch(4, B, r->n_x, r->d_nbr27, r->d_soln_keep, u, f, r->dx, -aii * dt, uinf, s);
+        }));
+        LGF_TRY(timed(pr, "op_curl", s, [&] { return op_launch(0, B, r->n_x, r->d_nbr27, nullptr, f, g, r->dx, 1.0, nullptr, s); }));
+        if (r->n_x > r->n_soln)
+            LGF_CUDA_TRY(cudaMemsetAsync(g + (size_t)r->n_soln * 3 * B3, 0, (size_t)(r->n_x - r->n_soln) * 3 * B3 * sizeof(float), s));
+        if (i < 3) {
+            LGF_TRY(LC(z[i - 1], g, 1.0 / (aii * dt)));  // w^{i,i}
+            if (i == 1) {
+                LGF_TRY(H(1, w_in, q));  // q^2 = H^1 q^1, q^1 = w_k
+            } else {
+                LGF_TRY(H(i, q, spare));  // q^{i+1} = H^i q^i
+                std::swap(q, spare);
+            }
+            for (int j = 1; j <= i; j++) {  // w^{i+1,j} = H^i w^{i,j}
+                LGF_TRY(H(i, z[j - 1], spare));
+                std::swap(z[j - 1], spare);
+            }
+            // stage value H^i r^i = q^{i+1} + dt sum_{j<=i} a~_ij w^{i+1,j}
+            if (i == 1) LGF_TRY(LC(wi, q, 1.0, z[0], dt * r->at[1][1]));
+            else LGF_TRY(LC(wi, q, 1.0, z[0], dt * r->at[2][1], z[1], dt * r->at[2][2]));
+            wprev = wi;
+        } else {
+            LGF_TRY(LC(rv, q, 1.0, z[0], dt * r->at[3][1], z[1], dt * r->at[3][2], g, 1.0));  // r^3
+            LGF_TRY(H(3, rv, w_out));
+        }
+    }
+    return LGF_OK;
+}
+}  // namespace lgf
+
 extern "C" {
+
+lgf_status lgf_rk_step_vorticity(lgf_plan *p, const float *w_in, float *w_out, const double uinf[3], void *stream)
+{
+    clear_error();
+    LGF_CHECK_ARG(p && w_in && w_out && uinf && w_in != w_out, "lgf_rk_step_vorticity: NULL or aliasing argument");
+    LGF_CHECK_ARG(p->kind == LGF_PLAN_RK, "lgf_rk_step_vorticity: needs a plan from lgf_rk_plan");
+    return rk_step_vorticity_launches(p, w_in, w_out, uinf, (cudaStream_t)stream);
+}
 
 lgf_status lgf_rk_refresh(lgf_plan *p, const float *u_in, float *u_out, void *stream)
 {

@@ -108,6 +108,8 @@ _SIGS = {
     "lgf_rk_blocks": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_int]),
     "lgf_rk_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                    ctypes.c_void_p]),
+    "lgf_rk_step_vorticity": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "lgf_op_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                                     ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "lgf_rk_refresh": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -363,6 +365,11 @@ class RKPlan:
     def step(self, u_in, u_out, uinf=(0.0, 0.0, 0.0), stream=None):
         ui = (ctypes.c_double * 3)(*[float(v) for v in uinf])
         _check(load().lgf_rk_step(self._h, _ptr(u_in), _ptr(u_out), ui, _stream(stream)))
+
+    def step_vorticity(self, w_in, w_out, uinf=(0.0, 0.0, 0.0), stream=None):
+        """One step of the vorticity formulation (lgf_rk_step_vorticity): edge vorticity on D_xsoln."""
+        ui = (ctypes.c_double * 3)(*[float(v) for v in uinf])
+        _check(load().lgf_rk_step_vorticity(self._h, _ptr(w_in), _ptr(w_out), ui, _stream(stream)))
 
     def refresh(self, u_in, u_out, stream=None):
         """Velocity refresh (lgf_rk_refresh); u_out may be u_in."""

@@ -429,3 +429,24 @@ def test_full_size_graph_step_divergence_free():
     assert d < 1e-5 * u.abs().max().item() / dx, d
     I1 = rk.diagnostics(u)["I"]
     assert np.abs(I1 - I0).max() < 1e-5 * np.linalg.norm(I0)
+
+
+@pytest.mark.parametrize("scheme", ["A", "B", "C"])
+def test_vorticity_step_matches_oracle(scheme):
+    """lgf_rk_step_vorticity (Sec. 4.1 vorticity formulation, a vector Poisson solve per stage)
+    against the oracle's step in the paper's q / w recursions."""
+    lgf = built()
+    cs = small_case(B=8, amp=3.0)
+    B, n, org, dx = cs["B"], cs["n"], cs["origin"], cs["dx"]
+    dt, re, uinf = 0.5, 10.0, (0.05, -0.02, 0.1)
+    rk, xs = _plan(lgf, cs, dt, re, scheme="ABC".index(scheme))
+    m = cs["masks"]
+    w0 = O.op_C(cs["u0"] * m["xsoln"], dx) * m["xsoln"]
+    ref = O.if_herk_step_vorticity(w0, dt, re, dx, uinf, m, O.lgf_cube(64), tab=O.SCHEMES[scheme])
+    d_w0 = torch.from_numpy(to_blocks_dense(w0, B, xs, org)).cuda()
+    d_w1 = torch.zeros_like(d_w0)
+    rk.step_vorticity(d_w0, d_w1, uinf)
+    torch.cuda.synchronize()
+    got = from_blocks_dense(d_w1.cpu().numpy(), B, xs, org, (n, n, n))
+    assert rel_l2(got - w0, ref - w0) < 2e-6, rel_l2(got - w0, ref - w0)
+    assert rel_l2(got, ref) < 1e-6
