@@ -139,7 +139,7 @@ void lgf_table_destroy(lgf_table *t);
  * zero-padded FFT grid of each distinct grid size (Hockney's free-space
  * embedding of eq. dpoisson_conv: exact up to FP32 rounding, no far-field
  * approximation), and allocates every workspace.  Per axis the FFT length is
- * the smallest of 16, 32, 64, 96, 128, 192, 256, 384, 512, 1024 that is
+ * the smallest of 16, 32, 64, 96, 128, 192, 256, 384, 512, 768, 1024 that is
  * >= max(2 m + 2, 2 E), m the largest |target - source| offset and E the
  * source extent (points); at most 1024 (FP32) or 512 (FP64), else
  * LGF_ERR_ARG.  The table must outlive the
@@ -158,6 +158,13 @@ int lgf_plan_method(const lgf_plan *p, double *ms_whole_box, double *ms_split);
  * the executions since then are not valid), LGF_OK otherwise.  Only the block-sparse
  * method's tensor-core kernels wait; lgf_conv_execute_host checks on its own. */
 lgf_status lgf_plan_check(lgf_plan *p, void *stream);
+
+/* Failure detection of the bounded device waits (the paper has no counterpart): runs the
+ * wait the tensor-core kernels use on an mbarrier that nothing arrives on, for `polls` polls
+ * (1..2^20), and returns LGF_ERR_TIMEOUT when it gives up, as a kernel whose dependency never
+ * completes reports through lgf_plan_check.  Nothing faults or hangs; the context stays usable.
+ * Allocates 4 bytes of device memory; synchronises `stream`. */
+lgf_status lgf_wait_probe(int polls, void *stream);
 
 /* Device bytes held by the plan (workspaces + spectra + lookups). */
 lgf_status lgf_plan_workspace_bytes(const lgf_plan *p, size_t *bytes);

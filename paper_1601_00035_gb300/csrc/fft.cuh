@@ -1,4 +1,4 @@
-// 1-D complex FFTs of length N = 2^k (16..1024) or 3 * 2^k (96, 192, 384) with
+// 1-D complex FFTs of length N = 2^k (16..1024) or 3 * 2^k (96, 192, 384, 768) with
 // the data held in registers, for batches of lines processed by one thread block.
 //
 // A line is transformed by G lanes (threads); lane j holds E = N / G elements.
@@ -459,6 +459,11 @@ template <>
 struct Plan<384> {
     static constexpr int G = 16, E = 24, S = 3;
     static constexpr int R[3] = {8, 6, 8};
+};
+template <>
+struct Plan<768> {
+    static constexpr int G = 32, E = 24, S = 3;
+    static constexpr int R[3] = {8, 12, 8};
 };
 template <>
 struct Plan<1024> {

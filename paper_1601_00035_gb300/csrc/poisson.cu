@@ -544,6 +544,10 @@ lgf_status launch_x_inv(const Geom &g, const cx<T> *in, T *dst, cudaStream_t s)
         case 256: { constexpr int NN = 256; CALL; } break;                                  \
         case 384: { constexpr int NN = 384; CALL; } break;                                  \
         case 512: { constexpr int NN = 512; CALL; } break;                                  \
+        case 768:                                                                           \
+            if constexpr (sizeof(T) == 4) { constexpr int NN = 768; CALL; }                 \
+            else { set_error("FP64 transforms are limited to N <= 512"); return LGF_ERR_ARG; } \
+            break;                                                                          \
         case 1024:                                                                          \
             if constexpr (sizeof(T) == 4) { constexpr int NN = 1024; CALL; }                \
             else { set_error("FP64 transforms are limited to N <= 512"); return LGF_ERR_ARG; } \
@@ -601,7 +605,7 @@ lgf_status poisson_prepare()
 }
 
 // supported FFT lengths, ascending: powers of two and 3 times a power of two
-static const int kLengths[] = {16, 32, 64, 96, 128, 192, 256, 384, 512, 1024};
+static const int kLengths[] = {16, 32, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
 
 bool poisson_supported_n(int n)
 {

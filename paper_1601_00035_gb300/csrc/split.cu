@@ -688,6 +688,20 @@ __global__ void __launch_bounds__(TC_THREADS) k_far_interp_tc(const float *__res
     pdl_trigger();
 }
 
+// The bounded wait of the tensor-core kernels, run on an mbarrier that nothing arrives on:
+// after `polls` polls the wait gives up and the kernel records it in *err (no fault, no trap).
+__global__ void k_wait_probe(int polls, int *err)
+{
+    __shared__ uint64_t mbar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(tc::smem_addr(&mbar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = tc::mbar_wait(tc::smem_addr(&mbar), 0, polls);
+    if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+}
+
 // ---------------------------------------------------------------------------
 // host helpers
 // ---------------------------------------------------------------------------
@@ -1138,3 +1152,29 @@ lgf_status run_split(lgf_plan *p, const float *src, float *dst, cudaStream_t s, 
 }
 
 }  // namespace lgf
+
+extern "C" lgf_status lgf_wait_probe(int polls, void *stream)
+{
+    lgf::clear_error();
+    LGF_CHECK_ARG(polls >= 1 && polls <= (1 << 20), "lgf_wait_probe: polls %d outside [1, 2^20]", polls);
+    cudaStream_t s = (cudaStream_t)stream;
+    int *d_err = nullptr, h = 0;
+    LGF_CUDA_TRY(cudaMalloc(&d_err, sizeof(int)));
+    cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+        lgf::k_wait_probe<<<1, 32, 0, s>>>(polls, d_err);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_err);
+    if (e != cudaSuccess) {
+        lgf::set_error("lgf_wait_probe: %s", cudaGetErrorString(e));
+        return LGF_ERR_CUDA;
+    }
+    if (h) {
+        lgf::set_error("bounded device wait gave up after %d polls", polls);
+        return LGF_ERR_TIMEOUT;
+    }
+    return LGF_OK;
+}

@@ -87,6 +87,7 @@ _SIGS = {
     "lgf_plan_method": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)]),
     "lgf_plan_check": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "lgf_wait_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p]),
     "lgf_conv_execute": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
                                         ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
     "lgf_conv_execute_f64": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
@@ -448,12 +449,18 @@ def measure_peak(kind: int, ms: float = 200.0, stream=None) -> float:
     return out.value
 
 
+def wait_probe(polls: int = 1000, stream=None):
+    """Run a bounded device wait that cannot complete (lgf_wait_probe): raises LGFError with
+    LGF_ERR_TIMEOUT when the wait gives up."""
+    _check(load().lgf_wait_probe(int(polls), _stream(stream)))
+
+
 def version() -> str:
     return load().lgf_version().decode()
 
 
 # FFT lengths the library supports, ascending (powers of two and 3 times a power of two)
-FFT_LENGTHS = (16, 32, 64, 96, 128, 192, 256, 384, 512, 1024)
+FFT_LENGTHS = (16, 32, 64, 96, 128, 192, 256, 384, 512, 768, 1024)
 
 
 def fft_length(need: int) -> int:

@@ -52,8 +52,8 @@ def test_required_max_offset():
     for e, n in ((40, 96), (80, 192), (160, 384), (200, 512)):
         c = np.array([[0, 0, 0], [e // 8 - 1, 0, 0]])
         assert lgf.required_max_offset(c, c, 8) == n // 2 - 1, e
-    assert [lgf.fft_length(v) for v in (1, 17, 65, 97, 129, 193, 257, 385, 513, 1025)] == \
-        [16, 32, 96, 128, 192, 256, 384, 512, 1024, 0]
+    assert [lgf.fft_length(v) for v in (1, 17, 65, 97, 129, 193, 257, 385, 513, 769, 1025)] == \
+        [16, 32, 96, 128, 192, 256, 384, 512, 768, 1024, 0]
 
 
 def test_size_rule_matches_the_library():

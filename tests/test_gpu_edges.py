@@ -206,3 +206,23 @@ def test_argument_errors():
     with pytest.raises(lgf.LGFError) as e:
         p.ifactor(x, torch.zeros_like(x))                   # wrong kind of plan
     assert e.value.status == lgf.LGF_ERR_STATE
+
+
+def test_length_768():
+    """FFT length 768 (3 * 256) along x: a target block 20 blocks (320 cells) from the
+    source, beside two near blocks; sampled against the per-point direct sum."""
+    lgf = built()
+    B = 16
+    rng = np.random.default_rng(768)
+    src_c = np.array([[0, 0, 0]], dtype=np.int32)
+    dst_c = np.array([[20, 0, 0], [0, 0, 0], [1, 1, 1]], dtype=np.int32)
+    f = rng.standard_normal((1, 1, B, B, B))
+    K = lgf.required_max_offset(src_c, dst_c, B)
+    assert K == 383
+    out = _solve(lgf, B, src_c, dst_c, f).reshape(-1)
+    pts = inputs.block_points(dst_c, B)
+    sel = rng.choice(len(pts), 192, replace=False)
+    ref = _reference(f, src_c, dst_c, B, pts[sel])
+    # one of the three target blocks lies 20 blocks away: stated bound 4e-6 (FP32)
+    err = rel_l2(out[sel], ref)
+    assert err < 4e-6, err

@@ -253,3 +253,25 @@ def test_split_thin_ring_sampled():
     ref = -O.direct_conv(O.lgf_cube(offs_max), sp[nz], v[nz], pts)
     err = rel_l2(block_values_at(out, dst_c, B, pts), ref)
     assert err < 1e-6, err
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """Failure detection without a fault: the tensor-core kernels' mbarrier wait, run on a
+    barrier nothing arrives on, gives up after its poll limit and the host reads
+    LGF_ERR_TIMEOUT; a split solve on the same context afterwards is still correct."""
+    lgf = built()
+    with pytest.raises(lgf.LGFError) as e:
+        lgf.wait_probe(1000)
+    assert e.value.status == lgf.LGF_ERR_TIMEOUT
+    B = 16
+    rng = np.random.default_rng(3)
+    src_c = np.array([[0, 0, 0], [1, 0, 0]], dtype=np.int32)
+    dst_c = np.array([[0, 0, 0], [1, 1, 0], [3, 0, 0]], dtype=np.int32)
+    f = rng.standard_normal((2, 1, B, B, B)).astype(np.float32)
+    _, plan = _plan(lgf, src_c, dst_c, far_precision=1)
+    d = torch.zeros((3, 1, B, B, B), device="cuda")
+    plan.execute([torch.from_numpy(f).cuda()], [d])
+    plan.check()
+    pts = inputs.block_points(dst_c, B)
+    ref = oracle_poisson_blocks(f, src_c, B, pts, lgf.required_max_offset(src_c, dst_c, B))
+    assert rel_l2(d.cpu().numpy().reshape(-1), ref) < 1e-5
