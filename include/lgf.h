@@ -139,7 +139,7 @@ void lgf_table_destroy(lgf_table *t);
  * zero-padded FFT grid of each distinct grid size (Hockney's free-space
  * embedding of eq. dpoisson_conv: exact up to FP32 rounding, no far-field
  * approximation), and allocates every workspace.  Per axis the FFT length is
- * the smallest of 16, 32, 64, 96, 128, 192, 256, 384, 512, 768, 1024 that is
+ * the smallest of 16, 32, 64, 96, 128, 192, 256, 288, 384, 432, 512, 768, 1024 that is
  * >= max(2 m + 2, 2 E), m the largest |target - source| offset and E the
  * source extent (points); at most 1024 (FP32) or 512 (FP64), else
  * LGF_ERR_ARG.  The table must outlive the

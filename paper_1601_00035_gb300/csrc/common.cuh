@@ -73,13 +73,13 @@ __host__ __device__ __forceinline__ cx<T> conj(cx<T> a) { return {a.x, -a.y}; }
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
-// Twiddle table w_3072^j = exp(-2 pi i j / 3072), j = 0..3071, computed on the
-// host in double precision and uploaded once per device (FP32 and FP64 copies);
-// every FFT length (a power of two up to 1024, or 3 times one) divides 3072.
+// Twiddle table w_M^j = exp(-2 pi i j / M), M = 27648 = 2^10 * 27, j < M, computed
+// on the host in double precision and uploaded once per device (FP32 and FP64
+// copies); every FFT length (2^k <= 1024, 3 * 2^k <= 768, 288, 432) divides M.
 const float2 *twiddle_table_f32();   // device pointer, current device
 const double2 *twiddle_table_f64();  // device pointer, current device
 lgf_status ensure_twiddles();
-constexpr int TW_MAX = 3072;
+constexpr int TW_MAX = 27648;
 
 // Programmatic dependent launch (sm_90 and later).  A kernel launched by
 // launch_pdl may begin while its predecessor on the stream is still draining:

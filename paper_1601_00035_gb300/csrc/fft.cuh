@@ -1,5 +1,7 @@
-// 1-D complex FFTs of length N = 2^k (16..1024) or 3 * 2^k (96, 192, 384, 768) with
-// the data held in registers, for batches of lines processed by one thread block.
+// 1-D complex FFTs of length N = 2^k (16..1024), 3 * 2^k (96, 192, 384, 768),
+// 288 = 9 * 2^5 or 432 = 27 * 2^4 with the data held in registers, for batches
+// of lines processed by one thread block.  In-register DFTs have lengths 2^k,
+// 3 * 2^k (dividing 48) or 9 * 2^k (dividing 36).
 //
 // A line is transformed by G lanes (threads); lane j holds E = N / G elements.
 // Algorithm: Stockham autosort, mixed radix R_0 .. R_{S-1} (product N).  In
@@ -400,12 +402,120 @@ __device__ __forceinline__ void dft_reg3(cx<T> *a)
     }
 }
 
+// cos(2 pi j / 36), j = 0..9 (the other quadrants by symmetry): the twiddles of
+// the in-register DFTs whose length has the factor 9 (R divides 36)
+__host__ __device__ constexpr double cos36_q(int j)
+{
+    constexpr double t[10] = {1.0, 0.98480775301220805937, 0.93969262078590838405, 0.86602540378443864676,
+                              0.76604444311897803520, 0.64278760968653932632, 0.5, 0.34202014332566873304,
+                              0.17364817766693034885, 0.0};
+    return t[j];
+}
+__host__ __device__ constexpr double cos36(int j)
+{
+    j = ((j % 36) + 36) % 36;
+    return j <= 9 ? cos36_q(j) : (j <= 18 ? -cos36_q(18 - j) : (j <= 27 ? -cos36_q(j - 18) : cos36_q(36 - j)));
+}
+__host__ __device__ constexpr double sin36(int j) { return cos36(j - 9); }
+
+// v times w_R^j (its conjugate for the inverse); R divides 36, j compile-time
+template <bool INV, int R, typename T>
+__device__ __forceinline__ cx<T> twiddle36(cx<T> v, int j)
+{
+    j %= R;
+    if (j == 0) return v;
+    if (2 * j == R) return {neg(v.x), neg(v.y)};
+    if (4 * j == R) return INV ? cx<T>{neg(v.y), v.x} : cx<T>{v.y, neg(v.x)};
+    if (4 * j == 3 * R) return INV ? cx<T>{v.y, neg(v.x)} : cx<T>{neg(v.y), v.x};
+    const int q = j * (36 / R);
+    const double sd = INV ? sin36(q) : -sin36(q);
+    const T c = cst<T>(cos36(q)), sn = cst<T>(sd), nsn = cst<T>(-sd);
+    return {fmaT(v.x, c, v.y * nsn), fmaT(v.x, sn, v.y * c)};
+}
+
+// length-3 DFT of (a, b, c) in place (forward: w_3 = exp(-2 pi i / 3))
+template <bool INV, typename T>
+__device__ __forceinline__ void dft3(cx<T> &a, cx<T> &b, cx<T> &c)
+{
+    const T nh = cst<T>(-0.5), s3 = cst<T>(0.86602540378443864676);
+    const cx<T> t1 = b + c;
+    const cx<T> t2 = {fmaT(nh, t1.x, a.x), fmaT(nh, t1.y, a.y)};
+    const cx<T> t3 = {s3 * (b.x - c.x), s3 * (b.y - c.y)};
+    a = a + t1;
+    if (!INV) {
+        b = {t2.x + t3.y, t2.y - t3.x};
+        c = {t2.x - t3.y, t2.y + t3.x};
+    } else {
+        b = {t2.x - t3.y, t2.y + t3.x};
+        c = {t2.x + t3.y, t2.y - t3.x};
+    }
+}
+
+// length-9 DFT, natural order in and out, as 3 x 3: with n = 3 n1 + n2 and
+// k = k1 + 3 k2, X[k] = sum_{n2} w_3^{n2 k2} w_9^{n2 k1} sum_{n1} w_3^{n1 k1} x[3 n1 + n2]
+template <bool INV, typename T>
+__device__ __forceinline__ void dft9(cx<T> (&b)[9])
+{
+    cx<T> z[3][3];  // z[n2][k1]
+#pragma unroll
+    for (int n2 = 0; n2 < 3; n2++) {
+        z[n2][0] = b[n2];
+        z[n2][1] = b[3 + n2];
+        z[n2][2] = b[6 + n2];
+        dft3<INV>(z[n2][0], z[n2][1], z[n2][2]);
+#pragma unroll
+        for (int k1 = 0; k1 < 3; k1++) z[n2][k1] = twiddle36<INV, 9, T>(z[n2][k1], n2 * k1);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 3; k1++) {
+        dft3<INV>(z[0][k1], z[1][k1], z[2][k1]);
+        b[k1] = z[0][k1];
+        b[k1 + 3] = z[1][k1];
+        b[k1 + 6] = z[2][k1];
+    }
+}
+
+// In-register DFT of length R = 9 M (M a power of two), natural order in and
+// out, structured as dft_reg3 with a length-9 DFT in place of the length-3 one:
+// the nine stride-9 subsequences are transformed by the radix-2 DFT of length M,
+// then X[k + m M] = sum_r w_R^{r k} Y_r[k] w_9^{r m}.  HALF: inputs R/2 .. R-1
+// are zero, which leaves the upper half of every subsequence zero (M >= 2).
+template <int R, bool INV, typename T, int OFF, bool HALF>
+__device__ __forceinline__ void dft_reg9(cx<T> *a)
+{
+    constexpr int M = R / 9;
+    static_assert(R == 9 * M && is_pow2(M) && 36 % R == 0, "R = 9 M, R divides 36");
+    cx<T> y[9][M];
+#pragma unroll
+    for (int r = 0; r < 9; r++)
+#pragma unroll
+        for (int n = 0; n < M; n++) y[r][n] = a[OFF + 9 * n + r];
+    if constexpr (M > 1) {
+#pragma unroll
+        for (int r = 0; r < 9; r++) {
+            bitrev_perm<M, T, 0>(y[r]);
+            levels<M, INV, T, 0, HALF>(y[r]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < M; k++) {
+        cx<T> b[9];
+#pragma unroll
+        for (int r = 0; r < 9; r++) b[r] = twiddle36<INV, R>(y[r][k], r * k);
+        dft9<INV>(b);
+#pragma unroll
+        for (int m = 0; m < 9; m++) a[OFF + k + m * M] = b[m];
+    }
+}
+
 template <int R, bool INV, typename T, int OFF, bool HALF = false>
 __device__ __forceinline__ void dft_reg(cx<T> *a)
 {
     if constexpr (is_pow2(R)) {
         bitrev_perm<R, T, OFF>(a);
         levels<R, INV, T, OFF, HALF>(a);
+    } else if constexpr (R % 9 == 0) {
+        dft_reg9<R, INV, T, OFF, HALF && R / 9 >= 2>(a);
     } else {
         dft_reg3<R, INV, T, OFF, HALF>(a);
     }
@@ -464,6 +574,19 @@ template <>
 struct Plan<768> {
     static constexpr int G = 32, E = 24, S = 3;
     static constexpr int R[3] = {8, 12, 8};
+};
+// lengths with the factor 9 or 27, two stages each: 288 = 12 x 24 (radices with one
+// factor 3) and 432 = 12 x 36 (radix 36 = 4 x 9 in registers); G = 12 is not a
+// power of two, only a divisor or multiple of every stage's span
+template <>
+struct Plan<288> {
+    static constexpr int G = 12, E = 24, S = 2;
+    static constexpr int R[2] = {12, 24};
+};
+template <>
+struct Plan<432> {
+    static constexpr int G = 12, E = 36, S = 2;
+    static constexpr int R[2] = {12, 36};
 };
 template <>
 struct Plan<1024> {

@@ -92,7 +92,7 @@ lgf_status build_spectrum(const double *d_octant, int K, const int N[3], float *
     lgf_status st = LGF_OK;
     std::vector<double> hct;
     if (cudaMalloc(&a, total * sizeof(double)) != cudaSuccess || cudaMalloc(&b, total * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&ct, 3 * TW_MAX * sizeof(double)) != cudaSuccess) {
+        cudaMalloc(&ct, (size_t)std::max(N[0], std::max(N[1], N[2])) * sizeof(double)) != cudaSuccess) {
         set_error("spectrum workspace allocation failed (%lld doubles)", (long long)total);
         st = LGF_ERR_OOM;
         goto done;

@@ -459,8 +459,9 @@ def version() -> str:
     return load().lgf_version().decode()
 
 
-# FFT lengths the library supports, ascending (powers of two and 3 times a power of two)
-FFT_LENGTHS = (16, 32, 64, 96, 128, 192, 256, 384, 512, 768, 1024)
+# FFT lengths the library supports, ascending (powers of two, 3 times a power of two,
+# 288 = 9 * 32 and 432 = 27 * 16)
+FFT_LENGTHS = (16, 32, 64, 96, 128, 192, 256, 288, 384, 432, 512, 768, 1024)
 
 
 def fft_length(need: int) -> int:

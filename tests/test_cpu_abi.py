@@ -47,13 +47,14 @@ def test_required_max_offset():
     assert lgf.required_max_offset(s, t, 16) == 95
     # far target: the offsets decide
     assert lgf.required_max_offset(np.array([[0, 0, 0]]), np.array([[30, 0, 0]]), 16) == 511
-    # lengths 3 * 2^k: a 40-point box needs 2 * 39 + 2 = 80 -> 96; 80 points -> 160 -> 192;
-    # 160 points -> 320 -> 384; 200 points -> 400 -> 512
-    for e, n in ((40, 96), (80, 192), (160, 384), (200, 512)):
+    # lengths 3 * 2^k, 9 * 2^5, 27 * 2^4: a 40-point box needs 2 * 39 + 2 = 80 -> 96;
+    # 80 points -> 160 -> 192; 136 points -> 272 -> 288; 160 points -> 320 -> 384;
+    # 200 points -> 400 -> 432; 232 points -> 464 -> 512
+    for e, n in ((40, 96), (80, 192), (136, 288), (160, 384), (200, 432), (232, 512)):
         c = np.array([[0, 0, 0], [e // 8 - 1, 0, 0]])
         assert lgf.required_max_offset(c, c, 8) == n // 2 - 1, e
-    assert [lgf.fft_length(v) for v in (1, 17, 65, 97, 129, 193, 257, 385, 513, 769, 1025)] == \
-        [16, 32, 96, 128, 192, 256, 384, 512, 768, 1024, 0]
+    assert [lgf.fft_length(v) for v in (1, 17, 65, 97, 129, 193, 257, 289, 385, 433, 513, 769, 1025)] == \
+        [16, 32, 96, 128, 192, 256, 288, 384, 432, 512, 768, 1024, 0]
 
 
 def test_size_rule_matches_the_library():

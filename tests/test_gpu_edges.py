@@ -7,7 +7,7 @@ made mostly (4e-6) or only (1e-4) of blocks far from every source the whole-box 
 transforms, which round at the near-field scale, reach the stated looser bounds.
 
 Lengths 16 and 32 run one thread per line; 64..512 two-stage transforms
-(512 with 32 elements per lane); 1024 a three-stage transform.  Far offsets use the oracle's per-point
+(512 with 32 elements per lane); 384, 432, 768 and 1024 three-stage transforms.  Far offsets use the oracle's per-point
 LGF evaluation (same Bessel-integral quadrature as its tables)."""
 import numpy as np
 import pytest
@@ -185,6 +185,53 @@ def test_full_box_3x2k(e):
     out = _solve(lgf, B, c, c, inputs.to_blocks(f, B, c))
     pts = inputs.block_points(c, B)
     sel = rng.choice(len(pts), 64, replace=False)
+    ref = O.direct_conv_box(O.lgf_cube(K), f, pts[sel])
+    got = out.reshape(-1)[sel]
+    assert rel_l2(got, ref) < 1e-6
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_lengths_9x2k(precision):
+    """FFT lengths 288 = 9 * 32 (x, two radix-12/24 stages, 12 lanes per line) and
+    432 = 27 * 16 (y, three stages 6/12/6, 18 lanes per line) at once: one source block and
+    targets 17 and 26 blocks away, in FP32 and FP64; sampled against the direct sum."""
+    lgf = built()
+    B = 8
+    rng = np.random.default_rng(432)
+    src_c = np.array([[0, 0, 0]], dtype=np.int32)
+    dst_c = np.array([[17, 0, 0], [0, 26, 0], [0, 0, 3], [5, 9, 1], [0, 0, 0]], dtype=np.int32)
+    f = rng.standard_normal((1, 1, B, B, B))
+    K = lgf.required_max_offset(src_c, dst_c, B)
+    assert K == 215 and lgf.fft_length(2 * (17 * B + 7) + 2) == 288
+    table = lgf.Table(lgf.LAPLACE7, max_offset=K)
+    plan = lgf.Plan(table, [lgf.Solve(B, 1, src_c, dst_c)], precision=precision)
+    dt = torch.float64 if precision else torch.float32
+    d_src = torch.from_numpy(f).to(dt).cuda()
+    d_dst = torch.zeros((len(dst_c), 1, B, B, B), dtype=dt, device="cuda")
+    (plan.execute_f64 if precision else plan.execute)([d_src], [d_dst])
+    out = d_dst.cpu().numpy().reshape(-1)
+    pts = inputs.block_points(dst_c, B)
+    sel = rng.choice(len(pts), 160, replace=False)
+    ref = _reference(f, src_c, dst_c, B, pts[sel])
+    # four of the five target blocks lie 3-26 blocks from the source: stated bound 4e-6 (FP32)
+    err = rel_l2(out[sel], ref)
+    assert err < (1e-10 if precision else 4e-6), err
+
+
+@pytest.mark.parametrize("e", [136, 200])
+def test_full_box_9x2k(e):
+    """A dense e^3 source on its own box: FFT length 288 (e = 136) or 432 (e = 200) on
+    every axis, so the packed z pass runs at 288; FP32, sampled against the direct sum."""
+    lgf = built()
+    B = 8
+    rng = np.random.default_rng(e)
+    f = rng.standard_normal((e, e, e))
+    c = inputs.block_grid(f.shape, B)
+    K = lgf.required_max_offset(c, c, B)
+    assert K == {136: 143, 200: 215}[e]
+    out = _solve(lgf, B, c, c, inputs.to_blocks(f, B, c))
+    pts = inputs.block_points(c, B)
+    sel = rng.choice(len(pts), 48, replace=False)
     ref = O.direct_conv_box(O.lgf_cube(K), f, pts[sel])
     got = out.reshape(-1)[sel]
     assert rel_l2(got, ref) < 1e-6
