@@ -48,17 +48,19 @@ def test_if_taps(alpha):
     assert np.max(np.abs(t.values() - ref) / ref) < 1e-14
 
 
-@pytest.mark.parametrize("alpha", [0.05, 0.2, 1.0])
-def test_ifactor_holed_set(alpha):
+@pytest.mark.parametrize("B,alpha", [(16, 0.05), (16, 0.2), (16, 1.0), (16, 0.002), (8, 0.05), (8, 0.002)])
+def test_ifactor_holed_set(B, alpha):
+    """A 3 x 3 x 3 block box with holes, 2 components, radii 4, 7, 9 and 15 (instantiated
+    radii 4, 8, 12 and 16), B = 16 and B = 8."""
     lgf = built()
-    B = 16
-    rng = np.random.default_rng(int(alpha * 100))
+    rng = np.random.default_rng(int(alpha * 1000) + B)
     box = np.array([[x, y, z] for z in range(3) for y in range(3) for x in range(3)], dtype=np.int32)
     keep = rng.random(len(box)) < 0.75
     keep[13] = True  # centre block
     blocks = box[keep]
     x = rng.standard_normal((len(blocks), 2, B, B, B)).astype(np.float32)
     t = lgf.Table(lgf.IFACTOR, alpha=alpha)
+    assert t.radius == {0.002: 4, 0.05: 7, 0.2: 9, 1.0: 15}[alpha]
     plan = lgf.Plan(t, [lgf.Solve(B, 2, blocks, None)])
     dx = torch.from_numpy(x).cuda()
     dy = torch.zeros_like(dx)
@@ -69,7 +71,7 @@ def test_ifactor_holed_set(alpha):
     pts = inputs.block_points(blocks, B)
     sub = rng.choice(len(pts), size=6000, replace=False)
     for c in range(2):
-        dense = inputs.from_blocks(x[:, c:c + 1], B, blocks, (48, 48, 48))[0]
+        dense = inputs.from_blocks(x[:, c:c + 1], B, blocks, (3 * B,) * 3)[0]
         ref = O.ifactor_direct(g, dense, pts[sub])
         got = y[:, c].reshape(-1)[sub]
         assert rel_l2(got, ref) < 1e-6
