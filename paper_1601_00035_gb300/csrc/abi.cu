@@ -152,18 +152,21 @@ lgf_status ensure_twiddles()
     }
     std::lock_guard<std::mutex> lk(g_tw_mu);
     if (g_tw.count(dev)) return LGF_OK;
-    std::vector<float2> hf(TW_MAX);
-    std::vector<double2> hd(TW_MAX);
-    for (int j = 0; j < TW_MAX; j++) {
-        const double a = -2.0 * 3.14159265358979323846 * (double)j / (double)TW_MAX;
+    // w_TW_MAX^j (j < TW_MAX), then w_TW_POW^j (j < TW_POW)
+    const int total = TW_MAX + TW_POW;
+    std::vector<float2> hf(total);
+    std::vector<double2> hd(total);
+    for (int j = 0; j < total; j++) {
+        const double a = j < TW_MAX ? -2.0 * 3.14159265358979323846 * (double)j / (double)TW_MAX
+                                    : -2.0 * 3.14159265358979323846 * (double)(j - TW_MAX) / (double)TW_POW;
         hd[j] = make_double2(std::cos(a), std::sin(a));
         hf[j] = make_float2((float)hd[j].x, (float)hd[j].y);
     }
     TwTables t;
-    LGF_CUDA_TRY(cudaMalloc(&t.f, TW_MAX * sizeof(float2)));
-    LGF_CUDA_TRY(cudaMalloc(&t.d, TW_MAX * sizeof(double2)));
-    LGF_CUDA_TRY(cudaMemcpy(t.f, hf.data(), TW_MAX * sizeof(float2), cudaMemcpyHostToDevice));
-    LGF_CUDA_TRY(cudaMemcpy(t.d, hd.data(), TW_MAX * sizeof(double2), cudaMemcpyHostToDevice));
+    LGF_CUDA_TRY(cudaMalloc(&t.f, total * sizeof(float2)));
+    LGF_CUDA_TRY(cudaMalloc(&t.d, total * sizeof(double2)));
+    LGF_CUDA_TRY(cudaMemcpy(t.f, hf.data(), total * sizeof(float2), cudaMemcpyHostToDevice));
+    LGF_CUDA_TRY(cudaMemcpy(t.d, hd.data(), total * sizeof(double2), cudaMemcpyHostToDevice));
     g_tw[dev] = t;
     return LGF_OK;
 }

@@ -76,10 +76,14 @@ inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 // Twiddle table w_M^j = exp(-2 pi i j / M), M = 27648 = 2^10 * 27, j < M, computed
 // on the host in double precision and uploaded once per device (FP32 and FP64
 // copies); every FFT length (2^k <= 1024, 3 * 2^k <= 768, 288, 432) divides M.
+// Behind it follow the powers of w_3072 (TW_POW entries), read by the lengths
+// 768 and 1024, whose per-block tables hold all N powers of w_N: a short stride
+// through the global table keeps those loads coalesced.
 const float2 *twiddle_table_f32();   // device pointer, current device
 const double2 *twiddle_table_f64();  // device pointer, current device
 lgf_status ensure_twiddles();
 constexpr int TW_MAX = 27648;
+constexpr int TW_POW = 3072;
 
 // Programmatic dependent launch (sm_90 and later).  A kernel launched by
 // launch_pdl may begin while its predecessor on the stream is still draining:

@@ -768,8 +768,9 @@ __host__ __device__ constexpr bool in_lower_half(int e)
     return (e % R) * (N / R) < N / 2;
 }
 
-// Fill the shared twiddle array (tw_size<N>() entries) from the TW_MAX-entry
-// global table of the same precision (float2 for T = float, double2 for double).
+// Fill the shared twiddle array (tw_size<N>() entries) from the global table of
+// the same precision (float2 for T = float, double2 for double): stage tables
+// from its w_TW_MAX part, the N powers of w_N (N > 512) from its w_TW_POW part.
 template <typename T>
 __device__ __forceinline__ cx<T> tw_global_at(const void *tw_global, int idx)
 {
@@ -807,7 +808,8 @@ __device__ __forceinline__ void load_twiddles(cx<T> *tw_s, const void *tw_global
         load_dir<N, false, T>(tw_s, tw_global);
         if constexpr (!tw_palindrome<N>()) load_dir<N, true, T>(tw_s, tw_global);
     } else {
-        for (int q = threadIdx.x; q < N; q += blockDim.x) tw_s[q] = tw_global_at<T>(tw_global, q * (TW_MAX / N));
+        static_assert(TW_POW % N == 0, "N divides the second twiddle table's length");
+        for (int q = threadIdx.x; q < N; q += blockDim.x) tw_s[q] = tw_global_at<T>(tw_global, TW_MAX + q * (TW_POW / N));
     }
 }
 
