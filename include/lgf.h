@@ -187,7 +187,9 @@ lgf_status lgf_conv_execute_f64(lgf_plan *p, const double *const *src, double *c
  * synchronises `stream` before returning.  Each unit copies its own
  * component slice in and out on its worker stream, so copies overlap the
  * other units' passes.  Host buffers should be pinned for full copy
- * bandwidth. */
+ * bandwidth.  With opts->use_graph and every buffer page-locked, the copies
+ * and passes are captured once per set of host pointers and replayed as one
+ * graph (pageable buffers take the launch-by-launch path). */
 lgf_status lgf_conv_execute_host(lgf_plan *p, const float *const *src, float *const *dst, void *stream);
 
 /* IF plan (table of kind LGF_KERNEL_IFACTOR, one solve): y = M E_Q(alpha) M x

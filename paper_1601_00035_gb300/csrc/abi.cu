@@ -108,6 +108,7 @@ void free_plan(lgf_plan *p)
     cudaFree(p->ifp.y1);
     cudaFree(p->ifp.y2);
     if (p->graph) cudaGraphExecDestroy(p->graph);
+    if (p->host_graph) cudaGraphExecDestroy(p->host_graph);
     if (p->rk) free_rk(p->rk);
     if (p->split) free_split(p->split);
     if (p->sub) free_plan(p->sub);
@@ -1045,7 +1046,59 @@ lgf_status lgf_conv_execute_host(lgf_plan *p, const float *const *src, float *co
         dd[i] = q.d_stage_dst;
     }
     const HostIO host{src, dst};
-    LGF_TRY(run_poisson(p, ds.data(), dd.data(), s, false, &host));
+    // page-locked host buffers (every one of them): the copies and passes are
+    // captured once per set of host pointers and replayed as one graph
+    bool pinned = p->use_graph && !p->prof.on;
+    for (size_t i = 0; pinned && i < p->solves.size(); i++) {
+        for (const void *h : {(const void *)src[i], (const void *)dst[i]}) {
+            cudaPointerAttributes at;
+            if (cudaPointerGetAttributes(&at, h) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+                cudaGetLastError();  // a pageable pointer may leave an error behind: clear it
+                pinned = false;
+            }
+        }
+    }
+    if (!pinned) {
+        LGF_TRY(run_poisson(p, ds.data(), dd.data(), s, false, &host));
+        LGF_CUDA_TRY(cudaStreamSynchronize(s));
+        return LGF_OK;
+    }
+    std::vector<const void *> key;
+    for (size_t i = 0; i < p->solves.size(); i++) {
+        key.push_back(src[i]);
+        key.push_back(dst[i]);
+    }
+    if (!p->host_graph || key != p->host_graph_key) {
+        if (p->host_graph) {
+            cudaGraphExecDestroy(p->host_graph);
+            p->host_graph = nullptr;
+        }
+        cudaStream_t cs;
+        LGF_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t gr = nullptr;
+        lgf_status st = LGF_OK;
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            set_error("stream capture failed to start");
+            st = LGF_ERR_CUDA;
+        } else {
+            st = run_poisson(p, ds.data(), dd.data(), cs, true, &host);
+            cudaError_t e = cudaStreamEndCapture(cs, &gr);
+            if (st == LGF_OK && e != cudaSuccess) {
+                set_error("stream capture failed: %s", cudaGetErrorString(e));
+                st = LGF_ERR_CUDA;
+            }
+            if (st == LGF_OK && cudaGraphInstantiate(&p->host_graph, gr, 0) != cudaSuccess) {
+                set_error("graph instantiation failed");
+                st = LGF_ERR_CUDA;
+                p->host_graph = nullptr;
+            }
+        }
+        if (gr) cudaGraphDestroy(gr);
+        cudaStreamDestroy(cs);
+        if (st != LGF_OK) return st;
+        p->host_graph_key = key;
+    }
+    LGF_CUDA_TRY(cudaGraphLaunch(p->host_graph, s));
     LGF_CUDA_TRY(cudaStreamSynchronize(s));
     return LGF_OK;
 }

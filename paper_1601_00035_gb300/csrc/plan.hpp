@@ -271,6 +271,9 @@ struct lgf_plan {
     int use_graph = 0;
     cudaGraphExec_t graph = nullptr;
     std::vector<const void *> graph_key;
+    // lgf_conv_execute_host with page-locked host buffers: copies and passes as one graph
+    cudaGraphExec_t host_graph = nullptr;
+    std::vector<const void *> host_graph_key;
     lgf::Profiler prof;
     lgf::RkPlan *rk = nullptr;  // kind == LGF_PLAN_RK
     int method = 0;                 // 0 whole-box FFT, 1 block-sparse split

@@ -153,6 +153,15 @@ def test_ring128_vector_sampled():
     host = np.zeros_like(out[0])
     plan_g.execute_host([np.ascontiguousarray(f, dtype=np.float32)], [host])
     assert np.array_equal(host, out[0])
+    # page-locked buffers: copies and passes replayed as one graph, re-captured
+    # when the host pointers change
+    h_src = torch.from_numpy(np.ascontiguousarray(f, dtype=np.float32)).pin_memory()
+    for _ in range(2):
+        h_dst = torch.full(out[0].shape, float("nan"), dtype=torch.float32).pin_memory()
+        plan_g.execute_host([h_src], [h_dst])
+        assert np.array_equal(h_dst.numpy(), out[0])
+        plan_g.execute_host([h_src], [h_dst])
+        assert np.array_equal(h_dst.numpy(), out[0])
     rng = np.random.default_rng(2)
     pts = rng.integers(0, 128, size=(2048, 3)).astype(np.int32)
     for c in range(3):
@@ -206,6 +215,15 @@ def test_vector_component_streams_bitwise():
     for a, b, c in zip(out, out_g, host_dst):
         assert np.array_equal(a, b)
         assert np.array_equal(a, c)
+    # a graph plan with page-locked buffers: the staggered units replayed as one graph
+    plan_g = lgf.Plan(lgf.Table(lgf.LAPLACE7, max_offset=max(lgf.required_max_offset(s.src_blocks, s.dst_blocks, B)
+                                                             for s in solves)), solves, use_graph=True)
+    h_src = [torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).pin_memory() for x in srcs]
+    h_dst = [torch.full(x.shape, float("nan"), dtype=torch.float32).pin_memory() for x in out]
+    for _ in range(2):
+        plan_g.execute_host(h_src, h_dst)
+        for a, c in zip(out, h_dst):
+            assert np.array_equal(a, c.numpy())
     for s, x, o in zip(solves, srcs, out):
         for c in range(s.ncomp):
             one = lgf.Solve(B, 1, s.src_blocks, s.dst_blocks, scale=-1.0)
