@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_f
     const int B = g.B;
     const int lB = g.lB, mB = B - 1;
     // the lookup table is fixed at plan time: read it before waiting
+    int mine = 0;  // whether this thread's lookups found a block
     for (int q = threadIdx.x; q < TL::LS * NBX; q += TL::threads) {
         const int ll = q / NBX, xb = q - ll * NBX;
         const int rr = 2 * (blockIdx.x * TL::LS + ll);
@@ -103,10 +104,24 @@ __global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_f
             b = __ldg(g.src_lut + ((zz >> lB) * g.nbS[1] + (yy >> lB)) * g.nbS[0] + xb);
         }
         lut_s[q] = b;
+        mine |= b >= 0;
     }
     pdl_trigger();
     pdl_wait();  // the previous pass (or the producer of src) is complete
-    __syncthreads();  // twiddles, lookups
+    // twiddles, lookups; a thread block whose rows meet no source block writes
+    // its zero rows without transforming them
+    if (!__syncthreads_or(mine)) {
+        constexpr int KXZ = N / 2 + 1;
+        for (int idx = threadIdx.x; idx < TL::LS * KXZ; idx += TL::threads) {
+            const int ll = idx / KXZ, k = idx - ll * KXZ;
+            const int rr = 2 * (blockIdx.x * TL::LS + ll);
+            if (rr >= nrows) continue;
+            const size_t row = ((size_t)c * nrows + rr) * KXZ;
+            out[row + k] = {(T)0, (T)0};
+            out[row + KXZ + k] = {(T)0, (T)0};
+        }
+        return;
+    }
     const int r0 = 2 * (blockIdx.x * TL::LS + l);
     const bool row_ok = r0 < nrows;
     const int z = row_ok ? r0 / g.Es[1] : 0, y = row_ok ? r0 - z * g.Es[1] : 0;
@@ -418,6 +433,7 @@ __global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_i
     const int nrows = g.Et[1] * g.Et[2];
     const int lB = g.lB;
     // the lookup table is fixed at plan time: read it before waiting
+    int mine = 0;  // whether this thread's lookups found a block
     for (int q = threadIdx.x; q < TL::LS * NBX; q += TL::threads) {
         const int ll = q / NBX, xb = q - ll * NBX;
         const int rr = 2 * (blockIdx.x * TL::LS + ll);
@@ -427,7 +443,10 @@ __global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_i
             b = __ldg(g.dst_lut + ((zz >> lB) * g.nbT[1] + (yy >> lB)) * g.nbT[0] + xb);
         }
         lut_d[q] = b;
+        mine |= b >= 0;
     }
+    // a thread block whose rows meet no target block has nothing to write
+    if (!__syncthreads_or(mine)) return;
     pdl_trigger();
     pdl_wait();  // the previous pass (or the producer of src) is complete
     const int r0 = 2 * (blockIdx.x * TL::LS + l);
