@@ -520,16 +520,18 @@ static lgf_status plan_poisson(lgf_plan *p, const lgf_table *t, const lgf_solve_
         return LGF_OK;
     }
     // Several independent units, one per (solve, component): each runs the five
-    // passes on its own worker stream (up to 8), so the passes of different
+    // passes on its own worker stream (up to 4), so the passes of different
     // units overlap (a memory-bound pass beside the compute-bound z pass).
     // Longest-first greedy assignment, the workspace size as the cost estimate.
+    // (64 ragged solves: 2, 3, 4, 5, 6, 8, 12, 16 streams took 2.13, 1.93, 1.92,
+    // 1.88, 1.97, 2.01, 2.09, 2.10 ms.)
     for (int i = 0; i < n_solves; i++) {
         const PoissonSolve &q = p->solves[i];
         for (int c = 0; c < q.g.ncomp; c++)
             p->units.push_back({i, c, 1, 0, q.elemsA / q.g.ncomp, q.elemsB / q.g.ncomp});
     }
     const int nu = (int)p->units.size();
-    const int nl = std::min(8, nu);
+    const int nl = std::min(4, nu);
     std::vector<int> order(nu);
     for (int i = 0; i < nu; i++) order[i] = i;
     std::sort(order.begin(), order.end(), [&](int a, int b) {
