@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "plan.hpp"
+#include "poisson_passes.hpp"
 
 namespace lgf {
 
@@ -107,6 +108,13 @@ void free_plan(lgf_plan *p)
     cudaFree(p->ifp.nbx);
     cudaFree(p->ifp.y1);
     cudaFree(p->ifp.y2);
+    for (auto &gr : p->groups)
+        for (auto &gl : gr.pass) {
+            cudaFree(gl.d_tasks);
+            cudaFree(gl.d_cta);
+        }
+    for (auto *w : p->unit_wa) cudaFree(w);
+    for (auto *w : p->unit_wb) cudaFree(w);
     if (p->graph) cudaGraphExecDestroy(p->graph);
     if (p->host_graph) cudaGraphExecDestroy(p->host_graph);
     if (p->rk) free_rk(p->rk);
@@ -374,6 +382,94 @@ void lgf_table_destroy(lgf_table *t)
     delete t;
 }
 
+// A plan with at least this many units runs grouped: one launch per (pass, length).
+constexpr int kGroupMinUnits = 8;
+
+// Grouped execution: the units with the same FFT grid form a group, whose pass
+// launches cover all its units through device task tables (thread blocks numbered
+// unit after unit).  Groups are assigned to up to four worker streams, largest
+// first; every unit gets its own workspaces.
+static lgf_status plan_grouped(lgf_plan *p, cudaStream_t s)
+{
+    p->grouped = true;
+    const int nu = (int)p->units.size();
+    p->unit_wa.assign(nu, nullptr);
+    p->unit_wb.assign(nu, nullptr);
+    for (int i = 0; i < nu; i++) {
+        LGF_TRY(dalloc(&p->unit_wa[i], p->units[i].elemsA, p->bytes));
+        LGF_TRY(dalloc(&p->unit_wb[i], p->units[i].elemsB, p->bytes));
+    }
+    std::map<std::vector<int>, int> by_grid;
+    std::vector<double> cost;
+    for (int i = 0; i < nu; i++) {
+        const Geom &g0 = p->solves[p->units[i].solve].g;
+        const std::vector<int> key = {g0.N[0], g0.N[1], g0.N[2]};
+        auto it = by_grid.find(key);
+        if (it == by_grid.end()) {
+            it = by_grid.emplace(key, (int)p->groups.size()).first;
+            p->groups.emplace_back();
+            cost.push_back(0.0);
+        }
+        p->groups[it->second].units.push_back(i);
+        cost[it->second] += (double)(p->units[i].elemsA + p->units[i].elemsB);
+    }
+    const int ng = (int)p->groups.size();
+    for (int gi = 0; gi < ng; gi++) {
+        lgf_plan::Group &gr = p->groups[gi];
+        for (int pass = 0; pass < 5; pass++) {
+            std::vector<GroupTask<float>> tasks;
+            std::vector<int> cta;
+            for (int i : gr.units) {
+                const auto &u = p->units[i];
+                Geom g = p->solves[u.solve].g;
+                g.c0 = u.c0;
+                g.nc = 1;
+                const int nt = poisson_tiles(pass, g);
+                LGF_CHECK_ARG(nt >= 0, "grouped plan: unsupported FFT length %d", g.N[pass_axis(pass)]);
+                GroupTask<float> t;
+                t.g = g;
+                t.wa = p->unit_wa[i];
+                t.wb = p->unit_wb[i];
+                t.solve = u.solve;
+                t.first = (int)cta.size();
+                cta.insert(cta.end(), nt, (int)tasks.size());
+                tasks.push_back(t);
+            }
+            lgf_plan::GroupLaunch &L = gr.pass[pass];
+            L.pass = pass;
+            L.n = p->solves[p->units[gr.units[0]].solve].g.N[pass_axis(pass)];
+            L.ncta = (int)cta.size();
+            L.d_tasks = nullptr;
+            L.d_cta = nullptr;
+            GroupTask<float> *dt = nullptr;
+            LGF_TRY(dalloc(&dt, tasks.size(), p->bytes));
+            L.d_tasks = dt;
+            LGF_TRY(upload(dt, tasks, s));
+            LGF_TRY(dalloc(&L.d_cta, cta.size(), p->bytes));
+            LGF_TRY(upload(L.d_cta, cta, s));
+        }
+    }
+    // largest group first onto the least loaded stream
+    const int nl = std::min(4, ng);
+    std::vector<int> order(ng);
+    for (int i = 0; i < ng; i++) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<double> load(nl, 0.0);
+    for (int gi : order) {
+        const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        p->groups[gi].lane = k;
+        load[k] += cost[gi];
+    }
+    p->lanes.assign(nl, nullptr);
+    p->lane_done.assign(nl, nullptr);
+    LGF_CUDA_TRY(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming));
+    for (int k = 0; k < nl; k++) {
+        LGF_CUDA_TRY(cudaStreamCreateWithFlags(&p->lanes[k], cudaStreamNonBlocking));
+        LGF_CUDA_TRY(cudaEventCreateWithFlags(&p->lane_done[k], cudaEventDisableTiming));
+    }
+    return LGF_OK;
+}
+
 static lgf_status plan_poisson(lgf_plan *p, const lgf_table *t, const lgf_solve_desc *solves, int n_solves, cudaStream_t s)
 {
     LGF_TRY(poisson_prepare());
@@ -531,6 +627,7 @@ static lgf_status plan_poisson(lgf_plan *p, const lgf_table *t, const lgf_solve_
             p->units.push_back({i, c, 1, 0, q.elemsA / q.g.ncomp, q.elemsB / q.g.ncomp});
     }
     const int nu = (int)p->units.size();
+    if (nu >= kGroupMinUnits && n_solves <= kGroupMaxSolves) return plan_grouped(p, s);
     const int nl = std::min(4, nu);
     std::vector<int> order(nu);
     for (int i = 0; i < nu; i++) order[i] = i;
@@ -905,6 +1002,48 @@ static lgf_status run_poisson(lgf_plan *p, const float *const *src, float *const
         if (host) LGF_TRY(copy_slice(dst[u.solve], host->dst[u.solve], q, q.ndst, u.c0, u.nc, false, st));
         return LGF_OK;
     };
+    if (p->grouped) {
+        SolvePtrs<float> ptrs;
+        for (size_t i = 0; i < p->solves.size(); i++) {
+            ptrs.src[i] = src[i];
+            ptrs.dst[i] = dst[i];
+        }
+        static const char *names[5] = {"x_fwd_gather_r2c", "y_fwd", "z_fwd_mul_inv", "y_inv", "x_inv_c2r_scatter"};
+        // one group on stream st: its units' copies in, five grouped launches, copies out
+        auto run_group = [&](const lgf_plan::Group &gr, cudaStream_t st, Profiler *pr) -> lgf_status {
+            if (host)
+                for (int i : gr.units) {
+                    const auto &u = p->units[i];
+                    const PoissonSolve &q = p->solves[u.solve];
+                    LGF_TRY(copy_slice((float *)src[u.solve], host->src[u.solve], q, q.nsrc, u.c0, u.nc, true, st));
+                }
+            for (const auto &gl : gr.pass) {
+                if (pr) pr->begin(st);
+                LGF_TRY(poisson_launch_grouped(gl.pass, gl.n, (const GroupTask<float> *)gl.d_tasks, gl.d_cta, gl.ncta,
+                                               ptrs, st));
+                if (pr) pr->end(names[gl.pass], st);
+            }
+            if (host)
+                for (int i : gr.units) {
+                    const auto &u = p->units[i];
+                    const PoissonSolve &q = p->solves[u.solve];
+                    LGF_TRY(copy_slice(dst[u.solve], host->dst[u.solve], q, q.ndst, u.c0, u.nc, false, st));
+                }
+            return LGF_OK;
+        };
+        if (prof && prof->on) {
+            for (const auto &gr : p->groups) LGF_TRY(run_group(gr, s, prof));
+            return LGF_OK;
+        }
+        LGF_CUDA_TRY(cudaEventRecord(p->fork, s));
+        for (size_t k = 0; k < p->lanes.size(); k++) LGF_CUDA_TRY(cudaStreamWaitEvent(p->lanes[k], p->fork, 0));
+        for (const auto &gr : p->groups) LGF_TRY(run_group(gr, p->lanes[gr.lane], nullptr));
+        for (size_t k = 0; k < p->lanes.size(); k++) {
+            LGF_CUDA_TRY(cudaEventRecord(p->lane_done[k], p->lanes[k]));
+            LGF_CUDA_TRY(cudaStreamWaitEvent(s, p->lane_done[k], 0));
+        }
+        return LGF_OK;
+    }
     if (p->lanes.empty()) {
         for (size_t i = 0; i < p->solves.size(); i++)
             LGF_TRY(run_unit({(int)i, 0, p->solves[i].g.ncomp, 0, 0, 0}, p->d_wsA, p->d_wsB, s, prof));

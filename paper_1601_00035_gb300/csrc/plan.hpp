@@ -263,6 +263,22 @@ struct lgf_plan {
     };
     std::vector<Unit> units;
     std::vector<cudaEvent_t> unit_mark;  // per unit: recorded after one of its passes (staggered start)
+    // grouped execution (many units): the units with the same FFT grid form a group
+    // whose five passes are five launches over device task tables; the groups run on
+    // the worker streams (lanes); every unit has its own workspaces
+    bool grouped = false;
+    std::vector<lgf::cx<float> *> unit_wa, unit_wb;
+    struct GroupLaunch {
+        int pass, n, ncta;
+        void *d_tasks;  // GroupTask<float>[]
+        int *d_cta;     // task of every thread block
+    };
+    struct Group {
+        int lane;
+        std::vector<int> units;
+        GroupLaunch pass[5];
+    };
+    std::vector<Group> groups;
     double *d_acc = nullptr;  // residual accumulators
     // IF
     int B = 0, ncomp = 0, nblk = 0, R = 0;

@@ -122,6 +122,28 @@ int poisson_pick_n(int need)
     return 0;
 }
 
+int poisson_tiles(int pass, const Geom &g)
+{
+    switch (g.N[pass_axis(pass)]) {
+#define LGF_TILES_CASE(n) \
+    case n: return PoissonPasses<n, float>::tiles(pass, g);
+        LGF_POISSON_LENGTHS_A(LGF_TILES_CASE)
+        LGF_POISSON_LENGTHS_B(LGF_TILES_CASE)
+        LGF_POISSON_LENGTHS_C(LGF_TILES_CASE)
+        LGF_POISSON_LENGTHS_D(LGF_TILES_CASE)
+#undef LGF_TILES_CASE
+        default: return -1;
+    }
+}
+
+lgf_status poisson_launch_grouped(int pass, int n, const GroupTask<float> *tasks, const int *cta_task, int ncta,
+                                  const SolvePtrs<float> &ptrs, cudaStream_t s)
+{
+    LGF_TRY(upload_all_tw());
+    LGF_DISPATCH_N(float, n, LGF_TRY((PoissonPasses<NN, float>::grouped(pass, tasks, cta_task, ncta, ptrs, s))));
+    return LGF_OK;
+}
+
 lgf_status poisson_launch(const Geom &g, const float *src, float *dst, cx<float> *wsA, cx<float> *wsB,
                           cudaStream_t s, Profiler *prof, cudaEvent_t mark, int mark_after)
 {

@@ -74,9 +74,10 @@ __device__ __forceinline__ int wrap_mod(int v)
 
 // ---------------------------------------------------------------------------
 // x forward: gather two source rows per complex line from the block list, R2C.
+// bx: this thread block's tile; c: workspace component (g.c0 + c in the source layout)
 template <int N, typename T>
-__global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_fwd(Geom g, const T *__restrict__ src,
-                                                                 cx<T> *__restrict__ out, const void *tw_g)
+__device__ __forceinline__ void x_fwd_body(const Geom &g, const T *__restrict__ src, cx<T> *__restrict__ out,
+                                           const void *tw_g, int bx, int c)
 {
     using TL = TileX<N, T>;
     constexpr int E = Plan<N>::E;
@@ -88,7 +89,6 @@ __global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_f
     __shared__ cx<T> tw[fft::tw_size<N>()];
     __shared__ int lut_s[TL::LS * NBX];
     fft::load_twiddles<N, T>(tw, tw_g);
-    const int c = blockIdx.y;  // workspace component; g.c0 + c in the source layout
     const int j = threadIdx.x % TL::G, l = threadIdx.x / TL::G;
     const int nrows = g.Es[1] * g.Es[2];
     const int B = g.B;
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_f
     int mine = 0;  // whether this thread's lookups found a block
     for (int q = threadIdx.x; q < TL::LS * NBX; q += TL::threads) {
         const int ll = q / NBX, xb = q - ll * NBX;
-        const int rr = 2 * (blockIdx.x * TL::LS + ll);
+        const int rr = 2 * (bx * TL::LS + ll);
         int b = -1;
         if (rr < nrows && xb < g.nbS[0]) {
             const int zz = rr / g.Es[1], yy = rr - zz * g.Es[1];
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_f
         constexpr int KXZ = N / 2 + 1;
         for (int idx = threadIdx.x; idx < TL::LS * KXZ; idx += TL::threads) {
             const int ll = idx / KXZ, k = idx - ll * KXZ;
-            const int rr = 2 * (blockIdx.x * TL::LS + ll);
+            const int rr = 2 * (bx * TL::LS + ll);
             if (rr >= nrows) continue;
             const size_t row = ((size_t)c * nrows + rr) * KXZ;
             out[row + k] = {(T)0, (T)0};
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_f
         }
         return;
     }
-    const int r0 = 2 * (blockIdx.x * TL::LS + l);
+    const int r0 = 2 * (bx * TL::LS + l);
     const bool row_ok = r0 < nrows;
     const int z = row_ok ? r0 / g.Es[1] : 0, y = row_ok ? r0 - z * g.Es[1] : 0;
     const int in_blk = (((z & mB) << lB) + (y & mB)) << lB;
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_f
     constexpr int KX = N / 2 + 1;
     for (int idx = threadIdx.x; idx < TL::LS * KX; idx += TL::threads) {
         const int ll = idx / KX, k = idx - ll * KX;
-        const int rr = 2 * (blockIdx.x * TL::LS + ll);
+        const int rr = 2 * (bx * TL::LS + ll);
         if (rr >= nrows) continue;
         const cx<T> zk = buf[sm.at(k, ll)];
         const cx<T> zn = buf[sm.at(k == 0 ? 0 : N - k, ll)];
@@ -160,6 +160,12 @@ __global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_f
         out[row + k] = {h * (zk.x + zn.x), h * (zk.y - zn.y)};
         out[row + KX + k] = {h * (zk.y + zn.y), -h * (zk.x - zn.x)};
     }
+}
+template <int N, typename T>
+__global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_fwd(Geom g, const T *__restrict__ src,
+                                                                 cx<T> *__restrict__ out, const void *tw_g)
+{
+    x_fwd_body<N, T>(g, src, out, tw_g, blockIdx.x, blockIdx.y);
 }
 
 // y forward (MODE 0), z forward + spectral multiply + z inverse (MODE 1),
@@ -181,8 +187,8 @@ __host__ __device__ __forceinline__ int line_planes(const Geom &g)
 }
 
 template <int N, int MODE, typename T>
-__global__ void __launch_bounds__(TileY<N, T>::threads, TileY<N, T>::minb(MODE))
-    k_line(Geom g, const cx<T> *__restrict__ in, cx<T> *__restrict__ out, const void *tw_g)
+__device__ __forceinline__ void line_body(const Geom &g, const cx<T> *__restrict__ in, cx<T> *__restrict__ out,
+                                          const void *tw_g, int bx, int c)
 {
     using TL = TileY<N, T>;
     constexpr int E = Plan<N>::E;
@@ -197,9 +203,8 @@ __global__ void __launch_bounds__(TileY<N, T>::threads, TileY<N, T>::minb(MODE))
     fft::load_twiddles<N, T>(tw, tw_g);
     const int KX = g.KX;
     const int l = threadIdx.x % TL::LS, j = threadIdx.x / TL::LS;
-    const int i = blockIdx.x * TL::LS + l;  // line p * KX + kx
+    const int i = bx * TL::LS + l;  // line p * KX + kx
     const bool ok = i < KX * line_planes<MODE>(g);
-    const int c = blockIdx.y;
     const int Ny = g.N[1];
     pdl_trigger();
     if constexpr (SLAB) {
@@ -303,6 +308,12 @@ __global__ void __launch_bounds__(TileY<N, T>::threads, TileY<N, T>::minb(MODE))
         }
     }
 }
+template <int N, int MODE, typename T>
+__global__ void __launch_bounds__(TileY<N, T>::threads, TileY<N, T>::minb(MODE))
+    k_line(Geom g, const cx<T> *__restrict__ in, cx<T> *__restrict__ out, const void *tw_g)
+{
+    line_body<N, MODE, T>(g, in, out, tw_g, blockIdx.x, blockIdx.y);
+}
 
 // z pass on line pairs (FP32, N = 128, 256 with 16 elements per lane and
 // N = 384 with 24): lanes of a packed value carry lines 2q and
@@ -324,8 +335,8 @@ struct TileZ2 {
 };
 
 template <int N>
-__global__ void __launch_bounds__(TileZ2<N>::threads, TileZ2<N>::minb)
-    k_zmid2(Geom g, const cx<float> *__restrict__ in, cx<float> *__restrict__ out, const void *tw_g)
+__device__ __forceinline__ void zmid2_body(const Geom &g, const cx<float> *__restrict__ in,
+                                           cx<float> *__restrict__ out, const void *tw_g, int bx, int c)
 {
     using TL = TileZ2<N>;
     using P = fft::f32x2;
@@ -342,10 +353,9 @@ __global__ void __launch_bounds__(TileZ2<N>::threads, TileZ2<N>::minb)
     fft::load_twiddles<N, P>(tw, tw_g);
     const int KX = g.KX, Ny = g.N[1];
     const int l = threadIdx.x % TL::LS, j = threadIdx.x / TL::LS;
-    const int q = blockIdx.x * TL::LS + l;  // lines 2q, 2q+1 (numbered as in k_line)
+    const int q = bx * TL::LS + l;  // lines 2q, 2q+1 (numbered as in k_line)
     const int half = KX * Ny / 2;           // KX * Ny is even (Ny a power of two)
     const bool ok = q < half;
-    const int c = blockIdx.y;
     pdl_trigger();
     if (ok) {
         // fixed at plan time: read before waiting on the previous pass
@@ -410,12 +420,19 @@ __global__ void __launch_bounds__(TileZ2<N>::threads, TileZ2<N>::minb)
         }
     }
 }
+template <int N>
+__global__ void __launch_bounds__(TileZ2<N>::threads, TileZ2<N>::minb)
+    k_zmid2(Geom g, const cx<float> *__restrict__ in, cx<float> *__restrict__ out, const void *tw_g)
+{
+    zmid2_body<N>(g, in, out, tw_g, blockIdx.x, blockIdx.y);
+}
 
 // x inverse: two target rows per complex line (Z = A + i B with Hermitian
 // extension), C2R, scatter into the target block list.
+// bx: this thread block's tile; c: workspace component (g.c0 + c in the target layout)
 template <int N, typename T>
-__global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_inv(Geom g, const cx<T> *__restrict__ in,
-                                                                 T *__restrict__ dst, const void *tw_g)
+__device__ __forceinline__ void x_inv_body(const Geom &g, const cx<T> *__restrict__ in, T *__restrict__ dst,
+                                           const void *tw_g, int bx, int c)
 {
     using TL = TileX<N, T>;
     constexpr int E = Plan<N>::E;
@@ -428,7 +445,6 @@ __global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_i
     __shared__ int lut_d[TL::LS * NBX];
     fft::load_twiddles<N, T>(tw, tw_g);
     constexpr int KX = N / 2 + 1;
-    const int c = blockIdx.y;  // workspace component; g.c0 + c in the target layout
     const int j = threadIdx.x % TL::G, l = threadIdx.x / TL::G;
     const int nrows = g.Et[1] * g.Et[2];
     const int lB = g.lB;
@@ -436,7 +452,7 @@ __global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_i
     int mine = 0;  // whether this thread's lookups found a block
     for (int q = threadIdx.x; q < TL::LS * NBX; q += TL::threads) {
         const int ll = q / NBX, xb = q - ll * NBX;
-        const int rr = 2 * (blockIdx.x * TL::LS + ll);
+        const int rr = 2 * (bx * TL::LS + ll);
         int b = -1;
         if (rr < nrows && xb < g.nbT[0]) {
             const int zz = rr / g.Et[1], yy = rr - zz * g.Et[1];
@@ -449,7 +465,7 @@ __global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_i
     if (!__syncthreads_or(mine)) return;
     pdl_trigger();
     pdl_wait();  // the previous pass (or the producer of src) is complete
-    const int r0 = 2 * (blockIdx.x * TL::LS + l);
+    const int r0 = 2 * (bx * TL::LS + l);
     const bool row_ok = r0 < nrows;
     const size_t row = ((size_t)c * nrows + (row_ok ? r0 : 0)) * KX;
     cx<T> v[E];
@@ -491,6 +507,12 @@ __global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_i
             }
         }
     }
+}
+template <int N, typename T>
+__global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb) k_x_inv(Geom g, const cx<T> *__restrict__ in,
+                                                                 T *__restrict__ dst, const void *tw_g)
+{
+    x_inv_body<N, T>(g, in, dst, tw_g, blockIdx.x, blockIdx.y);
 }
 
 template <typename T>
@@ -540,7 +562,89 @@ lgf_status launch_x_inv(const Geom &g, const cx<T> *in, T *dst, cudaStream_t s)
     return LGF_OK;
 }
 
+// Grouped launches (poisson_passes.hpp): the thread block finds its task, then runs
+// the same body on that unit's geometry and buffers.
+template <int N, typename T>
+__global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb)
+    k_x_fwd_grp(const GroupTask<T> *__restrict__ tasks, const int *__restrict__ cta_task, SolvePtrs<T> ptrs,
+                const void *tw_g)
+{
+    const GroupTask<T> &t = tasks[__ldg(cta_task + blockIdx.x)];
+    const Geom g = t.g;
+    x_fwd_body<N, T>(g, ptrs.src[t.solve], t.wa, tw_g, blockIdx.x - t.first, 0);
+}
+template <int N, int MODE, typename T>
+__global__ void __launch_bounds__(TileY<N, T>::threads, TileY<N, T>::minb(MODE))
+    k_line_grp(const GroupTask<T> *__restrict__ tasks, const int *__restrict__ cta_task, const void *tw_g)
+{
+    const GroupTask<T> &t = tasks[__ldg(cta_task + blockIdx.x)];
+    const Geom g = t.g;
+    // y forward wa -> wb, z wb -> wa, y inverse wa -> wb
+    line_body<N, MODE, T>(g, MODE == 1 ? t.wb : t.wa, MODE == 1 ? t.wa : t.wb, tw_g, blockIdx.x - t.first, 0);
+}
+template <int N>
+__global__ void __launch_bounds__(TileZ2<N>::threads, TileZ2<N>::minb)
+    k_zmid2_grp(const GroupTask<float> *__restrict__ tasks, const int *__restrict__ cta_task, const void *tw_g)
+{
+    const GroupTask<float> &t = tasks[__ldg(cta_task + blockIdx.x)];
+    const Geom g = t.g;
+    zmid2_body<N>(g, t.wb, t.wa, tw_g, blockIdx.x - t.first, 0);
+}
+template <int N, typename T>
+__global__ void __launch_bounds__(TileX<N, T>::threads, TileX<N, T>::minb)
+    k_x_inv_grp(const GroupTask<T> *__restrict__ tasks, const int *__restrict__ cta_task, SolvePtrs<T> ptrs,
+                const void *tw_g)
+{
+    const GroupTask<T> &t = tasks[__ldg(cta_task + blockIdx.x)];
+    const Geom g = t.g;
+    x_inv_body<N, T>(g, t.wb, ptrs.dst[t.solve], tw_g, blockIdx.x - t.first, 0);
+}
+
 }  // namespace
+
+template <int N, typename T>
+int PoissonPasses<N, T>::tiles(int pass, const Geom &g)
+{
+    switch (pass) {
+        case 0: return ceil_div(g.Es[1] * g.Es[2] / 2, TileX<N, T>::LS);
+        case 1: return ceil_div((long long)g.KX * g.Es[2], TileY<N, T>::LS);
+        case 2:
+            if constexpr (use_zmid2<N, T>()) return ceil_div((long long)g.KX * g.N[1] / 2, TileZ2<N>::LS);
+            else return ceil_div((long long)g.KX * g.N[1], TileY<N, T>::LS);
+        case 3: return ceil_div((long long)g.KX * g.Et[2], TileY<N, T>::LS);
+        default: return ceil_div(g.Et[1] * g.Et[2] / 2, TileX<N, T>::LS);
+    }
+}
+
+template <int N, typename T>
+lgf_status PoissonPasses<N, T>::grouped(int pass, const GroupTask<T> *tasks, const int *cta_task, int ncta,
+                                        const SolvePtrs<T> &ptrs, cudaStream_t s)
+{
+    const void *tw = tw_table<T>();
+    switch (pass) {
+        case 0:
+            LGF_CUDA_TRY(launch_pdl(k_x_fwd_grp<N, T>, dim3(ncta), dim3(TileX<N, T>::threads), s, tasks, cta_task,
+                                    ptrs, tw));
+            break;
+        case 1:
+            LGF_CUDA_TRY(launch_pdl(k_line_grp<N, 0, T>, dim3(ncta), dim3(TileY<N, T>::threads), s, tasks, cta_task, tw));
+            break;
+        case 2:
+            if constexpr (use_zmid2<N, T>())
+                LGF_CUDA_TRY(launch_pdl(k_zmid2_grp<N>, dim3(ncta), dim3(TileZ2<N>::threads), s, tasks, cta_task, tw));
+            else
+                LGF_CUDA_TRY(
+                    launch_pdl(k_line_grp<N, 1, T>, dim3(ncta), dim3(TileY<N, T>::threads), s, tasks, cta_task, tw));
+            break;
+        case 3:
+            LGF_CUDA_TRY(launch_pdl(k_line_grp<N, 2, T>, dim3(ncta), dim3(TileY<N, T>::threads), s, tasks, cta_task, tw));
+            break;
+        default:
+            LGF_CUDA_TRY(launch_pdl(k_x_inv_grp<N, T>, dim3(ncta), dim3(TileX<N, T>::threads), s, tasks, cta_task,
+                                    ptrs, tw));
+    }
+    return LGF_OK;
+}
 
 template <int N, typename T>
 lgf_status PoissonPasses<N, T>::x_fwd(const Geom &g, const T *src, cx<T> *out, cudaStream_t s)

@@ -8,8 +8,30 @@
 
 namespace lgf {
 
+// Grouped execution of a plan with many units (solve, component): one launch per
+// (pass, FFT length of that pass's axis) covers every unit with that length.
+// Thread block b of a grouped launch runs tile b - first of task cta_task[b].
+constexpr int kGroupMaxSolves = 128;  // solves of a plan that runs grouped
+template <typename T>
+struct GroupTask {
+    Geom g;          // the unit's geometry (c0 = its component, nc = 1)
+    cx<T> *wa, *wb;  // the unit's two workspaces
+    int solve;       // index of the unit's buffers in SolvePtrs
+    int first;       // first thread block of this task in its launch
+};
+template <typename T>
+struct SolvePtrs {  // the buffers of one execution (kernel parameter)
+    const T *src[kGroupMaxSolves];
+    T *dst[kGroupMaxSolves];
+};
+// pass index: 0 x forward, 1 y forward, 2 z, 3 y inverse, 4 x inverse; its axis
+constexpr int pass_axis(int pass) { return pass == 0 || pass == 4 ? 0 : (pass == 2 ? 2 : 1); }
+
 template <int N, typename T>
 struct PoissonPasses {
+    static int tiles(int pass, const Geom &g);  // thread blocks of one unit's pass
+    static lgf_status grouped(int pass, const GroupTask<T> *tasks, const int *cta_task, int ncta,
+                              const SolvePtrs<T> &ptrs, cudaStream_t s);
     static lgf_status x_fwd(const Geom &g, const T *src, cx<T> *out, cudaStream_t s);     // gather, R2C in x
     static lgf_status y_fwd(const Geom &g, const cx<T> *in, cx<T> *out, cudaStream_t s);  // forward in y
     static lgf_status z_mid(const Geom &g, const cx<T> *in, cx<T> *out, cudaStream_t s);  // z: fwd, multiply, inv
@@ -23,6 +45,11 @@ cudaError_t poisson_tw_upload_a();
 cudaError_t poisson_tw_upload_b();
 cudaError_t poisson_tw_upload_c();
 cudaError_t poisson_tw_upload_d();
+
+// thread blocks of a unit's pass (-1: unsupported length); one grouped launch (poisson.cu)
+int poisson_tiles(int pass, const Geom &g);
+lgf_status poisson_launch_grouped(int pass, int n, const GroupTask<float> *tasks, const int *cta_task, int ncta,
+                                  const SolvePtrs<float> &ptrs, cudaStream_t s);
 
 #define LGF_POISSON_LENGTHS_A(X) X(16) X(32) X(64) X(96) X(128)
 #define LGF_POISSON_LENGTHS_B(X) X(192) X(256) X(288)
