@@ -92,12 +92,13 @@ lgf_status rk_project(RkPlan *r, Profiler &pr, const float *rv, const float *g, 
                       cudaStream_t s)
 {
     float *sx = r->work + 8 * r->vec;  // G^T r on xsoln cells
-    float *ss = sx + r->scal_x;        // restricted to supp
-    const int B3 = r->B * r->B * r->B;
     LGF_TRY(timed(pr, "op_div_t", s, [&] { return op_launch(2, r->B, r->n_x, r->d_nbr27, nullptr, rv, sx, r->dx, 1.0, nullptr, s); }));
-    LGF_TRY(timed(pr, "gather_supp", s, [&] { return gather_launch(sx, ss, r->d_supp_idx, r->n_soln, B3, s); }));
-    const float *srcs[1] = {ss};
-    float *dsts[1] = {sx};  // d^ overwrites G^T r on xsoln
+    // The D_supp blocks are the first n_soln blocks of D_xsoln, so the xsoln array is
+    // the solve's source array as it stands (M^supp: the plan reads only those blocks).
+    // d^ overwrites G^T r: the whole-box passes read their source only in the first
+    // pass and write their result only in the last, which starts after it has completed.
+    const float *srcs[1] = {sx};
+    float *dsts[1] = {sx};
     LGF_TRY(lgf_conv_execute(r->poisson, srcs, dsts, s));
     LGF_TRY(timed(pr, "grad_combine", s, [&] {
         return grad_combine_launch(r->B, r->n_x, r->d_nbr27, sx, rv, g, out1, out2, c2, r->dx, s);
@@ -463,13 +464,13 @@ lgf_status lgf_rk_step(lgf_plan *p, const float *u_in, float *u_out, const doubl
 }  // extern "C"
 
 namespace lgf {
-// u_out = M^xsoln C^T M^xsoln (-M^xsoln L^{-1} M^supp w), w on D_supp in the plan's staging buffer
-lgf_status rk_vor2vel_supp(lgf_plan *p, float *u_out, cudaStream_t s)
+// u_out = M^xsoln C^T M^xsoln (-M^xsoln L^{-1} M^supp w); w: a 3-component array whose first
+// n_soln blocks are the D_supp blocks (a D_xsoln field, or the plan's D_supp staging buffer)
+lgf_status rk_vor2vel_supp(lgf_plan *p, const float *w, float *u_out, cudaStream_t s)
 {
     RkPlan *r = p->rk;
     float *ax = r->work + r->vec;
-    float *ws = r->work + 8 * r->vec + r->scal_x + r->scal_s;
-    const float *srcs[1] = {ws};
+    const float *srcs[1] = {w};
     float *dsts[1] = {ax};
     LGF_TRY(lgf_conv_execute(r->poisson3, srcs, dsts, s));
     return timed(p->prof, "op_curl_t", s,
@@ -515,8 +516,7 @@ static lgf_status rk_step_vorticity_launches(lgf_plan *p, const float *w_in, flo
     for (int i = 1; i <= 3; i++) {
         const double aii = r->at[i][i];
         // velocity of the previous stage value (eq. vel_vor, source on D_supp)
-        LGF_TRY(timed(pr, "gather_supp", s, [&] { return gather_launch(wprev, ws, r->d_supp_idx, r->n_soln, 3 * B3, s); }));
-        LGF_TRY(rk_vor2vel_supp(p, u, s));
+        LGF_TRY(rk_vor2vel_supp(p, wprev, u, s));
         // g = -a~_ii dt M^soln C M^soln N~(M^xsoln (u + u_inf)); the D_soln blocks come first
         LGF_TRY(timed(pr, "op_nonlinear", s, [&] {
             return op_launch(4, B, r->n_x, r->d_nbr27, r->d_soln_keep, u, f, r->dx, -aii * dt, uinf, s);
@@ -566,15 +566,11 @@ lgf_status lgf_rk_refresh(lgf_plan *p, const float *u_in, float *u_out, void *st
     LGF_CHECK_ARG(p->kind == LGF_PLAN_RK, "lgf_rk_refresh: needs a plan from lgf_rk_plan");
     RkPlan *r = p->rk;
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t V = r->vec;
-    float *wx = r->work;                                         // w on D_xsoln
-    float *ws = r->work + 8 * V + r->scal_x + r->scal_s;         // w on D_supp
-    const int B3 = r->B * r->B * r->B;
+    float *wx = r->work;  // w on D_xsoln (its first n_soln blocks: D_supp)
     Profiler &pr = p->prof;
     // w = M^xsoln C M^xsoln u; a = -M^xsoln L^{-1} M^supp w; u' = M^xsoln C^T M^xsoln a (eq. vel_refresh)
     LGF_TRY(timed(pr, "op_curl", s, [&] { return op_launch(0, r->B, r->n_x, r->d_nbr27, nullptr, u_in, wx, r->dx, 1.0, nullptr, s); }));
-    LGF_TRY(timed(pr, "gather_supp", s, [&] { return gather_launch(wx, ws, r->d_supp_idx, r->n_soln, 3 * B3, s); }));
-    return rk_vor2vel_supp(p, u_out, s);
+    return rk_vor2vel_supp(p, wx, u_out, s);
 }
 
 int lgf_rk_qmax(const lgf_plan *p, double eps)
@@ -698,7 +694,7 @@ lgf_status lgf_rk_transfer(lgf_plan *from, const float *u_from, lgf_plan *to, fl
     // the old mask edge's spurious vortex sheet must not enter the new D_supp
     LGF_TRY(zero_rim_launch(a->B, a->n_x, a->d_nbr27, w_old, s));
     LGF_TRY(gather_launch(w_old, ws_new, b->d_tidx, b->n_soln, 3 * B3, s));
-    LGF_TRY(rk_vor2vel_supp(to, u_to, s));
+    LGF_TRY(rk_vor2vel_supp(to, ws_new, u_to, s));
     // the host index array must outlive the copy
     LGF_CUDA_TRY(cudaStreamSynchronize(s));
     return LGF_OK;
