@@ -76,9 +76,9 @@ inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 // Twiddle table w_M^j = exp(-2 pi i j / M), M = 27648 = 2^10 * 27, j < M, computed
 // on the host in double precision and uploaded once per device (FP32 and FP64
 // copies); every FFT length (2^k <= 1024, 3 * 2^k <= 768, 288, 432) divides M.
-// Behind it follow the powers of w_3072 (TW_POW entries), read by the lengths
-// 768 and 1024, whose per-block tables hold all N powers of w_N: a short stride
-// through the global table keeps those loads coalesced.
+// Behind it follow the powers of w_3072 (TW_POW entries), read by every length
+// that divides 3072 (all but 288 and 432): a few KB that stay cached across
+// thread blocks, and short strides that keep the loads coalesced.
 const float2 *twiddle_table_f32();   // device pointer, current device
 const double2 *twiddle_table_f64();  // device pointer, current device
 lgf_status ensure_twiddles();

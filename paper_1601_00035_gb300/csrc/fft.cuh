@@ -769,8 +769,8 @@ __host__ __device__ constexpr bool in_lower_half(int e)
 }
 
 // Fill the shared twiddle array (tw_size<N>() entries) from the global table of
-// the same precision (float2 for T = float, double2 for double): stage tables
-// from its w_TW_MAX part, the N powers of w_N (N > 512) from its w_TW_POW part.
+// the same precision (float2 for T = float, double2 for double): from its
+// w_TW_POW part for every length dividing TW_POW, else from its w_TW_MAX part.
 template <typename T>
 __device__ __forceinline__ cx<T> tw_global_at(const void *tw_global, int idx)
 {
@@ -790,12 +790,15 @@ __device__ __forceinline__ void load_dir(cx<T> *tw_s, const void *tw_global)
 {
     if constexpr (s < Plan<N>::S) {
         static_assert(TW_MAX % N == 0, "N divides the twiddle table length");
-        constexpr int SC = TW_MAX / N;
+        // lengths dividing TW_POW read the short w_TW_POW part (a few KB, cached across
+        // thread blocks); 288 and 432 the w_TW_MAX part
+        constexpr bool SHORT = TW_POW % N == 0;
+        constexpr int M = SHORT ? TW_POW : TW_MAX, BASE = SHORT ? TW_MAX : 0, SC = M / N;
         constexpr int R = radix<N, INV>(s), L = span<N, INV>(s), STEP = N / (R * L);
         cx<T> *ts = tw_s + tw_base<N>(INV) + tw_stage_off<N, INV>(s);
         for (int q = threadIdx.x; q < L * R; q += blockDim.x) {
             const int m = q / L, k = q - m * L;
-            ts[q] = tw_global_at<T>(tw_global, (m * k * STEP * SC) % TW_MAX);
+            ts[q] = tw_global_at<T>(tw_global, BASE + (m * k * STEP * SC) % M);
         }
         load_dir<N, INV, T, s + 1>(tw_s, tw_global);
     }
