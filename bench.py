@@ -644,6 +644,44 @@ def aux_workload(name, lgf, torch):
                         + {0: "whole-box FFT convolution", 1: "block-sparse split solve"}[method]
                         + (", far field on the tensor cores (tcgen05, TF32 split)" if name.endswith("_tc") else ""),
             "supp_blocks": int(len(supp)), "xsoln_blocks": int(len(xs)), "points": "D_xsoln points per solve"}, [t]
+    if name == "rk_thinring":
+        # one Scheme-A IF-HERK step of the delta/R0 = 0.0125 ring (Sec. 6: R0 = 400 cells, core
+        # 5 cells, Re = 500, u_inf as for the 256^3 ring), its Poisson solves by the block-sparse
+        # split (the box, ~750 cells across, is beyond the whole-box FFT lengths); dt is the 256^3
+        # ring's dt Gamma/R0^2 scaled by the cell size and the core radius
+        import math
+        R0c, dcells = 400.0, 5.0
+        dx = 1.0 / R0c
+        dt, re = 0.01721 * (50.0 / R0c) * ((dcells / R0c) / 0.2), 500.0
+        uinf = (0.0, 0.0, -0.18686)
+        supp, w, _ = inputs.thin_ring_vorticity(R0c, dcells, B)
+        rk = lgf.RKPlan(B, supp, dx, dt, re, scheme=0, use_graph=True)
+        xs = rk.blocks(0)
+        pv = lgf.Plan(lgf.Table(lgf.LAPLACE7, max_offset=63), [lgf.Solve(B, 3, supp, xs, dx=dx, scale=-1.0)],
+                      method=1)
+        a = torch.zeros((len(xs), 3, B, B, B), device="cuda")
+        pv.execute([torch.from_numpy(w / dx ** 2).cuda()], [a])
+        u0 = torch.zeros_like(a)
+        rk.op(lgf.OP_CURL_T, a, u0)
+        del a, pv
+        # ring speed over 7 steps (outside the timed region) against eq. u_saffman (beta_0 = 0.557966)
+        u, v = u0.clone(), torch.zeros_like(u0)
+        d0 = rk.diagnostics(u)
+        for _ in range(7):
+            rk.step(u, v, uinf)
+            u, v = v, u
+        d1 = rk.diagnostics(u)
+        ih = d0["I"] / np.linalg.norm(d0["I"])
+        speed = float((d1["X"] - d0["X"]) @ ih / (7 * dt) - np.asarray(uinf) @ ih)
+        eps = dcells / R0c
+        saffman = (math.log(8 / eps) - 0.557966) / (4 * math.pi)
+        u1 = torch.zeros_like(u0)
+        del u, v
+        return (lambda: rk.step(u0, u1, uinf)), [rk], len(xs) * B ** 3, {
+            "workload": "one Scheme-A IF-HERK step of the delta/R0 = 0.0125 ring (R0 = 400 cells, core 5 cells, "
+                        "Re = 500), Poisson solves by the block-sparse split solve",
+            "supp_blocks": int(len(supp)), "xsoln_blocks": int(len(xs)), "dt": dt, "alpha": dt / (re * dx * dx),
+            "ring_speed_vs_saffman": round(speed / saffman - 1, 5), "points": "D_xsoln points per step"}, []
     if name == "thinring_split":
         # the thinnest ring of Sec. 6 (delta / R0 = 0.0125: R0 = 400 cells, core 5 cells), w_x on the
         # blocks above 1e-6 max, targets their one-block dilation: its bounding box (about 750 cells
@@ -776,7 +814,7 @@ def main():
     ap.add_argument("--workload", default="ring128",
                     choices=["ring128", "blobs32", "blobs32_f64", "if128", "rk256", "rk256_b", "rk256_c",
                              "rk256_refresh", "vecscal256", "ragged64", "shell256", "shell256_split",
-                             "shell256_split_tc", "thinring_split", "rk256_vort"],
+                             "shell256_split_tc", "thinring_split", "rk256_vort", "rk_thinring"],
                     help="ring128 is the headline workload; the others print their own throughput")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -266,14 +266,19 @@ typedef struct {
     int scheme;                  /* tableau of eq. ifherk_schemes: 0 = Scheme A, 1 = Scheme B, 2 = Scheme C */
     int use_graph;               /* 1: lgf_rk_step captures its launch sequence in a CUDA graph on first
                                     use for a given (u_in, u_out, u_inf) and replays it (two cached) */
-    int reserved[2];             /* must be zero */
+    int poisson_method;          /* the Poisson solves D_supp -> D_xsoln: 0 = the whole-box FFT
+                                    convolution where its FFT lengths (<= 1024) reach, else the
+                                    block-sparse split solve (B = 16; boxes beyond 1024 cells, e.g. the
+                                    thin ring of Sec. 6); 1 = whole box; 2 = split */
+    int reserved[1];             /* must be zero */
 } lgf_rk_desc;
 
 /* Builds the LGF table, a scalar Poisson plan D_supp -> D_xsoln, the
  * integrating-factor plans H^i = E((c~_i - c~_{i-1}) alpha) on D_xsoln of the
  * scheme's shifted nodes (Sec. 3.2; c~_0 = c_1: A: E(a/2), E(a/2), I;
  * B: E(a/3), E(2a/3), I; C: E(8a/15), E(2a/15), E(a/3)), and all workspaces.
- * LGF_ERR_ARG if an integrating-factor radius exceeds min(B, 16).
+ * LGF_ERR_ARG if an integrating-factor radius exceeds min(B, 16), or if the whole box
+ * is asked for (or, with B = 8, needed) beyond its FFT lengths.
  * Synchronises `stream`.  The result is used only with the lgf_rk_* and
  * lgf_op_apply calls (and destroyed with lgf_plan_destroy). */
 lgf_status lgf_rk_plan(const lgf_rk_desc *d, void *stream, lgf_plan **out);

@@ -168,6 +168,8 @@ struct RkPlan {
     std::vector<StepGraph> graphs;
     lgf_plan *poisson = nullptr;
     lgf_plan *poisson3 = nullptr;  // vector Poisson supp -> xsoln (velocity refresh)
+    int poisson_method = 0;        // as in lgf_rk_desc; split = the sub-plans are block-sparse split solves
+    bool split = false;
     int *d_nbr27 = nullptr;
     int *d_coords = nullptr;   // [n_x][3] block coordinates
     double *d_acc = nullptr;   // diagnostics accumulators

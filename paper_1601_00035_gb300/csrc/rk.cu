@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <cmath>
 #include <unordered_map>
+#include <cstring>
 #include <utility>
 #include <vector>
 
@@ -97,8 +98,15 @@ lgf_status rk_project(RkPlan *r, Profiler &pr, const float *rv, const float *g, 
     // the solve's source array as it stands (M^supp: the plan reads only those blocks).
     // d^ overwrites G^T r: the whole-box passes read their source only in the first
     // pass and write their result only in the last, which starts after it has completed.
+    // The split solve reads its source on two streams, so it gets a copy of its own.
     const float *srcs[1] = {sx};
     float *dsts[1] = {sx};
+    if (r->split) {
+        float *ss = sx + r->scal_x;
+        const int B3 = r->B * r->B * r->B;
+        LGF_TRY(timed(pr, "gather_supp", s, [&] { return gather_launch(sx, ss, r->d_supp_idx, r->n_soln, B3, s); }));
+        srcs[0] = ss;
+    }
     LGF_TRY(lgf_conv_execute(r->poisson, srcs, dsts, s));
     LGF_TRY(timed(pr, "grad_combine", s, [&] {
         return grad_combine_launch(r->B, r->n_x, r->d_nbr27, sx, rv, g, out1, out2, c2, r->dx, s);
@@ -122,7 +130,10 @@ lgf_status lgf_rk_plan(const lgf_rk_desc *d, void *stream, lgf_plan **out)
     LGF_CHECK_ARG(d->dx > 0 && d->dt > 0 && d->re > 0, "lgf_rk_plan: dx, dt, re must be positive");
     LGF_CHECK_ARG(d->scheme >= 0 && d->scheme <= 2, "lgf_rk_plan: scheme %d not in {0 (A), 1 (B), 2 (C)}",
                   d->scheme);
-    for (int i = 0; i < 2; i++) LGF_CHECK_ARG(d->reserved[i] == 0, "lgf_rk_plan: reserved fields must be zero");
+    LGF_CHECK_ARG(d->reserved[0] == 0, "lgf_rk_plan: reserved fields must be zero");
+    LGF_CHECK_ARG(d->poisson_method >= 0 && d->poisson_method <= 2, "lgf_rk_plan: poisson_method %d not in {0, 1, 2}",
+                  d->poisson_method);
+    LGF_CHECK_ARG(d->poisson_method != 2 || d->B == 16, "lgf_rk_plan: the split Poisson solve takes B = 16");
     const int B = d->B;
     // blocks: soln as given, xsoln = soln dilated by one block, soln first
     std::unordered_map<int64_t, int> xi;
@@ -216,12 +227,28 @@ lgf_status lgf_rk_plan(const lgf_rk_desc *d, void *stream, lgf_plan **out)
             // the Poisson plan's length rule: max(2 m + 2, 2 E_s)
             const long len = std::max<long>(2 * m + 2, 2L * (shi[a] - slo[a] + 1) * B);
             const int n = poisson_pick_n((int)std::min<long>(len, 1 << 20));
-            need = std::max(need, n / 2 - 1);
+            need = n == 0 ? (1 << 20) : std::max(need, n / 2 - 1);  // 0: beyond the longest FFT
         }
         return need;
     }();
-    LGF_CHECK_ARG(K >= 1 && K <= 1024, "lgf_rk_plan: block set too large for the FFT sizes");
-    if ((st = lgf_table_build(LGF_KERNEL_LAPLACE7, 0.0, K, stream, &r->lgf_table)) != LGF_OK) return fail(st);
+    // whole box where its FFT lengths reach (K <= 511 means every length <= 1024), else the split
+    // solve (which builds its own near- and far-field tables; the plan's table is then small)
+    const bool whole_fits = K >= 1 && K <= 511;
+    r->poisson_method = d->poisson_method;
+    r->split = d->poisson_method == 2 || (d->poisson_method == 0 && !whole_fits);
+    if (r->split && B != 16) {
+        set_error("lgf_rk_plan: the block set needs FFTs longer than 1024 and the split solve takes B = 16");
+        return fail(LGF_ERR_ARG);
+    }
+    if (!r->split && !whole_fits) {
+        set_error("lgf_rk_plan: block set too large for the whole-box FFT lengths (use poisson_method 0 or 2)");
+        return fail(LGF_ERR_ARG);
+    }
+    if ((st = lgf_table_build(LGF_KERNEL_LAPLACE7, 0.0, r->split ? 63 : K, stream, &r->lgf_table)) != LGF_OK)
+        return fail(st);
+    lgf_plan_opts po;
+    std::memset(&po, 0, sizeof(po));
+    po.method = r->split ? 1 : 0;
     lgf_solve_desc pd;
     pd.B = B;
     pd.ncomp = 1;
@@ -231,11 +258,11 @@ lgf_status lgf_rk_plan(const lgf_rk_desc *d, void *stream, lgf_plan **out)
     pd.dst_blocks = xs.data();
     pd.dx = d->dx;
     pd.scale = -1.0;
-    if ((st = lgf_conv_plan(r->lgf_table, &pd, 1, nullptr, stream, &r->poisson)) != LGF_OK) return fail(st);
+    if ((st = lgf_conv_plan(r->lgf_table, &pd, 1, &po, stream, &r->poisson)) != LGF_OK) return fail(st);
     {
         lgf_solve_desc pv = pd;  // vector potential a = -L^{-1} w (velocity refresh)
         pv.ncomp = 3;
-        if ((st = lgf_conv_plan(r->lgf_table, &pv, 1, nullptr, stream, &r->poisson3)) != LGF_OK) return fail(st);
+        if ((st = lgf_conv_plan(r->lgf_table, &pv, 1, &po, stream, &r->poisson3)) != LGF_OK) return fail(st);
     }
     // shifted tableau of the scheme (eq. ifherk_schemes, eq. herk_shift)
     {

@@ -182,6 +182,33 @@ def two_rings_vorticity(cfg: int = 3, n: int = 128, sigma: float = 3.0):
     return w
 
 
+def thin_ring_vorticity(R: float = 400.0, sigma: float = 5.0, B: int = 16, rel_thresh: float = 1e-6, cfg: int = 6):
+    """All three components of the thin ring of thin_ring_blocks (component q at edge(q)
+    centres, Gamma = 1), on the blocks where any component exceeds rel_thresh * max.
+    Returns (block coordinates [n, 3], values [n, 3, B, B, B] float32)."""
+    rng = rng_for(cfg)
+    axis = random_axis_tilted(rng)
+    reach = 6.0 * sigma + B
+    span = int(math.ceil((R + reach) / B)) + 1
+    g = np.arange(-span, span)
+    bz, by, bx = np.meshgrid(g, g, g, indexing="ij")
+    cen = (np.stack([bx.ravel(), by.ravel(), bz.ravel()], 1) + 0.5) * B
+    p = cen @ _rotation(axis)
+    near = np.hypot(np.hypot(p[:, 0], p[:, 1]) - R, p[:, 2]) < reach
+    cand = np.stack([bx.ravel(), by.ravel(), bz.ravel()], 1)[near].astype(np.int32)
+    k, j, i = np.meshgrid(np.arange(B), np.arange(B), np.arange(B), indexing="ij")
+    base = np.stack([i.ravel(), j.ravel(), k.ravel()], 1).astype(float)
+    vals = np.zeros((len(cand), 3, B, B, B), dtype=np.float32)
+    for q in range(3):
+        shift = np.zeros(3)
+        shift[q] = -0.5
+        for n, c in enumerate(cand):
+            vals[n, q] = ring_vorticity(c * B + base + shift, np.zeros(3), axis, R, sigma)[:, q].reshape(B, B, B)
+    mx = np.abs(vals).reshape(len(cand), -1).max(1)
+    keep = mx > rel_thresh * mx.max()
+    return cand[keep], vals[keep], axis
+
+
 def thin_ring_blocks(R: float = 400.0, sigma: float = 5.0, B: int = 16, rel_thresh: float = 1e-6, cfg: int = 6):
     """A thin Gaussian-core ring of radius R cells and core sigma (delta/R0 = 0.0125 at the
     defaults, the thinnest ring of Sec. 6) centred at the origin, axis tilted as in the 128^3

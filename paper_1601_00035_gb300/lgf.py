@@ -58,7 +58,8 @@ class _RkDesc(ctypes.Structure):
         ("re", ctypes.c_double),
         ("scheme", ctypes.c_int),
         ("use_graph", ctypes.c_int),
-        ("reserved", ctypes.c_int * 2),
+        ("poisson_method", ctypes.c_int),
+        ("reserved", ctypes.c_int * 1),
     ]
 
 
@@ -337,7 +338,9 @@ class RKPlan:
     """One IF-HERK step (Scheme A, B or C) on a block set (lgf_rk_plan / lgf_rk_step)."""
 
     def __init__(self, B: int, soln_blocks, dx: float, dt: float, re: float, stream=None, scheme: int = SCHEME_A,
-                 use_graph: bool = False):
+                 use_graph: bool = False, poisson_method: int = 0):
+        """poisson_method: 0 whole box where its FFT lengths reach, else the split solve;
+        1 whole box; 2 block-sparse split solve (B = 16)."""
         L = load()
         self._soln = np.ascontiguousarray(soln_blocks, dtype=np.int32).reshape(-1, 3)
         d = _RkDesc()
@@ -345,6 +348,7 @@ class RKPlan:
         d.soln_blocks = self._soln.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         d.dx, d.dt, d.re, d.scheme = float(dx), float(dt), float(re), int(scheme)
         d.use_graph = int(bool(use_graph))
+        d.poisson_method = int(poisson_method)
         h = ctypes.c_void_p()
         _check(L.lgf_rk_plan(ctypes.byref(d), _stream(stream), ctypes.byref(h)))
         self._h = h

@@ -196,7 +196,7 @@ def _ring_run(lgf, n, R0c, dcells, nsteps=7):
     from paper_1601_00035_gb300 import inputs
     B = 16
     dx = 1.0 / R0c
-    dt, re = golden("ring_dt_gamma0_over_R0sq") * (50.0 / R0c), 500.0
+    dt, re = golden("ring_dt_gamma0_over_R0sq") * (50.0 / R0c) * ((dcells / R0c) / 0.2), 500.0
     uinf = (0.0, 0.0, golden("ring_uinf_z_R0_over_gamma0"))
     axis = inputs.random_axis_tilted(inputs.rng_for(4))
     w = inputs.vortex_ring_edges(n, R0c, dcells, axis) / dx ** 2
@@ -315,7 +315,7 @@ def test_adaptive_ring_run():
     lgf = built()
     B, R0c, dcells, n = 16, 24.0, 4.8, 128
     dx = 1.0 / R0c
-    dt, re = golden("ring_dt_gamma0_over_R0sq") * (50.0 / R0c), 500.0
+    dt, re = golden("ring_dt_gamma0_over_R0sq") * (50.0 / R0c) * ((dcells / R0c) / 0.2), 500.0
     axis = inputs.random_axis_tilted(inputs.rng_for(4))
     w = inputs.vortex_ring_edges(n, R0c, dcells, axis) / dx ** 2
     eps = 1e-4
@@ -367,6 +367,57 @@ def test_ring_speed_approaches_saffman():
         speed = (ds[-1]["X"] - ds[0]["X"]) @ ih / ((len(ds) - 1) * dt) - uinf @ ih
         rel.append(speed / ((math.log(8 / eps) - golden("saffman_beta0")) / (4 * math.pi)) - 1)
     assert abs(rel[1]) < 0.03 and abs(rel[1]) < abs(rel[0]), rel
+
+
+def test_thin_ring_split_speed_saffman():
+    """delta / R0 = 0.0125 (R0 = 400 cells, core 5 cells), the thinnest ring of Sec. 6. Its box
+    (about 750 cells across) is beyond the whole-box FFT lengths, so the RK plan takes the
+    block-sparse split solve for its Poisson problems (poisson_method 0 chooses it). The
+    initial velocity is u = C^T(-L^-1 w) by a split vector solve; after seven Scheme-B steps
+    the ring speed along I (plus the freestream) is within 3 % of Saffman's leading-order
+    value (eq. u_saffman, beta_0 of the Gaussian core). The time step is the 256^3 ring's
+    dt Gamma / R0^2 scaled by the cell size and by the core radius (the core's swirl
+    velocity ~ Gamma / (2 pi delta) sets the convective limit)."""
+    import math
+    from paper_1601_00035_gb300 import inputs
+    lgf = built()
+    B, R0c, dcells = 16, 400.0, 5.0
+    dx = 1.0 / R0c
+    supp, w, _ = inputs.thin_ring_vorticity(R0c, dcells, B)
+    dt, re = golden("ring_dt_gamma0_over_R0sq") * (50.0 / R0c) * ((dcells / R0c) / 0.2), 500.0
+    uinf = np.array([0.0, 0.0, golden("ring_uinf_z_R0_over_gamma0")])
+    rk = lgf.RKPlan(B, supp, dx, dt, re, scheme=1)
+    xs = rk.blocks(0)
+    pv = lgf.Plan(lgf.Table(lgf.LAPLACE7, max_offset=63), [lgf.Solve(B, 3, supp, xs, dx=dx, scale=-1.0)], method=1)
+    a = torch.zeros((len(xs), 3, B, B, B), device="cuda")
+    pv.execute([torch.from_numpy(w / dx ** 2).cuda()], [a])
+    u = torch.zeros_like(a)
+    rk.op(lgf.OP_CURL_T, a, u)
+    del a
+    v = torch.zeros_like(u)
+    # the step replayed as a graph (the split solve's second stream joins the capture)
+    # equals the eager step bitwise
+    rkg = lgf.RKPlan(B, supp, dx, dt, re, scheme=1, use_graph=True)
+    vg = torch.zeros_like(u)
+    rk.step(u, v, tuple(uinf))
+    rkg.step(u, vg, tuple(uinf))
+    rkg.step(u, vg, tuple(uinf))
+    torch.cuda.synchronize()
+    assert torch.equal(v, vg)
+    del rkg, vg
+    ds = []
+    for _ in range(8):
+        ds.append(rk.diagnostics(u))
+        rk.step(u, v, tuple(uinf))
+        u, v = v, u
+    ih = ds[0]["I"] / np.linalg.norm(ds[0]["I"])
+    speed = (ds[-1]["X"] - ds[0]["X"]) @ ih / ((len(ds) - 1) * dt) - uinf @ ih
+    eps = dcells / R0c
+    rel = speed / ((math.log(8 / eps) - golden("saffman_beta0")) / (4 * math.pi)) - 1
+    assert abs(rel) < 0.03, rel
+    # the impulse |I| = pi Gamma (R0^2 + delta^2 / 2) (Gamma = 1, R0 = 1)
+    assert abs(np.linalg.norm(ds[0]["I"]) / (math.pi * (1 + eps ** 2 / 2)) - 1) < 0.01
+    assert np.abs(ds[-1]["I"] - ds[0]["I"]).max() < 1e-4 * np.linalg.norm(ds[0]["I"])
 
 
 def test_step_graph_replay_bitwise():
