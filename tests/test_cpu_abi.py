@@ -97,3 +97,33 @@ def test_noalloc_rejects_bad_block_sets_on_the_host():
     # coordinates outside +-2^20
     st, msg = _noalloc_status([[1 << 20, 0, 0]])
     assert st == lgf.LGF_ERR_ARG and "coordinate" in msg
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The binding's ctypes structures have the size and field offsets that a C compiler
+    gives the header's structures (lgf_solve_desc, lgf_plan_opts, lgf_rk_desc)."""
+    import ctypes
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    from paper_1601_00035_gb300 import lgf
+    structs = {"lgf_solve_desc": lgf._SolveDesc, "lgf_plan_opts": lgf._PlanOpts, "lgf_rk_desc": lgf._RkDesc}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "lgf.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for fname, _ in py._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, fname, cname, fname))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([gcc, "-I", inc, str(src), "-o", str(exe)], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
