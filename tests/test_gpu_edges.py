@@ -255,14 +255,18 @@ def test_argument_errors():
     assert e.value.status == lgf.LGF_ERR_STATE
 
 
-def test_length_768():
-    """FFT length 768 (3 * 256) along x: a target block 20 blocks (320 cells) from the
-    source, beside two near blocks; sampled against the per-point direct sum."""
+@pytest.mark.parametrize("axis", [0, 2])
+def test_length_768(axis):
+    """FFT length 768 (3 * 256) along x (the x passes) or z (the packed z pass): a target
+    block 20 blocks (320 cells) from the source, beside two near blocks; sampled against
+    the per-point direct sum."""
     lgf = built()
     B = 16
-    rng = np.random.default_rng(768)
+    rng = np.random.default_rng(768 + axis)
     src_c = np.array([[0, 0, 0]], dtype=np.int32)
-    dst_c = np.array([[20, 0, 0], [0, 0, 0], [1, 1, 1]], dtype=np.int32)
+    far = [0, 0, 0]
+    far[axis] = 20
+    dst_c = np.array([far, [0, 0, 0], [1, 1, 1]], dtype=np.int32)
     f = rng.standard_normal((1, 1, B, B, B))
     K = lgf.required_max_offset(src_c, dst_c, B)
     assert K == 383
