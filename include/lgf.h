@@ -90,7 +90,7 @@ typedef struct {
                               split as G = G_near + G_far at split time a of its Bessel form,
                               G_near convolved block pair by block pair (16^3 blocks, offsets
                               up to 2 blocks), G_far on the coarse lattice of spacing 2 through
-                              8-point Lagrange interpolation and anterpolation; one solve, B = 16;
+                              10-point Lagrange interpolation and anterpolation; one solve, B = 16;
                               cost follows the active blocks; relative L2 error ~1e-7..1e-6;
                            2: autotune: plan both and keep the faster (one timed execution each) */
     int far_precision;  /* method 1: 0 = far-field interpolation and anterpolation in FP32 on the
@@ -98,9 +98,13 @@ typedef struct {
                            1 = the same as GEMMs on the tensor cores (tcgen05 kind::tf32 MMAs,
                            operands split into two TF32 parts, FP32 accumulation: the
                            reduced-precision far field, held to 1e-5) */
-    double split_alpha; /* method 1: the split time a; 0 takes 20 (the error and the near radius
-                           it sets are stated in DESIGN) */
-    int reserved[2];    /* must be zero */
+    double split_alpha; /* method 1: the split time a in [1, 64]; 0 takes 20, which keeps G_near
+                           within two blocks and the spacing-2 far field within 1e-6 */
+    int near_form;      /* method 1: the near-field multiply-accumulate: 0 = time both forms at
+                           plan time and keep the faster; 1 = one target per warp over its
+                           (offset, source) pairs; 2 = runs of 4 x-adjacent targets per warp
+                           (13 row loads per 20 multiply-adds, dense over each run) */
+    int reserved[1];    /* must be zero */
 } lgf_plan_opts;
 
 /* ---------------------------------------------------------------------------

@@ -881,7 +881,8 @@ lgf_status lgf_conv_plan(const lgf_table *t, const lgf_solve_desc *solves, int n
     *out = nullptr;
     LGF_CHECK_ARG(t != nullptr && solves != nullptr && n_solves >= 1, "lgf_conv_plan: bad table/solves/n_solves");
     if (opts) {
-        for (int i = 0; i < 2; i++) LGF_CHECK_ARG(opts->reserved[i] == 0, "lgf_conv_plan: reserved option fields must be zero");
+        LGF_CHECK_ARG(opts->reserved[0] == 0, "lgf_conv_plan: reserved option fields must be zero");
+        LGF_CHECK_ARG(opts->near_form >= 0 && opts->near_form <= 2, "lgf_conv_plan: near_form must be 0, 1 or 2");
         LGF_CHECK_ARG(opts->precision == 0 || opts->precision == 1, "lgf_conv_plan: precision must be 0 or 1");
         LGF_CHECK_ARG(opts->method >= 0 && opts->method <= 2, "lgf_conv_plan: method must be 0, 1 or 2");
         LGF_CHECK_ARG(opts->far_precision == 0 || opts->far_precision == 1,
@@ -916,7 +917,8 @@ lgf_status lgf_conv_plan(const lgf_table *t, const lgf_solve_desc *solves, int n
     } else if (method == 1) {
         st = check_split_solve(solves[0]);
         p->method = 1;
-        if (st == LGF_OK) st = plan_split(p, solves[0], alpha, opts ? opts->far_precision : 0, s);
+        if (st == LGF_OK)
+            st = plan_split(p, solves[0], alpha, opts ? opts->far_precision : 0, opts ? opts->near_form : 0, s);
         if (st == LGF_OK) st = plan_split_extras(p, solves[0], s);
     } else if (method == 2) {
         st = autotune_plan(p, t, solves, opts, s);

@@ -197,6 +197,15 @@ struct SplitPlan {
     float2 *d_U = nullptr;       // target spectra [nc][chunk][ndst][32]
     int *d_off = nullptr;        // [ndst + 1]
     int2 *d_pairs = nullptr;     // (offset index, source block)
+    // runs of 4 x-adjacent target slots: targets [nruns] (int4, -1 = empty slot); rows
+    // [run_row[r] .. run_row[r+1]): per (oy, oz) the W rows of ox = -2..2 and the 8
+    // sources x0 - 2 .. x0 + 5 (int4 x 4: w0..w3 | w4 s0 s1 s2 | s3..s6 | s7)
+    int nruns = 0, nrows = 0;
+    bool mac_runs = false;       // the run form measured faster than the pair form at plan time
+    float mac_ms[2] = {-1.f, -1.f};  // plan-time times of the pair and run forms (ms per launch)
+    int4 *d_run_tgt = nullptr;
+    int *d_run_row = nullptr;
+    int4 *d_rows = nullptr;
     // far field
     int ncsrc = 0, ncdst = 0;
     struct lgf_table *far_table = nullptr;  // G_far at even offsets (coarse octant)
@@ -217,7 +226,8 @@ struct SplitPlan {
     cudaEvent_t ev_fork = nullptr, ev_far = nullptr;
 };
 void free_split(SplitPlan *sp);
-lgf_status plan_split(lgf_plan *p, const lgf_solve_desc &d, double alpha, int far_precision, cudaStream_t s);
+lgf_status plan_split(lgf_plan *p, const lgf_solve_desc &d, double alpha, int far_precision, int near_form,
+                      cudaStream_t s);
 // device error flag of a split plan (a bounded tensor-core wait gave up): LGF_ERR_TIMEOUT, cleared
 lgf_status split_check(lgf_plan *p, cudaStream_t s);
 lgf_status run_split(lgf_plan *p, const float *src, float *dst, cudaStream_t s, Profiler *prof);

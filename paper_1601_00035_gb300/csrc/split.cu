@@ -264,6 +264,61 @@ __global__ void __launch_bounds__(256) k_near_mac(const float2 *__restrict__ W, 
     pdl_trigger();
 }
 
+// The same sum over runs of 4 x-adjacent target slots t_i = (x0 + i, y, z): for each
+// (oy, oz) row the warp loads the 8 source rows x0 - 2 .. x0 + 5 once and the 5 window
+// rows of ox = -2..2, and accumulates acc_i += W_(ox,oy,oz) S_(x0 + i - ox, y - oy, z - oz)
+// for all 20 (i, ox): 13 row loads per 20 complex multiply-adds.  W row noff is zero
+// (offsets without a window, and sources or targets that are absent).
+__global__ void __launch_bounds__(256) k_near_mac_runs(const float2 *__restrict__ W, int noff,
+                                                        const float2 *__restrict__ S, int nsrc,
+                                                        const int4 *__restrict__ run_tgt,
+                                                        const int *__restrict__ run_row,
+                                                        const int4 *__restrict__ rows, int nruns, int ndst,
+                                                        float2 *__restrict__ U)
+{
+    extern __shared__ float2 Kc[];  // [noff + 1][32]
+    const int chunk = blockIdx.x, c = blockIdx.z;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < noff * CH; i += 256) Kc[i] = W[(size_t)chunk * noff * CH + i];
+    if (threadIdx.x < CH) Kc[noff * CH + threadIdx.x] = make_float2(0.f, 0.f);
+    __syncthreads();
+    pdl_wait();
+    const int r = blockIdx.y * 8 + warp;
+    if (r < nruns) {
+        const float2 *Sc = S + ((size_t)c * NCHUNK + chunk) * nsrc * CH;
+        float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
+        const int r0 = __ldg(run_row + r), r1 = __ldg(run_row + r + 1);
+        for (int q = r0; q < r1; q++) {
+            const int4 a = __ldg(rows + 4 * q), b = __ldg(rows + 4 * q + 1), cc = __ldg(rows + 4 * q + 2),
+                       dd = __ldg(rows + 4 * q + 3);
+            const int wrow[5] = {a.x, a.y, a.z, a.w, b.x};
+            const int src[8] = {b.y, b.z, b.w, cc.x, cc.y, cc.z, cc.w, dd.x};
+            float2 sv[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) sv[k] = src[k] >= 0 ? Sc[(size_t)src[k] * CH + lane] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int o = 0; o < 5; o++) {  // ox = o - 2
+                const float2 w = Kc[wrow[o] * CH + lane];
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const float2 v = sv[i - o + 4];  // x0 + i - ox = x0 - 2 + (i - o + 4)
+                    ar[i] = fmaf(w.x, v.x, ar[i]);
+                    ar[i] = fmaf(-w.y, v.y, ar[i]);
+                    ai[i] = fmaf(w.x, v.y, ai[i]);
+                    ai[i] = fmaf(w.y, v.x, ai[i]);
+                }
+            }
+        }
+        const int4 tg = __ldg(run_tgt + r);
+        const int t4[4] = {tg.x, tg.y, tg.z, tg.w};
+        float2 *Uc = U + ((size_t)c * NCHUNK + chunk) * ndst * CH;
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+            if (t4[i] >= 0) Uc[(size_t)t4[i] * CH + lane] = make_float2(ar[i], ai[i]);
+    }
+    pdl_trigger();
+}
+
 // Inverse: one thread block per (target block, component): z, y (keeping the first
 // 16 outputs of each), then C2R in x with two rows per complex line; writes
 // dst = mul * result (the target window of the circular convolution).
@@ -797,6 +852,9 @@ void free_split(SplitPlan *sp)
     cudaFree(sp->d_U);
     cudaFree(sp->d_off);
     cudaFree(sp->d_pairs);
+    cudaFree(sp->d_run_tgt);
+    cudaFree(sp->d_run_row);
+    cudaFree(sp->d_rows);
     cudaFree(sp->d_Q);
     cudaFree(sp->d_q);
     cudaFree(sp->d_v);
@@ -817,7 +875,10 @@ void free_split(SplitPlan *sp)
     delete sp;
 }
 
-lgf_status plan_split(lgf_plan *p, const lgf_solve_desc &d, double alpha, int far_precision, cudaStream_t s)
+static lgf_status choose_near_mac(SplitPlan *sp, int near_form, cudaStream_t s);
+
+lgf_status plan_split(lgf_plan *p, const lgf_solve_desc &d, double alpha, int far_precision, int near_form,
+                      cudaStream_t s)
 {
     LGF_CHECK_ARG(d.B == BN, "block-sparse method: B=%d (the near-field blocks are 16^3)", d.B);
     LGF_CHECK_ARG(alpha >= 1.0 && alpha <= 64.0, "block-sparse method: split time %g outside [1, 64]", alpha);
@@ -931,8 +992,74 @@ lgf_status plan_split(lgf_plan *p, const lgf_solve_desc &d, double alpha, int fa
     LGF_TRY(dalloc_n(&sp->d_pairs, pairs.size(), bytes));
     LGF_TRY(upload_v(sp->d_off, off, s));
     LGF_TRY(upload_v(sp->d_pairs, pairs, s));
+    {
+        // runs of 4 x-adjacent target slots (x0 a multiple of 4) and their (oy, oz) rows
+        std::unordered_map<int, int> dmap;  // (ox+2) + 5 (oy+2) + 25 (oz+2) -> W row
+        for (int k = 0; k < sp->noff; k++)
+            dmap[(offs[3 * k] + 2) + 5 * (offs[3 * k + 1] + 2) + 25 * (offs[3 * k + 2] + 2)] = k;
+        auto wrow = [&](int ox, int oy, int oz) {
+            auto it = dmap.find((ox + 2) + 5 * (oy + 2) + 25 * (oz + 2));
+            return it == dmap.end() ? sp->noff : it->second;
+        };
+        auto fdiv4 = [](int v) { return v >= 0 ? v / 4 : -((-v + 3) / 4); };
+        std::unordered_map<int64_t, int> rmap;
+        std::vector<int4> rt;
+        for (int t = 0; t < d.n_dst; t++) {
+            const int x = d.dst_blocks[3 * t], y = d.dst_blocks[3 * t + 1], z = d.dst_blocks[3 * t + 2];
+            const int x0 = 4 * fdiv4(x);
+            auto it = rmap.find(key3(x0, y, z));
+            if (it == rmap.end()) {
+                it = rmap.emplace(key3(x0, y, z), (int)rt.size()).first;
+                rt.push_back(make_int4(-1, -1, -1, -1));
+            }
+            int *slot = &rt[it->second].x;
+            slot[x - x0] = t;
+        }
+        // run coordinates back from any of its targets
+        std::vector<int> run_row(rt.size() + 1, 0);
+        std::vector<int4> rows;
+        for (size_t r = 0; r < rt.size(); r++) {
+            run_row[r] = (int)(rows.size() / 4);
+            const int *slot = &rt[r].x;
+            int t = -1;
+            for (int i = 0; i < 4 && t < 0; i++) t = slot[i];
+            const int x0 = 4 * fdiv4(d.dst_blocks[3 * t]), y = d.dst_blocks[3 * t + 1], z = d.dst_blocks[3 * t + 2];
+            for (int oz = -RNEAR; oz <= RNEAR; oz++)
+                for (int oy = -RNEAR; oy <= RNEAR; oy++) {
+                    int src[8];
+                    bool any = false;
+                    for (int k = 0; k < 8; k++) {
+                        auto it = smap.find(key3(x0 - 2 + k, y - oy, z - oz));
+                        src[k] = it == smap.end() ? -1 : it->second;
+                        any = any || src[k] >= 0;
+                    }
+                    if (!any) continue;
+                    int w[5];
+                    bool anyw = false;
+                    for (int o = 0; o < 5; o++) {
+                        w[o] = wrow(o - 2, oy, oz);
+                        anyw = anyw || w[o] < sp->noff;
+                    }
+                    if (!anyw) continue;
+                    rows.push_back(make_int4(w[0], w[1], w[2], w[3]));
+                    rows.push_back(make_int4(w[4], src[0], src[1], src[2]));
+                    rows.push_back(make_int4(src[3], src[4], src[5], src[6]));
+                    rows.push_back(make_int4(src[7], -1, -1, -1));
+                }
+        }
+        run_row[rt.size()] = (int)(rows.size() / 4);
+        sp->nruns = (int)rt.size();
+        sp->nrows = (int)(rows.size() / 4);
+        LGF_TRY(dalloc_n(&sp->d_run_tgt, rt.size(), bytes));
+        LGF_TRY(dalloc_n(&sp->d_run_row, run_row.size(), bytes));
+        LGF_TRY(dalloc_n(&sp->d_rows, std::max<size_t>(rows.size(), 4), bytes));
+        LGF_TRY(upload_v(sp->d_run_tgt, rt, s));
+        LGF_TRY(upload_v(sp->d_run_row, run_row, s));
+        if (!rows.empty()) LGF_TRY(upload_v(sp->d_rows, rows, s));
+    }
     LGF_TRY(dalloc_n(&sp->d_S, (size_t)d.ncomp * NFREQ * d.n_src, bytes));
     LGF_TRY(dalloc_n(&sp->d_U, (size_t)d.ncomp * NFREQ * d.n_dst, bytes));
+    LGF_TRY(choose_near_mac(sp, near_form, s));
 
     // --- far field: coarse block sets, G_far table, coarse plan ---
     float P[BN * W];
@@ -1087,6 +1214,64 @@ lgf_status split_check(lgf_plan *p, cudaStream_t s)
     return LGF_OK;
 }
 
+// The near-field multiply-accumulate in the form the plan chose (runs: 4 x-adjacent
+// targets per warp; pairs: one target per warp over its (offset, source) list).
+static lgf_status launch_near_mac(const SplitPlan *sp, bool runs, cudaStream_t s)
+{
+    const int nc = sp->ncomp;
+    if (runs)
+        LGF_CUDA_TRY(launch_pdl_smem(k_near_mac_runs, dim3(NCHUNK, (sp->nruns + 7) / 8, nc), dim3(256),
+                                     (size_t)(sp->noff + 1) * CH * sizeof(float2), s, (const float2 *)sp->d_W,
+                                     sp->noff, (const float2 *)sp->d_S, sp->nsrc, (const int4 *)sp->d_run_tgt,
+                                     (const int *)sp->d_run_row, (const int4 *)sp->d_rows, sp->nruns, sp->ndst,
+                                     sp->d_U));
+    else
+        LGF_CUDA_TRY(launch_pdl_smem(k_near_mac, dim3(NCHUNK, (sp->ndst + 63) / 64, nc), dim3(256),
+                                     (size_t)sp->noff * CH * sizeof(float2), s, (const float2 *)sp->d_W, sp->noff,
+                                     (const float2 *)sp->d_S, sp->nsrc, (const int *)sp->d_off,
+                                     (const int2 *)sp->d_pairs, sp->ndst, sp->d_U));
+    return LGF_OK;
+}
+
+// Plan time (near_form 0): time both forms (three launches each, on zeroed spectra) and
+// keep the faster; near_form 1 / 2 takes the pair / run form.
+// The run form does 20 multiply-adds per 13 row loads, dense over each run's rows, so it
+// wins where targets fill their runs (the 256^3 shell) and loses where they are sparse.
+static lgf_status choose_near_mac(SplitPlan *sp, int near_form, cudaStream_t s)
+{
+    if (near_form != 0) {  // the caller's choice
+        sp->mac_runs = near_form == 2;
+        return LGF_OK;
+    }
+    LGF_CUDA_TRY(cudaMemsetAsync(sp->d_S, 0, (size_t)sp->ncomp * NFREQ * sp->nsrc * sizeof(float2), s));
+    cudaEvent_t e[2];
+    LGF_CUDA_TRY(cudaEventCreate(&e[0]));
+    if (cudaEventCreate(&e[1]) != cudaSuccess) {
+        cudaEventDestroy(e[0]);
+        set_error("event creation failed");
+        return LGF_ERR_CUDA;
+    }
+    lgf_status st = LGF_OK;
+    for (int form = 0; form < 2 && st == LGF_OK; form++) {
+        st = launch_near_mac(sp, form == 1, s);  // warm-up
+        if (st == LGF_OK && cudaEventRecord(e[0], s) != cudaSuccess) st = LGF_ERR_CUDA;
+        for (int k = 0; k < 3 && st == LGF_OK; k++) st = launch_near_mac(sp, form == 1, s);
+        if (st == LGF_OK && cudaEventRecord(e[1], s) != cudaSuccess) st = LGF_ERR_CUDA;
+        if (st == LGF_OK && cudaEventSynchronize(e[1]) != cudaSuccess) st = LGF_ERR_CUDA;
+        float ms = 0.f;
+        if (st == LGF_OK && cudaEventElapsedTime(&ms, e[0], e[1]) != cudaSuccess) st = LGF_ERR_CUDA;
+        sp->mac_ms[form] = ms / 3.f;
+    }
+    cudaEventDestroy(e[0]);
+    cudaEventDestroy(e[1]);
+    if (st != LGF_OK) {
+        if (st == LGF_ERR_CUDA) set_error("timing the near-field forms failed");
+        return st;
+    }
+    sp->mac_runs = sp->mac_ms[1] < sp->mac_ms[0];
+    return LGF_OK;
+}
+
 lgf_status run_split(lgf_plan *p, const float *src, float *dst, cudaStream_t s, Profiler *prof)
 {
     SplitPlan *sp = p->split;
@@ -1127,10 +1312,7 @@ lgf_status run_split(lgf_plan *p, const float *src, float *dst, cudaStream_t s, 
     LGF_CUDA_TRY(launch_pdl_smem(k_near_fwd, dim3(sp->nsrc, nc), dim3(256), NEAR_SMEM, s, src, nc, 0, sp->nsrc, sp->d_S));
     if (P) prof->end("near_fwd", s);
     if (P) prof->begin(s);
-    LGF_CUDA_TRY(launch_pdl_smem(k_near_mac, dim3(NCHUNK, (sp->ndst + 63) / 64, nc), dim3(256),
-                                 (size_t)sp->noff * CH * sizeof(float2), s, (const float2 *)sp->d_W, sp->noff,
-                                 (const float2 *)sp->d_S, sp->nsrc, (const int *)sp->d_off, (const int2 *)sp->d_pairs,
-                                 sp->ndst, sp->d_U));
+    LGF_TRY(launch_near_mac(sp, sp->mac_runs, s));
     if (P) prof->end("near_mac", s);
     if (P) prof->begin(s);
     LGF_CUDA_TRY(launch_pdl_smem(k_near_inv, dim3(sp->ndst, nc), dim3(256), NEAR_SMEM, s, (const float2 *)sp->d_U,

@@ -65,7 +65,8 @@ class _RkDesc(ctypes.Structure):
 
 class _PlanOpts(ctypes.Structure):
     _fields_ = [("use_graph", ctypes.c_int), ("precision", ctypes.c_int), ("method", ctypes.c_int),
-                ("far_precision", ctypes.c_int), ("split_alpha", ctypes.c_double), ("reserved", ctypes.c_int * 2)]
+                ("far_precision", ctypes.c_int), ("split_alpha", ctypes.c_double), ("near_form", ctypes.c_int),
+                ("reserved", ctypes.c_int * 1)]
 
 
 METHOD_WHOLE_BOX, METHOD_SPLIT, METHOD_AUTOTUNE = 0, 1, 2
@@ -218,7 +219,8 @@ class Plan:
     """lgf_conv_plan over one or more solves."""
 
     def __init__(self, table: Table, solves: Sequence[Solve], use_graph: bool = False, stream=None,
-                 precision: int = 0, method: int = 0, split_alpha: float = 0.0, far_precision: int = 0):
+                 precision: int = 0, method: int = 0, split_alpha: float = 0.0, far_precision: int = 0,
+                 near_form: int = 0):
         L = load()
         self.table = table  # keep alive
         self.solves = list(solves)
@@ -238,6 +240,7 @@ class Plan:
         opts.method = int(method)
         opts.split_alpha = float(split_alpha)
         opts.far_precision = int(far_precision)
+        opts.near_form = int(near_form)
         h = ctypes.c_void_p()
         _check(L.lgf_conv_plan(table._h, descs, len(self.solves), ctypes.byref(opts), _stream(stream), ctypes.byref(h)))
         self._h = h

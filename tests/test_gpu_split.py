@@ -3,7 +3,7 @@ LGF-FMM's near field by block pairs and far field by interpolation, evaluated to
 tolerance) against the FP64 direct sum of eq. dpoisson_conv.
 
 The split G = G_near + G_far at time a = 20 of the Bessel form, near offsets up to two
-16^3 blocks and 8-point Lagrange interpolation on the spacing-2 coarse lattice give a
+16^3 blocks and 10-point Lagrange interpolation on the spacing-2 coarse lattice give a
 relative L2 error of a few 1e-7 on smooth and on white-noise sources (the committed CPU
 study tests/test_oracle_split_study.py); the FP32 bound 1e-6 is applied unscaled, also
 to a target set that sees only the far field.
@@ -21,13 +21,13 @@ pytestmark = pytest.mark.gpu
 SPLIT = 1
 
 
-def _plan(lgf, src_c, dst_c, ncomp=1, scale=1.0, dx=1.0, method=SPLIT, use_graph=False, far_precision=0):
+def _plan(lgf, src_c, dst_c, ncomp=1, scale=1.0, dx=1.0, method=SPLIT, use_graph=False, far_precision=0, near_form=0):
     # the split plan builds its own tables; the whole-box plan (methods 0 and 2) samples
     # this one up to half its FFT length (a box beyond the FFT limit gets the largest table)
     K = 31 if method == SPLIT else max(31, lgf.required_max_offset(src_c, dst_c, 16))
     t = lgf.Table(lgf.LAPLACE7, max_offset=min(K, 1024))
     return t, lgf.Plan(t, [lgf.Solve(16, ncomp, src_c, dst_c, dx=dx, scale=scale)], method=method,
-                       use_graph=use_graph, far_precision=far_precision)
+                       use_graph=use_graph, far_precision=far_precision, near_form=near_form)
 
 
 def _dilate(blocks, r=1):
@@ -41,11 +41,12 @@ def _dilate(blocks, r=1):
     return np.array(sorted(out), dtype=np.int32)
 
 
-@pytest.mark.parametrize("seed", [0, 1])
-def test_split_random_blocks_full(seed):
+@pytest.mark.parametrize("seed,near_form", [(0, 0), (1, 0), (0, 1), (0, 2)])
+def test_split_random_blocks_full(seed, near_form):
     """White-noise sources on a holed set of 16^3 blocks, targets on their two-block
     dilation (every near offset and the far field), two components, dx != 1, scale -1:
-    every target point against the direct sum."""
+    every target point against the direct sum; with the near-field multiply-accumulate
+    chosen at plan time, and in each of its two forms (pairs, runs of 4 targets)."""
     lgf = built()
     B = 16
     rng = np.random.default_rng(200 + seed)
@@ -55,7 +56,7 @@ def test_split_random_blocks_full(seed):
     dst_c = dst_c[rng.random(len(dst_c)) < 0.5]
     f = rng.standard_normal((len(src_c), 2, B, B, B)).astype(np.float32)
     dx, scale = 0.5, -1.0
-    _, plan = _plan(lgf, src_c, dst_c, ncomp=2, scale=scale, dx=dx)
+    _, plan = _plan(lgf, src_c, dst_c, ncomp=2, scale=scale, dx=dx, near_form=near_form)
     d_dst = torch.zeros((len(dst_c), 2, B, B, B), device="cuda")
     plan.execute([torch.from_numpy(f).cuda()], [d_dst])
     out = d_dst.cpu().numpy()
