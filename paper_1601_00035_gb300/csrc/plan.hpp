@@ -200,6 +200,7 @@ struct SplitPlan {
     // runs of 4 x-adjacent target slots: targets [nruns] (int4, -1 = empty slot); rows
     // [run_row[r] .. run_row[r+1]): per (oy, oz) the W rows of ox = -2..2 and the 8
     // sources x0 - 2 .. x0 + 5 (int4 x 4: w0..w3 | w4 s0 s1 s2 | s3..s6 | s7)
+    int levels = 1;              // split levels (1: the coarse convolution is a whole-box plan)
     int nruns = 0, nrows = 0;
     bool mac_runs = false;       // the run form measured faster than the pair form at plan time
     float mac_ms[2] = {-1.f, -1.f};  // plan-time times of the pair and run forms (ms per launch)

@@ -877,11 +877,29 @@ void free_split(SplitPlan *sp)
 
 static lgf_status choose_near_mac(SplitPlan *sp, int near_form, cudaStream_t s);
 
+// One level of the split on the lattice of spacing `stride` (in unit cells; the level's own
+// block coordinates are in units of 16 of its points): the near part of the kernel is the
+// Bessel-form integral over t in [t_lo, alpha] (t_lo = 0: the LGF's own split), the far part
+// the integral from alpha on, sampled on the lattice of spacing 2 stride.  The far part's
+// coarse convolution is a whole-box plan, or, where that box is beyond the FFT lengths or
+// large (a 512^3 grid or more), the next level: a split plan on the coarse lattice with
+// t in [alpha, 4 alpha] near and [4 alpha, inf) far (the same near radius and interpolation
+// error in that level's units, since the heat kernel's width grows as sqrt t).
+static lgf_status plan_split_level(lgf_plan *p, const lgf_solve_desc &d, double t_lo, double alpha, int stride,
+                                   int far_precision, int near_form, cudaStream_t s);
+
 lgf_status plan_split(lgf_plan *p, const lgf_solve_desc &d, double alpha, int far_precision, int near_form,
                       cudaStream_t s)
 {
-    LGF_CHECK_ARG(d.B == BN, "block-sparse method: B=%d (the near-field blocks are 16^3)", d.B);
     LGF_CHECK_ARG(alpha >= 1.0 && alpha <= 64.0, "block-sparse method: split time %g outside [1, 64]", alpha);
+    return plan_split_level(p, d, 0.0, alpha, 1, far_precision, near_form, s);
+}
+
+static lgf_status plan_split_level(lgf_plan *p, const lgf_solve_desc &d, double t_lo, double alpha, int stride,
+                                   int far_precision, int near_form, cudaStream_t s)
+{
+    LGF_CHECK_ARG(d.B == BN, "block-sparse method: B=%d (the near-field blocks are 16^3)", d.B);
+    LGF_CHECK_ARG(stride <= 16, "block-sparse method: more than five levels");
     SplitPlan *sp = new (std::nothrow) SplitPlan();
     if (!sp) {
         set_error("host allocation failed");
@@ -902,7 +920,7 @@ lgf_status plan_split(lgf_plan *p, const lgf_solve_desc &d, double alpha, int fa
     double *d_near = nullptr;
     const int64_t noct = (int64_t)(KNEAR + 1) * (KNEAR + 2) * (KNEAR + 3) / 6;
     LGF_TRY(dalloc_n(&d_near, (size_t)noct, bytes));
-    lgf_status st = build_lgf_octant_part(KNEAR, 1, 0.0, alpha, d_near, s);
+    lgf_status st = build_lgf_octant_part(KNEAR, stride, t_lo, alpha, d_near, s);
     std::vector<double> h_near(noct);
     if (st == LGF_OK && cudaMemcpy(h_near.data(), d_near, noct * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
         st = LGF_ERR_CUDA;
@@ -1103,6 +1121,8 @@ lgf_status plan_split(lgf_plan *p, const lgf_solve_desc &d, double alpha, int fa
     sp->ncdst = (int)cdst.size() / 3;
     // the coarse plan's table must cover half its FFT length: same size rule as lgf_conv_plan
     int Kc = 1;
+    bool beyond = false;  // a whole-box coarse plan would need an FFT longer than 1024
+    double vol = 1.0;     // its FFT grid points
     for (int a = 0; a < 3; a++) {
         int smin = 1 << 30, smax = -(1 << 30), tmin = 1 << 30, tmax = -(1 << 30);
         for (int i = 0; i < sp->ncsrc; i++) smin = std::min(smin, csrc[3 * i + a]), smax = std::max(smax, csrc[3 * i + a]);
@@ -1110,9 +1130,36 @@ lgf_status plan_split(lgf_plan *p, const lgf_solve_desc &d, double alpha, int fa
         const long S0 = 16L * smin, S1 = 16L * (smax + 1) - 1, T0 = 16L * tmin, T1 = 16L * (tmax + 1) - 1;
         const long m = std::max(std::labs(T0 - S1), std::labs(T1 - S0));
         const int n = poisson_pick_n((int)std::min<long>(std::max(2 * m + 2, 2 * (S1 - S0 + 1)), 1 << 20));
-        LGF_CHECK_ARG(n > 0, "block-sparse method: the coarse far-field box needs an FFT longer than 1024 on axis %d", a);
+        beyond = beyond || n == 0;
+        vol *= n;
         Kc = std::max(Kc, n / 2 - 1);
     }
+    lgf_solve_desc cd;
+    std::memset(&cd, 0, sizeof(cd));
+    cd.B = BN;
+    cd.ncomp = d.ncomp;
+    cd.n_src = sp->ncsrc;
+    cd.n_dst = sp->ncdst;
+    cd.src_blocks = csrc.data();
+    cd.dst_blocks = cdst.data();
+    cd.dx = 1.0;
+    cd.scale = 1.0;
+    if (beyond || vol >= (double)(1 << 28)) {
+        // the next level: a split plan on the coarse lattice (convolves the coarse charges
+        // with G_far(2 stride .) as its own near part t in [alpha, 4 alpha] and far part)
+        lgf_plan *q = new (std::nothrow) lgf_plan();
+        if (!q) {
+            set_error("host allocation failed");
+            return LGF_ERR_OOM;
+        }
+        q->kind = LGF_KERNEL_LAPLACE7;
+        q->device = p->device;
+        q->method = 1;
+        sp->coarse = q;
+        LGF_TRY(plan_split_level(q, cd, alpha, 4.0 * alpha, 2 * stride, far_precision, near_form, s));
+        sp->levels = 1 + q->split->levels;
+        bytes += q->bytes;
+    } else {
     lgf_table *ft = new (std::nothrow) lgf_table();
     if (!ft) {
         set_error("host allocation failed");
@@ -1131,21 +1178,13 @@ lgf_status plan_split(lgf_plan *p, const lgf_solve_desc &d, double alpha, int fa
         set_error("far table allocation failed");
         return LGF_ERR_OOM;
     }
-    LGF_TRY(build_lgf_octant_part(Kc, 2, alpha, 0.0, ft->d_vals, s));
-    lgf_solve_desc cd;
-    std::memset(&cd, 0, sizeof(cd));
-    cd.B = BN;
-    cd.ncomp = d.ncomp;
-    cd.n_src = sp->ncsrc;
-    cd.n_dst = sp->ncdst;
-    cd.src_blocks = csrc.data();
-    cd.dst_blocks = cdst.data();
-    cd.dx = 1.0;
-    cd.scale = 1.0;
+    LGF_TRY(build_lgf_octant_part(Kc, 2 * stride, alpha, 0.0, ft->d_vals, s));
     lgf_plan_opts co;
     std::memset(&co, 0, sizeof(co));
     LGF_TRY(lgf_conv_plan(ft, &cd, 1, &co, (void *)s, &sp->coarse));
     bytes += sp->coarse->bytes;
+    sp->levels = 1;
+    }
     // lookups: fine source blocks (dense over their box + 1), coarse target blocks
     int fmin[3], fmax[3], cmin[3], cmax[3];
     for (int a = 0; a < 3; a++) {
