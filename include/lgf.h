@@ -90,7 +90,10 @@ typedef struct {
                               split as G = G_near + G_far at split time a of its Bessel form,
                               G_near convolved block pair by block pair (16^3 blocks, offsets
                               up to 2 blocks), G_far on the coarse lattice of spacing 2 through
-                              10-point Lagrange interpolation and anterpolation; one solve, B = 16;
+                              10-point Lagrange interpolation and anterpolation, the coarse sum
+                              by a whole-box convolution or, where that box is large (a 512^3 FFT
+                              grid or more, or beyond 1024-point FFTs), by the next split level
+                              (near t in [a, 4a], far on the spacing-4 lattice); one solve, B = 16;
                               cost follows the active blocks; relative L2 error ~1e-7..1e-6;
                            2: autotune: plan both and keep the faster (one timed execution each) */
     int far_precision;  /* method 1: 0 = far-field interpolation and anterpolation in FP32 on the
