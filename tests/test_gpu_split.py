@@ -228,18 +228,21 @@ def test_split_tensor_core_far_field():
     assert err < 1e-5, err
 
 
-def test_split_thin_ring_sampled():
+@pytest.mark.parametrize("far_precision", [0, 1])
+def test_split_thin_ring_sampled(far_precision):
     """The thinnest ring of Sec. 6 (delta / R0 = 0.0125: R0 = 400 cells, 5-cell core, tilted),
     whose bounding box (about 750 cells across) the whole-box embedding cannot take: the
-    split solve on its 1616 source blocks and their dilation, 512 sampled targets against
-    the direct sum."""
+    split solve on its 1616 source blocks and their dilation (two levels: its coarse box is a
+    768^3 FFT grid), 512 sampled targets against the direct sum; 1e-6 with the FP32 far
+    field, 1e-5 with the tensor-core far field on both levels."""
     lgf = built()
     B = 16
     src_c, vals = inputs.thin_ring_blocks()
     dst_c = _dilate(src_c)
-    with pytest.raises(lgf.LGFError):
-        _plan(lgf, src_c, dst_c, method=0)
-    _, plan = _plan(lgf, src_c, dst_c, scale=-1.0)
+    if far_precision == 0:
+        with pytest.raises(lgf.LGFError):
+            _plan(lgf, src_c, dst_c, method=0)
+    _, plan = _plan(lgf, src_c, dst_c, scale=-1.0, far_precision=far_precision)
     d_dst = torch.zeros((len(dst_c), 1, B, B, B), device="cuda")
     plan.execute([torch.from_numpy(vals).cuda()], [d_dst])
     plan.check()
@@ -253,7 +256,7 @@ def test_split_thin_ring_sampled():
     offs_max = int(max(np.abs(pts.max(0) - sp.min(0)).max(), np.abs(sp.max(0) - pts.min(0)).max()))
     ref = -O.direct_conv(O.lgf_cube(offs_max), sp[nz], v[nz], pts)
     err = rel_l2(block_values_at(out, dst_c, B, pts), ref)
-    assert err < 1e-6, err
+    assert err < (1e-6 if far_precision == 0 else 1e-5), err
 
 
 def test_bounded_wait_reports_timeout_and_context_survives():
