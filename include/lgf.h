@@ -163,7 +163,8 @@ int lgf_plan_method(const lgf_plan *p, double *ms_whole_box, double *ms_split);
 /* Synchronises `stream` and reports LGF_ERR_TIMEOUT if a bounded device-side wait of the
  * plan's kernels gave up since the last check (the flag is then cleared; the results of
  * the executions since then are not valid), LGF_OK otherwise.  Only the block-sparse
- * method's tensor-core kernels wait; lgf_conv_execute_host checks on its own. */
+ * method waits on the device (its window-spectrum staging by bulk copy and its tensor-core
+ * completions); lgf_conv_execute_host checks on its own. */
 lgf_status lgf_plan_check(lgf_plan *p, void *stream);
 
 /* Failure detection of the bounded device waits (the paper has no counterpart): runs the

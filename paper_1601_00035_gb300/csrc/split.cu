@@ -224,19 +224,49 @@ __global__ void __launch_bounds__(256) k_near_fwd(const float *__restrict__ src,
     }
 }
 
+// The window spectra of a chunk ([noff][32] complex, contiguous) are staged in shared
+// memory by one bulk copy (TMA) that completes on an mbarrier; every thread waits on the
+// barrier with a bounded poll count and, if the copy has not landed by then, the block
+// records the error flag (LGF_ERR_TIMEOUT on the next check) and returns.
+constexpr int STAGE_WAIT = 1 << 18;
+__device__ __forceinline__ bool stage_windows(float2 *Kc, const float2 *src, int noff, unsigned long long *bar_s,
+                                              int *err)
+{
+    const uint32_t bar = tc::smem_addr(bar_s);
+    const uint32_t bytes = (uint32_t)noff * CH * sizeof(float2);
+    if (threadIdx.x == 0) {
+        tc::mbar_init(bar, 1);
+        tc::fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tc::mbar_expect_tx(bar, bytes);
+        tc::bulk_g2s(tc::smem_addr(Kc), src, bytes, bar);
+    }
+    const bool ok = tc::mbar_wait(bar, 0, STAGE_WAIT);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+            atomicExch(err, 1);
+            tc::mbar_wait(bar, 0, STAGE_WAIT);  // let a late copy land before the block exits
+        }
+        return false;
+    }
+    return true;
+}
+
 // Spectral multiply-accumulate: U_t(k) = sum_d W_d(k) S_{t-d}(k) over the kept offsets
 // present for target t.  One thread block per (chunk, group of 64 targets, component);
 // a warp per target, lane = frequency in the chunk.  pairs[off[t] .. off[t+1]) lists
 // (d, s) for target t.
 __global__ void __launch_bounds__(256) k_near_mac(const float2 *__restrict__ W, int noff, const float2 *__restrict__ S,
                                                    int nsrc, const int *__restrict__ off, const int2 *__restrict__ pairs,
-                                                   int ndst, float2 *__restrict__ U)
+                                                   int ndst, float2 *__restrict__ U, int *err)
 {
-    extern __shared__ float2 Kc[];  // [noff][32]
+    extern __shared__ __align__(128) float2 Kc[];  // [noff][32]
+    __shared__ __align__(8) unsigned long long kbar;
     const int chunk = blockIdx.x, c = blockIdx.z;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < noff * CH; i += 256) Kc[i] = W[(size_t)chunk * noff * CH + i];
-    __syncthreads();
+    if (!stage_windows(Kc, W + (size_t)chunk * noff * CH, noff, &kbar, err)) return;
     pdl_wait();
     const float2 *Sc = S + ((size_t)c * NCHUNK + chunk) * nsrc * CH;
     float2 *Uc = U + ((size_t)c * NCHUNK + chunk) * ndst * CH;
@@ -274,14 +304,14 @@ __global__ void __launch_bounds__(256) k_near_mac_runs(const float2 *__restrict_
                                                         const int4 *__restrict__ run_tgt,
                                                         const int *__restrict__ run_row,
                                                         const int4 *__restrict__ rows, int nruns, int ndst,
-                                                        float2 *__restrict__ U)
+                                                        float2 *__restrict__ U, int *err)
 {
-    extern __shared__ float2 Kc[];  // [noff + 1][32]
+    extern __shared__ __align__(128) float2 Kc[];  // [noff + 1][32]
+    __shared__ __align__(8) unsigned long long kbar;
     const int chunk = blockIdx.x, c = blockIdx.z;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < noff * CH; i += 256) Kc[i] = W[(size_t)chunk * noff * CH + i];
     if (threadIdx.x < CH) Kc[noff * CH + threadIdx.x] = make_float2(0.f, 0.f);
-    __syncthreads();
+    if (!stage_windows(Kc, W + (size_t)chunk * noff * CH, noff, &kbar, err)) return;  // (its barrier orders the zero row)
     pdl_wait();
     const int r = blockIdx.y * 8 + warp;
     if (r < nruns) {
@@ -914,6 +944,9 @@ static lgf_status plan_split_level(lgf_plan *p, const lgf_solve_desc &d, double 
     sp->dx = d.dx;
     sp->scale = d.scale;
     size_t &bytes = p->bytes;
+    // device error flag of the bounded waits (window staging, tensor-core completions)
+    LGF_TRY(dalloc_n(&sp->d_err, 1, bytes));
+    LGF_CUDA_TRY(cudaMemsetAsync(sp->d_err, 0, sizeof(int), s));
     LGF_CUDA_TRY(fft::upload_tw64());
 
     // --- near field: G_near table, kept offsets, window spectra ---
@@ -1091,8 +1124,6 @@ static lgf_status plan_split_level(lgf_plan *p, const lgf_solve_desc &d, double 
         LGF_TRY(dalloc_n(&sp->d_Bi, bi.size(), bytes));
         LGF_TRY(upload_v(sp->d_Ba, ba, s));
         LGF_TRY(upload_v(sp->d_Bi, bi, s));
-        LGF_TRY(dalloc_n(&sp->d_err, 1, bytes));
-        LGF_CUDA_TRY(cudaMemsetAsync(sp->d_err, 0, sizeof(int), s));
     }
     auto coarse_of = [&](const int32_t *bl, int n) {
         std::map<int64_t, int> m;  // ordered: deterministic coarse block order
@@ -1247,7 +1278,7 @@ lgf_status split_check(lgf_plan *p, cudaStream_t s)
     LGF_CUDA_TRY(cudaStreamSynchronize(s));
     if (h) {
         LGF_CUDA_TRY(cudaMemsetAsync(sp->d_err, 0, sizeof(int), s));
-        set_error("a tensor-core wait of the far-field interpolation gave up (its result is not valid)");
+        set_error("a bounded device wait of the split solve gave up (its result is not valid)");
         return LGF_ERR_TIMEOUT;
     }
     return LGF_OK;
@@ -1263,12 +1294,12 @@ static lgf_status launch_near_mac(const SplitPlan *sp, bool runs, cudaStream_t s
                                      (size_t)(sp->noff + 1) * CH * sizeof(float2), s, (const float2 *)sp->d_W,
                                      sp->noff, (const float2 *)sp->d_S, sp->nsrc, (const int4 *)sp->d_run_tgt,
                                      (const int *)sp->d_run_row, (const int4 *)sp->d_rows, sp->nruns, sp->ndst,
-                                     sp->d_U));
+                                     sp->d_U, sp->d_err));
     else
         LGF_CUDA_TRY(launch_pdl_smem(k_near_mac, dim3(NCHUNK, (sp->ndst + 63) / 64, nc), dim3(256),
                                      (size_t)sp->noff * CH * sizeof(float2), s, (const float2 *)sp->d_W, sp->noff,
                                      (const float2 *)sp->d_S, sp->nsrc, (const int *)sp->d_off,
-                                     (const int2 *)sp->d_pairs, sp->ndst, sp->d_U));
+                                     (const int2 *)sp->d_pairs, sp->ndst, sp->d_U, sp->d_err));
     return LGF_OK;
 }
 

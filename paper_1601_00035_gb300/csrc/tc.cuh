@@ -97,6 +97,24 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, int max
     return false;
 }
 
+// make an mbarrier's initialisation visible to the asynchronous (bulk-copy) proxy
+__device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// arrive on the mbarrier and announce `bytes` of bulk-copy transactions for its current phase
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// bulk copy (the untiled TMA form) of `bytes` from global memory to shared memory; both
+// addresses 16-byte aligned, bytes a multiple of 16; completes as transactions on mbar
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 // make this thread's generic-proxy shared-memory writes visible to the tensor cores
