@@ -15,13 +15,21 @@ using fft::Plan;
 
 // Lines per block: y/z passes run LS consecutive kx lines (line-fast thread
 // mapping, coalesced rows of kx); x passes run whole rows (lane-fast mapping).
-// (FP64 tiles are half as wide so that the static shared memory stays < 48 KB.)
-// largest power-of-two line count <= want whose exchange buffer and twiddles fit in 44 KB
+// (FP64 tiles are half as wide.)
+// Shared-memory budget of a pass's exchange buffer and twiddles: 44 KB, and 100 KB from
+// length 432 on (static shared memory beyond 48 KB compiles for this architecture).  On the
+// 256^3 ring's step the larger budget, which gives the 432-point y and x passes 16 and 21
+// lines per block instead of 8 and 10, took 1.611 ms against 1.644 ms; applied to every
+// length it slowed the 64-solve ragged batch (1.806 against 1.763 ms: its 96- and 192-point
+// passes went to 64 and 32 lines per block).
+template <int N>
+constexpr size_t smem_budget() { return (N >= 432 ? 100 : 44) * 1024; }
+// largest line count <= want (halving) whose exchange buffer and twiddles fit in the budget
 template <int N, typename T>
 constexpr int lines_fit(int want, int pad)
 {
     int ls = want;
-    while (ls > 1 && (size_t)N * (ls + pad) * sizeof(cx<T>) + fft::tw_size<N>() * sizeof(cx<T>) > 44 * 1024) ls /= 2;
+    while (ls > 1 && (size_t)N * (ls + pad) * sizeof(cx<T>) + fft::tw_size<N>() * sizeof(cx<T>) > smem_budget<N>()) ls /= 2;
     return ls;
 }
 template <int N, typename T>
@@ -40,9 +48,9 @@ struct TileY {
     }
     static constexpr int minb(int mode) { return 65536 / (threads * cap(mode)) > 0 ? 65536 / (threads * cap(mode)) : 1; }
     // the z pass's spectrum columns fit beside the exchange buffer and twiddles
-    // in the 48 KB of static shared memory
+    // in the shared-memory budget
     static constexpr bool slab_fits = (size_t)N * LSP * sizeof(cx<T>) + fft::tw_size<N>() * sizeof(cx<T>) +
-                                          (size_t)(N / 2 + 1) * LS * sizeof(T) <= 48 * 1024;
+                                          (size_t)(N / 2 + 1) * LS * sizeof(T) <= smem_budget<N>() + 4 * 1024;
 };
 template <int N, typename T>
 struct TileX {
