@@ -334,12 +334,14 @@ __global__ void __launch_bounds__(TileY<N, T>::threads, TileY<N, T>::minb(MODE))
 template <int N>
 struct TileZ2 {
     static constexpr int G = Plan<N>::G;
-    // line pairs per block: 24-element lanes take 64-thread blocks (60 for G = 12),
-    // so that the exchange rows (N x LS x 16 bytes) stay within the static
-    // shared memory
-    static constexpr int LS = (Plan<N>::E > 16 ? 64 : 128) / G;
+    // line pairs per block: 24-element lanes take 64-thread blocks; G = 12 (288) takes 8
+    // pairs, 96 threads and 55 KB of shared memory, so that an 8-thread phase of a 128-bit
+    // access covers one 128-byte exchange row (the pass 138 -> 121 us on the 256^3 step
+    // against 5 pairs; 6 pairs: 196 us; 4 pairs: 146 us)
+    static constexpr int LS = G == 12 ? 8 : (Plan<N>::E > 16 ? 64 : 128) / G;
     static constexpr int threads = LS * G;
-    static constexpr int minb = Plan<N>::E > 16 ? 6 : 4;  // 170 / 128 registers per thread
+    // 170 / 128 registers per thread (160 for G = 12)
+    static constexpr int minb = G == 12 ? 4 : (Plan<N>::E > 16 ? 6 : 4);
 };
 
 template <int N>
