@@ -147,11 +147,13 @@ __global__ void __launch_bounds__(B *B) k_op(const float *__restrict__ in, float
 // one-cell halo in x and y lives in a ring of three slots, and plane z' of
 // e = C f at in-plane positions -1 .. B-1 in a ring of two, so every stencil
 // value is one shared-memory read.  Same arithmetic as eq. opr_def_nonlin.
+// rv (optional): also writes rv = u + out (the first stage's r = u + g without a separate
+// linear combination; the same single FP32 addition).
 template <int B>
 __global__ void __launch_bounds__(B *B) k_nonlinear(const float *__restrict__ in, float *__restrict__ out,
                                                     const int *__restrict__ nbr27,
                                                     const unsigned char *__restrict__ out_keep, float inv_dx,
-                                                    float coef, float u0, float u1, float u2)
+                                                    float coef, float u0, float u1, float u2, float *__restrict__ rv)
 {
     constexpr int H = B + 2;  // f plane edge (halo -1 .. B)
     constexpr int HE = B + 1; // e plane edge (-1 .. B-1)
@@ -167,7 +169,11 @@ __global__ void __launch_bounds__(B *B) k_nonlinear(const float *__restrict__ in
     if (!keep) {
         for (int z = z0; z < z1; z++)
 #pragma unroll
-            for (int q = 0; q < 3; q++) out[((size_t)(blk * 3 + q) * B + z) * B * B + y * B + x] = 0.f;
+            for (int q = 0; q < 3; q++) {
+                const size_t o = ((size_t)(blk * 3 + q) * B + z) * B * B + y * B + x;
+                out[o] = 0.f;
+                if (rv) rv[o] = __ldg(in + o);
+            }
         return;
     }
     if (threadIdx.x < 27) nb[threadIdx.x] = nbr27[blk * 27 + threadIdx.x];
@@ -244,7 +250,10 @@ __global__ void __launch_bounds__(B *B) k_nonlinear(const float *__restrict__ in
                 const int bx = x + m * o[r][0], by = y + m * o[r][1], bz = z + m * o[r][2];
                 v -= Ev(s2, bx, by, bz) * (F(r, bx, by, bz) + F(r, bx + o[q][0], by + o[q][1], bz + o[q][2]));
             }
-            out[((size_t)(blk * 3 + q) * B + z) * B * B + y * B + x] = v * 0.25f * coef;
+            const size_t o = ((size_t)(blk * 3 + q) * B + z) * B * B + y * B + x;
+            const float gv = v * 0.25f * coef;
+            out[o] = gv;
+            if (rv) rv[o] = __ldg(in + o) + gv;
         }
         __syncthreads();  // plane z - 1 of f and of e are no longer read
         if (z + 2 <= z1) {
@@ -482,15 +491,19 @@ __global__ void k_gather_blocks(const float *__restrict__ in, float *__restrict_
 }  // namespace
 
 lgf_status op_launch(int op, int B, int nblk, const int *d_nbr27, const unsigned char *d_keep, const float *in,
-                     float *out, double dx, double coef, const double uinf[3], cudaStream_t s)
+                     float *out, double dx, double coef, const double uinf[3], cudaStream_t s, float *out2)
 {
+    if (out2 && op != 4) {
+        set_error("a second output is only for the nonlinear term");
+        return LGF_ERR_ARG;
+    }
     const float inv_dx = (float)(1.0 / dx);
     const float u0 = uinf ? (float)uinf[0] : 0.f, u1 = uinf ? (float)uinf[1] : 0.f, u2 = uinf ? (float)uinf[2] : 0.f;
     const float cf = (float)coef;
 #define LGF_OPCASE(BB, OPV)                                                                                     \
     if constexpr (OPV == 4)                                                                                     \
         k_nonlinear<BB><<<nblk * (BB >= 16 ? 2 : 1), BB * BB, 0, s>>>(in, out, d_nbr27, d_keep, inv_dx, cf, u0,  \
-                                                                       u1, u2);                                \
+                                                                       u1, u2, out2);                          \
     else                                                                                                        \
         k_op<BB, OPV><<<nblk, BB * BB, 0, s>>>(in, out, d_nbr27, d_keep, inv_dx, cf, u0, u1, u2);
 #define LGF_OPSWITCH(BB)                                                                                        \

@@ -122,8 +122,9 @@ namespace lgf {
 lgf_status ifactor_apply_io(lgf_plan *p, const IfIO &io, float *y, cudaStream_t s);
 
 // local operators (ops.cu): op 0 curl, 1 curl^T, 2 G^T, 3 G, 4 nonlinear
+// out2 (op 4 only, optional): also out2 = in + out
 lgf_status op_launch(int op, int B, int nblk, const int *d_nbr27, const unsigned char *d_keep, const float *in,
-                     float *out, double dx, double coef, const double uinf[3], cudaStream_t s);
+                     float *out, double dx, double coef, const double uinf[3], cudaStream_t s, float *out2 = nullptr);
 lgf_status lincomb_launch(float *out, int64_t n, const float *x0, double c0, const float *x1, double c1,
                           const float *x2, double c2, const float *x3, double c3, cudaStream_t s);
 lgf_status gather_launch(const float *in, float *out, const int *d_idx, int n, int block_floats, cudaStream_t s);
