@@ -432,10 +432,14 @@ __global__ void __launch_bounds__(256) k_near_inv(const float2 *__restrict__ U, 
 // 8b - 4 + l) is in constant memory.
 // ---------------------------------------------------------------------------
 __constant__ float c_P[BN * W];
+// threads per block of the two SIMT kernels: one thread block per (block, component), whose
+// three passes are short loops over the block's points; 512 threads keep every block of a
+// few-hundred-block set resident at once
+constexpr int FAR_THREADS = 512;
 
 // Q_b[lz][ly][lx] = sum_i P[iz][lz] P[iy][ly] P[ix][lx] f_b[iz][iy][ix] (a W^3 window), per
 // (source block, component)
-__global__ void __launch_bounds__(256) k_far_anterp(const float *__restrict__ src, int ncomp, int c0,
+__global__ void __launch_bounds__(FAR_THREADS) k_far_anterp(const float *__restrict__ src, int ncomp, int c0,
                                                      float *__restrict__ Q, int ncq)
 {
     __shared__ float A[W3];
@@ -443,12 +447,12 @@ __global__ void __launch_bounds__(256) k_far_anterp(const float *__restrict__ sr
     __shared__ float sP[BN * W];
     const int b = blockIdx.x, c = blockIdx.y, t = threadIdx.x;
     const float *f = src + ((size_t)b * ncomp + c0 + c) * (BN * BN * BN);
-    for (int i = t; i < BN * W; i += 256) sP[i] = c_P[i];
+    for (int i = t; i < BN * W; i += FAR_THREADS) sP[i] = c_P[i];
     pdl_wait();
-    for (int i = t; i < BN * BN * BN; i += 256) A[i] = f[i];
+    for (int i = t; i < BN * BN * BN; i += FAR_THREADS) A[i] = f[i];
     __syncthreads();
     // x: T[z][y][lx] = sum_x P[x][lx] A[z][y][x]      (16 x 16 x W)
-    for (int i = t; i < BN * BN * W; i += 256) {
+    for (int i = t; i < BN * BN * W; i += FAR_THREADS) {
         const int lx = i % W, row = i / W;
         float acc = 0.f;
 #pragma unroll
@@ -457,7 +461,7 @@ __global__ void __launch_bounds__(256) k_far_anterp(const float *__restrict__ sr
     }
     __syncthreads();
     // y: A[z][ly][lx] = sum_y P[y][ly] T[z][y][lx]    (16 x W x W)
-    for (int i = t; i < BN * W * W; i += 256) {
+    for (int i = t; i < BN * W * W; i += FAR_THREADS) {
         const int lx = i % W, ly = (i / W) % W, z = i / (W * W);
         float acc = 0.f;
 #pragma unroll
@@ -467,7 +471,7 @@ __global__ void __launch_bounds__(256) k_far_anterp(const float *__restrict__ sr
     __syncthreads();
     // z: Q[lz][ly][lx] = sum_z P[z][lz] A[z][ly][lx]  (W^3)
     float *out = Q + ((size_t)b * ncq + c) * W3;
-    for (int i = t; i < W3; i += 256) {
+    for (int i = t; i < W3; i += FAR_THREADS) {
         const int r = i % (W * W), lz = i / (W * W);
         float acc = 0.f;
 #pragma unroll
@@ -480,15 +484,20 @@ __global__ void __launch_bounds__(256) k_far_anterp(const float *__restrict__ sr
 // Coarse charges q on coarse block C: node n = 16 C + l receives Q_b[n - (8 b - 4)] from
 // each source block b whose window holds n (up to three per axis, fixed order).
 // flut: dense lookup of the fine source blocks over [fmin, fmin + fext).
+constexpr int GATHER_PARTS = 8;
 __global__ void __launch_bounds__(256) k_far_gather(const float *__restrict__ Q, int ncq,
                                                      const int *__restrict__ ccoords, const int *__restrict__ flut,
                                                      int3 fmin, int3 fext, float *__restrict__ q)
 {
-    const int C = blockIdx.x, c = blockIdx.y;
+    // GATHER_PARTS thread blocks per coarse block (a slab of 16 / GATHER_PARTS planes each):
+    // the coarse source blocks are few (hundreds), so one thread block each would leave
+    // most SMs idle
+    const int C = blockIdx.x / GATHER_PARTS, part = blockIdx.x % GATHER_PARTS, c = blockIdx.y;
     const int Cx = ccoords[3 * C], Cy = ccoords[3 * C + 1], Cz = ccoords[3 * C + 2];
     float *out = q + ((size_t)C * ncq + c) * (BN * BN * BN);
     pdl_wait();
-    for (int i = threadIdx.x; i < BN * BN * BN; i += 256) {
+    constexpr int PART = BN * BN * BN / GATHER_PARTS;
+    for (int i = part * PART + threadIdx.x; i < (part + 1) * PART; i += 256) {
         const int nx = 16 * Cx + i % BN, ny = 16 * Cy + (i / BN) % BN, nz = 16 * Cz + i / (BN * BN);
         const int bx1 = floordiv(nx + WOFF, 8), by1 = floordiv(ny + WOFF, 8), bz1 = floordiv(nz + WOFF, 8);
         float acc = 0.f;
@@ -514,7 +523,7 @@ __global__ void __launch_bounds__(256) k_far_gather(const float *__restrict__ Q,
 
 // dst_b += mul * sum_l P[iz][lz] P[iy][ly] P[ix][lx] v(8 b - 4 + l), per (target block, component);
 // v on coarse blocks through clut (dense lookup over [cmin, cmin + cext)), ncv components.
-__global__ void __launch_bounds__(256) k_far_interp(const float *__restrict__ v, int ncv, const int *__restrict__ tcoords,
+__global__ void __launch_bounds__(FAR_THREADS) k_far_interp(const float *__restrict__ v, int ncv, const int *__restrict__ tcoords,
                                                      const int *__restrict__ clut, int3 cmin, int3 cext,
                                                      float *__restrict__ dst, int ncomp, int c0, float mul)
 {
@@ -523,9 +532,9 @@ __global__ void __launch_bounds__(256) k_far_interp(const float *__restrict__ v,
     __shared__ float sP[BN * W];
     const int b = blockIdx.x, c = blockIdx.y, t = threadIdx.x;
     const int bx = tcoords[3 * b], by = tcoords[3 * b + 1], bz = tcoords[3 * b + 2];
-    for (int i = t; i < BN * W; i += 256) sP[i] = c_P[i];
+    for (int i = t; i < BN * W; i += FAR_THREADS) sP[i] = c_P[i];
     pdl_wait();
-    for (int i = t; i < W3; i += 256) {
+    for (int i = t; i < W3; i += FAR_THREADS) {
         const int nx = 8 * bx - WOFF + i % W, ny = 8 * by - WOFF + (i / W) % W, nz = 8 * bz - WOFF + i / (W * W);
         const int Cx = floordiv(nx, 16) - cmin.x, Cy = floordiv(ny, 16) - cmin.y, Cz = floordiv(nz, 16) - cmin.z;
         float val = 0.f;
@@ -540,7 +549,7 @@ __global__ void __launch_bounds__(256) k_far_interp(const float *__restrict__ v,
     }
     __syncthreads();
     // x: T[lz][ly][ix] = sum_lx P[ix][lx] A[lz][ly][lx]   (W x W x 16)
-    for (int i = t; i < W * W * BN; i += 256) {
+    for (int i = t; i < W * W * BN; i += FAR_THREADS) {
         const int ix = i % BN, row = i / BN;
         float acc = 0.f;
 #pragma unroll
@@ -548,7 +557,7 @@ __global__ void __launch_bounds__(256) k_far_interp(const float *__restrict__ v,
         T[i] = acc;
     }
     __syncthreads();
-    for (int i = t; i < W * BN * BN; i += 256) {  // y: A[lz][iy][ix]   (W x 16 x 16)
+    for (int i = t; i < W * BN * BN; i += FAR_THREADS) {  // y: A[lz][iy][ix]   (W x 16 x 16)
         const int ix = i % BN, iy = (i / BN) % BN, lz = i / (BN * BN);
         float acc = 0.f;
 #pragma unroll
@@ -557,7 +566,7 @@ __global__ void __launch_bounds__(256) k_far_interp(const float *__restrict__ v,
     }
     __syncthreads();
     float *o = dst + ((size_t)b * ncomp + c0 + c) * (BN * BN * BN);
-    for (int i = t; i < BN * BN * BN; i += 256) {  // z, added to the near field
+    for (int i = t; i < BN * BN * BN; i += FAR_THREADS) {  // z, added to the near field
         const int r = i % (BN * BN), iz = i / (BN * BN);
         float acc = 0.f;
 #pragma unroll
@@ -1373,7 +1382,7 @@ lgf_status run_split(lgf_plan *p, const float *src, float *dst, cudaStream_t s, 
     // far field
     if (P) prof->begin(fs);
     if (!sp->far_tensor_cores) {
-        k_far_anterp<<<dim3(sp->nsrc, nc), 256, 0, fs>>>(src, nc, 0, sp->d_Q, nc);
+        k_far_anterp<<<dim3(sp->nsrc, nc), FAR_THREADS, 0, fs>>>(src, nc, 0, sp->d_Q, nc);
         LGF_LAUNCH_CHECK("k_far_anterp");
     } else {
         LGF_CUDA_TRY(launch_pdl_smem(k_far_anterp_tc, dim3(sp->nsrc, nc), dim3(TC_THREADS), sizeof(TcSmem<16>), fs, src,
@@ -1381,7 +1390,7 @@ lgf_status run_split(lgf_plan *p, const float *src, float *dst, cudaStream_t s, 
     }
     if (P) prof->end("far_anterp", fs);
     if (P) prof->begin(fs);
-    k_far_gather<<<dim3(sp->ncsrc, nc), 256, 0, fs>>>(sp->d_Q, nc, sp->d_ccoords, sp->d_flut, sp->fmin, sp->fext,
+    k_far_gather<<<dim3(sp->ncsrc * GATHER_PARTS, nc), 256, 0, fs>>>(sp->d_Q, nc, sp->d_ccoords, sp->d_flut, sp->fmin, sp->fext,
                                                       sp->d_q);
     LGF_LAUNCH_CHECK("k_far_gather");
     if (P) prof->end("far_gather", fs);
@@ -1407,7 +1416,7 @@ lgf_status run_split(lgf_plan *p, const float *src, float *dst, cudaStream_t s, 
     if (!P) LGF_CUDA_TRY(cudaStreamWaitEvent(s, sp->ev_far, 0));
     if (P) prof->begin(s);
     if (!sp->far_tensor_cores) {
-        k_far_interp<<<dim3(sp->ndst, nc), 256, 0, s>>>(sp->d_v, nc, sp->d_tcoords, sp->d_clut, sp->cmin, sp->cext, dst,
+        k_far_interp<<<dim3(sp->ndst, nc), FAR_THREADS, 0, s>>>(sp->d_v, nc, sp->d_tcoords, sp->d_clut, sp->cmin, sp->cext, dst,
                                                         nc, 0, mul_far);
         LGF_LAUNCH_CHECK("k_far_interp");
     } else {
