@@ -225,7 +225,7 @@ struct SplitPlan {
     uint32_t *d_Ba = nullptr, *d_Bi = nullptr;  // tensor-core B operands (TF32 hi, lo)
     int *d_err = nullptr;                       // set by a tensor-core wait that gave up
     cudaStream_t far_stream = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_far = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_far = nullptr, ev_src = nullptr;
 };
 void free_split(SplitPlan *sp);
 lgf_status plan_split(lgf_plan *p, const lgf_solve_desc &d, double alpha, int far_precision, int near_form,

@@ -363,8 +363,9 @@ __global__ void __launch_bounds__(256) k_near_mac_runs(const float2 *__restrict_
 }
 
 // Inverse: one thread block per (target block, component): z, y (keeping the first
-// 16 outputs of each), then C2R in x with two rows per complex line; writes
-// dst = mul * result (the target window of the circular convolution).
+// 16 outputs of each), then C2R in x with two rows per complex line; adds
+// mul * result (the target window of the circular convolution) to dst, which holds the
+// far field.
 __global__ void __launch_bounds__(256) k_near_inv(const float2 *__restrict__ U, int ndst, float *__restrict__ dst,
                                                    int ncomp, int c0, float mul)
 {
@@ -419,9 +420,12 @@ __global__ void __launch_bounds__(256) k_near_inv(const float2 *__restrict__ U, 
         float4 *w0 = reinterpret_cast<float4 *>(o + (2 * t) * BN);
         float4 *w1 = reinterpret_cast<float4 *>(o + (2 * t + 1) * BN);
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
-            w0[i] = make_float4(mul * a[4 * i].x, mul * a[4 * i + 1].x, mul * a[4 * i + 2].x, mul * a[4 * i + 3].x);
-            w1[i] = make_float4(mul * a[4 * i].y, mul * a[4 * i + 1].y, mul * a[4 * i + 2].y, mul * a[4 * i + 3].y);
+        for (int i = 0; i < 4; i++) {  // added to the far field the interpolation wrote
+            const float4 f0 = w0[i], f1 = w1[i];
+            w0[i] = make_float4(f0.x + mul * a[4 * i].x, f0.y + mul * a[4 * i + 1].x, f0.z + mul * a[4 * i + 2].x,
+                                f0.w + mul * a[4 * i + 3].x);
+            w1[i] = make_float4(f1.x + mul * a[4 * i].y, f1.y + mul * a[4 * i + 1].y, f1.z + mul * a[4 * i + 2].y,
+                                f1.w + mul * a[4 * i + 3].y);
         }
     }
 }
@@ -521,7 +525,7 @@ __global__ void __launch_bounds__(256) k_far_gather(const float *__restrict__ Q,
     pdl_trigger();
 }
 
-// dst_b += mul * sum_l P[iz][lz] P[iy][ly] P[ix][lx] v(8 b - 4 + l), per (target block, component);
+// dst_b = mul * sum_l P[iz][lz] P[iy][ly] P[ix][lx] v(8 b - 4 + l), per (target block, component);
 // v on coarse blocks through clut (dense lookup over [cmin, cmin + cext)), ncv components.
 __global__ void __launch_bounds__(FAR_THREADS) k_far_interp(const float *__restrict__ v, int ncv, const int *__restrict__ tcoords,
                                                      const int *__restrict__ clut, int3 cmin, int3 cext,
@@ -566,12 +570,12 @@ __global__ void __launch_bounds__(FAR_THREADS) k_far_interp(const float *__restr
     }
     __syncthreads();
     float *o = dst + ((size_t)b * ncomp + c0 + c) * (BN * BN * BN);
-    for (int i = t; i < BN * BN * BN; i += FAR_THREADS) {  // z, added to the near field
+    for (int i = t; i < BN * BN * BN; i += FAR_THREADS) {  // z: the far field, to which the near field is added
         const int r = i % (BN * BN), iz = i / (BN * BN);
         float acc = 0.f;
 #pragma unroll
         for (int l = 0; l < W; l++) acc = fmaf(sP[iz * W + l], A[l * BN * BN + r], acc);
-        o[i] += mul * acc;
+        o[i] = mul * acc;
     }
     pdl_trigger();
 }
@@ -783,12 +787,12 @@ __global__ void __launch_bounds__(TC_THREADS) k_far_interp_tc(const float *__res
     }
     tc::fence_before_sync();
     if (ok) ok = tc_pass<24, 16>(sm, 2, ph = 0);
-    // D3 rows (iy, ix), cols iz: added to the near field
+    // D3 rows (iy, ix), cols iz: the far field, to which the near field is added
     float *o = dst + ((size_t)b * ncomp + c0 + c) * (BN * BN * BN);
     for (int mt = 0; mt < 2 && ok; mt++) {
         const int r = mt * 128 + t;
         tc_row<16>(sm.tmem_base, mt, v);
-        for (int i = 0; i < BN; i++) o[i * BN * BN + r] += mul * v[i];
+        for (int i = 0; i < BN; i++) o[i * BN * BN + r] = mul * v[i];
     }
     if (!ok && t == 0) atomicExch(err, 1);
     tc_teardown<24>(sm, ok, ph);
@@ -924,6 +928,7 @@ void free_split(SplitPlan *sp)
     if (sp->far_stream) cudaStreamDestroy(sp->far_stream);
     if (sp->ev_fork) cudaEventDestroy(sp->ev_fork);
     if (sp->ev_far) cudaEventDestroy(sp->ev_far);
+    if (sp->ev_src) cudaEventDestroy(sp->ev_src);
     delete sp;
 }
 
@@ -1274,6 +1279,7 @@ static lgf_status plan_split_level(lgf_plan *p, const lgf_solve_desc &d, double 
     LGF_CUDA_TRY(cudaStreamCreateWithFlags(&sp->far_stream, cudaStreamNonBlocking));
     LGF_CUDA_TRY(cudaEventCreateWithFlags(&sp->ev_fork, cudaEventDisableTiming));
     LGF_CUDA_TRY(cudaEventCreateWithFlags(&sp->ev_far, cudaEventDisableTiming));
+    LGF_CUDA_TRY(cudaEventCreateWithFlags(&sp->ev_src, cudaEventDisableTiming));
     static bool attr_done[64] = {false};
     if (p->device >= 0 && p->device < 64 && !attr_done[p->device]) {
         LGF_CUDA_TRY(cudaFuncSetAttribute(k_near_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NEAR_SMEM));
@@ -1288,10 +1294,7 @@ static lgf_status plan_split_level(lgf_plan *p, const lgf_solve_desc &d, double 
     return LGF_OK;
 }
 
-// One split solve: near field on stream s, far field (anterpolation, coarse charges,
-// coarse convolution) on the plan's far stream, joined before the interpolation
-// adds the far field to the near result.  prof: per-kernel event timing (then all
-// launches go to s, one after another).
+// The status of the split solve's bounded device waits (synchronises s).
 lgf_status split_check(lgf_plan *p, cudaStream_t s)
 {
     SplitPlan *sp = p->split;
@@ -1367,8 +1370,14 @@ static lgf_status choose_near_mac(SplitPlan *sp, int near_form, cudaStream_t s)
     return LGF_OK;
 }
 
+// One split solve.  prof: per-kernel event timing (then all launches go to s, one after
+// another).
 lgf_status run_split(lgf_plan *p, const float *src, float *dst, cudaStream_t s, Profiler *prof)
 {
+    // The far field runs on its own stream beside the near field and ends with the
+    // interpolation writing dst = u_far; the near field's inverse then adds u_near, so only
+    // that last kernel waits for both.  The interpolation first waits for the near field's
+    // forward transform, so that dst may share memory with src.
     SplitPlan *sp = p->split;
     const bool P = prof && prof->on;
     const int nc = sp->ncomp;
@@ -1379,7 +1388,7 @@ lgf_status run_split(lgf_plan *p, const float *src, float *dst, cudaStream_t s, 
         LGF_CUDA_TRY(cudaEventRecord(sp->ev_fork, s));
         LGF_CUDA_TRY(cudaStreamWaitEvent(fs, sp->ev_fork, 0));
     }
-    // far field
+    // far field: anterpolation, coarse charges, coarse convolution
     if (P) prof->begin(fs);
     if (!sp->far_tensor_cores) {
         k_far_anterp<<<dim3(sp->nsrc, nc), FAR_THREADS, 0, fs>>>(src, nc, 0, sp->d_Q, nc);
@@ -1390,8 +1399,8 @@ lgf_status run_split(lgf_plan *p, const float *src, float *dst, cudaStream_t s, 
     }
     if (P) prof->end("far_anterp", fs);
     if (P) prof->begin(fs);
-    k_far_gather<<<dim3(sp->ncsrc * GATHER_PARTS, nc), 256, 0, fs>>>(sp->d_Q, nc, sp->d_ccoords, sp->d_flut, sp->fmin, sp->fext,
-                                                      sp->d_q);
+    k_far_gather<<<dim3(sp->ncsrc * GATHER_PARTS, nc), 256, 0, fs>>>(sp->d_Q, nc, sp->d_ccoords, sp->d_flut, sp->fmin,
+                                                                     sp->fext, sp->d_q);
     LGF_LAUNCH_CHECK("k_far_gather");
     if (P) prof->end("far_gather", fs);
     {
@@ -1401,30 +1410,36 @@ lgf_status run_split(lgf_plan *p, const float *src, float *dst, cudaStream_t s, 
         LGF_TRY(lgf_conv_execute(sp->coarse, cs, cd, (void *)fs));
         if (P) prof->end("far_coarse_conv", fs);
     }
-    if (!P) LGF_CUDA_TRY(cudaEventRecord(sp->ev_far, fs));
-    // near field
+    // near field: forward transforms of the source blocks, multiply-accumulate
     if (P) prof->begin(s);
     LGF_CUDA_TRY(launch_pdl_smem(k_near_fwd, dim3(sp->nsrc, nc), dim3(256), NEAR_SMEM, s, src, nc, 0, sp->nsrc, sp->d_S));
     if (P) prof->end("near_fwd", s);
+    if (!P) {
+        LGF_CUDA_TRY(cudaEventRecord(sp->ev_src, s));
+        LGF_CUDA_TRY(cudaStreamWaitEvent(fs, sp->ev_src, 0));
+    }
+    // far field: interpolation, dst = u_far
+    if (P) prof->begin(fs);
+    if (!sp->far_tensor_cores) {
+        k_far_interp<<<dim3(sp->ndst, nc), FAR_THREADS, 0, fs>>>(sp->d_v, nc, sp->d_tcoords, sp->d_clut, sp->cmin,
+                                                                 sp->cext, dst, nc, 0, mul_far);
+        LGF_LAUNCH_CHECK("k_far_interp");
+    } else {
+        LGF_CUDA_TRY(launch_pdl_smem(k_far_interp_tc, dim3(sp->ndst, nc), dim3(TC_THREADS), sizeof(TcSmem<24>), fs,
+                                     (const float *)sp->d_v, nc, (const int *)sp->d_tcoords, (const int *)sp->d_clut,
+                                     sp->cmin, sp->cext, dst, nc, 0, mul_far, (const uint32_t *)sp->d_Bi, sp->d_err));
+    }
+    if (P) prof->end("far_interp", fs);
+    if (!P) LGF_CUDA_TRY(cudaEventRecord(sp->ev_far, fs));
     if (P) prof->begin(s);
     LGF_TRY(launch_near_mac(sp, sp->mac_runs, s));
     if (P) prof->end("near_mac", s);
+    // near field: inverse transforms, dst += u_near
+    if (!P) LGF_CUDA_TRY(cudaStreamWaitEvent(s, sp->ev_far, 0));
     if (P) prof->begin(s);
     LGF_CUDA_TRY(launch_pdl_smem(k_near_inv, dim3(sp->ndst, nc), dim3(256), NEAR_SMEM, s, (const float2 *)sp->d_U,
                                  sp->ndst, dst, nc, 0, mul_near));
     if (P) prof->end("near_inv", s);
-    if (!P) LGF_CUDA_TRY(cudaStreamWaitEvent(s, sp->ev_far, 0));
-    if (P) prof->begin(s);
-    if (!sp->far_tensor_cores) {
-        k_far_interp<<<dim3(sp->ndst, nc), FAR_THREADS, 0, s>>>(sp->d_v, nc, sp->d_tcoords, sp->d_clut, sp->cmin, sp->cext, dst,
-                                                        nc, 0, mul_far);
-        LGF_LAUNCH_CHECK("k_far_interp");
-    } else {
-        LGF_CUDA_TRY(launch_pdl_smem(k_far_interp_tc, dim3(sp->ndst, nc), dim3(TC_THREADS), sizeof(TcSmem<24>), s,
-                                     (const float *)sp->d_v, nc, (const int *)sp->d_tcoords, (const int *)sp->d_clut,
-                                     sp->cmin, sp->cext, dst, nc, 0, mul_far, (const uint32_t *)sp->d_Bi, sp->d_err));
-    }
-    if (P) prof->end("far_interp", s);
     return LGF_OK;
 }
 
