@@ -103,10 +103,13 @@ typedef struct {
                            reduced-precision far field, held to 1e-5) */
     double split_alpha; /* method 1: the split time a in [1, 64]; 0 takes 20, which keeps G_near
                            within two blocks and the spacing-2 far field within 1e-6 */
-    int near_form;      /* method 1: the near-field multiply-accumulate: 0 = time both forms at
-                           plan time and keep the faster; 1 = one target per warp over its
+    int near_form;      /* method 1: the near-field multiply-accumulate: 0 = time the forms at
+                           plan time and keep the fastest; 1 = one target per warp over its
                            (offset, source) pairs; 2 = runs of 4 x-adjacent targets per warp
-                           (13 row loads per 20 multiply-adds, dense over each run) */
+                           (13 row loads per 20 multiply-adds, dense over each run); 3 = quads
+                           of 4 x 2 targets per warp (a source row serves two rows of targets:
+                           up to 18 row loads per 40 multiply-adds; needs all 125 near offsets,
+                           else the run form) */
     int reserved[1];    /* must be zero */
 } lgf_plan_opts;
 

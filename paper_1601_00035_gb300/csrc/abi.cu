@@ -882,7 +882,7 @@ lgf_status lgf_conv_plan(const lgf_table *t, const lgf_solve_desc *solves, int n
     LGF_CHECK_ARG(t != nullptr && solves != nullptr && n_solves >= 1, "lgf_conv_plan: bad table/solves/n_solves");
     if (opts) {
         LGF_CHECK_ARG(opts->reserved[0] == 0, "lgf_conv_plan: reserved option fields must be zero");
-        LGF_CHECK_ARG(opts->near_form >= 0 && opts->near_form <= 2, "lgf_conv_plan: near_form must be 0, 1 or 2");
+        LGF_CHECK_ARG(opts->near_form >= 0 && opts->near_form <= 3, "lgf_conv_plan: near_form must be 0, 1, 2 or 3");
         LGF_CHECK_ARG(opts->precision == 0 || opts->precision == 1, "lgf_conv_plan: precision must be 0 or 1");
         LGF_CHECK_ARG(opts->method >= 0 && opts->method <= 2, "lgf_conv_plan: method must be 0, 1 or 2");
         LGF_CHECK_ARG(opts->far_precision == 0 || opts->far_precision == 1,

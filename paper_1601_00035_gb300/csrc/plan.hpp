@@ -203,11 +203,19 @@ struct SplitPlan {
     // sources x0 - 2 .. x0 + 5 (int4 x 4: w0..w3 | w4 s0 s1 s2 | s3..s6 | s7)
     int levels = 1;              // split levels (1: the coarse convolution is a whole-box plan)
     int nruns = 0, nrows = 0;
-    bool mac_runs = false;       // the run form measured faster than the pair form at plan time
-    float mac_ms[2] = {-1.f, -1.f};  // plan-time times of the pair and run forms (ms per launch)
+    int mac_form = 0;            // the multiply-accumulate form kept: 0 pairs, 1 runs, 2 quads
+    float mac_ms[3] = {-1.f, -1.f, -1.f};  // plan-time times of the three forms (ms per launch; -1 not timed)
     int4 *d_run_tgt = nullptr;
     int *d_run_row = nullptr;
     int4 *d_rows = nullptr;
+    // quads of 4 x 2 target slots (x0 = 4 k, y0 = 2 l): targets [nquads][2] (int4, slot j * 4 + i,
+    // -1 = empty), row-steps [quad_row[r] .. quad_row[r+1]) of 3 int4 each (sources 0-3 | 4-7 |
+    // first window row of slot row 0 and of slot row 1, -1 = none); only with the 125 offsets
+    // in canonical order (nquads = 0 otherwise)
+    int nquads = 0, nqrows = 0;
+    int4 *d_quad_tgt = nullptr;
+    int *d_quad_row = nullptr;
+    int4 *d_qrows = nullptr;
     // far field
     int ncsrc = 0, ncdst = 0;
     struct lgf_table *far_table = nullptr;  // G_far at even offsets (coarse octant)

@@ -362,6 +362,88 @@ __global__ void __launch_bounds__(256) k_near_mac_runs(const float2 *__restrict_
     pdl_trigger();
 }
 
+// Quads of 4 x 2 target slots t_ij = (x0 + i, y0 + j, z), y0 even: a source row (y', z - oz)
+// serves slot row j = 0 with oy = y0 - y' and j = 1 with oy = y0 + 1 - y', so the 8 source rows
+// a row-step loads feed up to 40 complex multiply-adds (against 20 in the run form), with the
+// 5 window rows of each valid half read from shared memory.  The windows are the plan's 125
+// offsets in canonical order, (ox + 2) + 5 (oy + 2) + 25 (oz + 2); a row-step names the first
+// window row of each half (its ox = -2), or -1 where that half has no target.
+// Row-step entry: int4 sources 0-3, int4 sources 4-7, int4 (wa, wb, 0, 0).
+__global__ void __launch_bounds__(256) k_near_mac_quads(const float2 *__restrict__ W, int noff,
+                                                         const float2 *__restrict__ S, int nsrc,
+                                                         const int4 *__restrict__ quad_tgt,
+                                                         const int *__restrict__ quad_row,
+                                                         const int4 *__restrict__ qrows, int nquads, int ndst,
+                                                         float2 *__restrict__ U, int *err)
+{
+    extern __shared__ __align__(128) float2 Kc[];  // [noff][32]
+    __shared__ __align__(8) unsigned long long kbar;
+    const int chunk = blockIdx.x, c = blockIdx.z;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (!stage_windows(Kc, W + (size_t)chunk * noff * CH, noff, &kbar, err)) return;
+    pdl_wait();
+    const float2 *Sc = S + ((size_t)c * NCHUNK + chunk) * nsrc * CH;
+    float2 *Uc = U + ((size_t)c * NCHUNK + chunk) * ndst * CH;
+    const fft::f32x2 zero = fft::pk2(0.f, 0.f);
+    for (int r = blockIdx.y * 8 + warp; r < nquads; r += gridDim.y * 8) {
+        fft::f32x2 PA[4] = {zero, zero, zero, zero}, QA[4] = {zero, zero, zero, zero};
+        fft::f32x2 PB[4] = {zero, zero, zero, zero}, QB[4] = {zero, zero, zero, zero};
+        const int r0 = __ldg(quad_row + r), r1 = __ldg(quad_row + r + 1);
+        for (int q = r0; q < r1; q++) {
+            const int4 a = __ldg(qrows + 3 * q), b = __ldg(qrows + 3 * q + 1), m = __ldg(qrows + 3 * q + 2);
+            const int src[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+            fft::f32x2 sr[8], si[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const float2 v = src[k] >= 0 ? Sc[(size_t)src[k] * CH + lane] : make_float2(0.f, 0.f);
+                sr[k] = fft::bc2(v.x);
+                si[k] = fft::bc2(v.y);
+            }
+            if (m.x >= 0) {
+#pragma unroll
+                for (int o = 0; o < 5; o++) {  // ox = o - 2; source x0 + i - ox
+                    fft::f32x2 w;
+                    w.r = *(const unsigned long long *)(Kc + (m.x + o) * CH + lane);
+#pragma unroll
+                    for (int i = 0; i < 4; i++) {
+                        PA[i] = fft::fma(sr[i - o + 4], w, PA[i]);
+                        QA[i] = fft::fma(si[i - o + 4], w, QA[i]);
+                    }
+                }
+            }
+            if (m.y >= 0) {
+#pragma unroll
+                for (int o = 0; o < 5; o++) {
+                    fft::f32x2 w;
+                    w.r = *(const unsigned long long *)(Kc + (m.y + o) * CH + lane);
+#pragma unroll
+                    for (int i = 0; i < 4; i++) {
+                        PB[i] = fft::fma(sr[i - o + 4], w, PB[i]);
+                        QB[i] = fft::fma(si[i - o + 4], w, QB[i]);
+                    }
+                }
+            }
+        }
+        const int4 ta = __ldg(quad_tgt + 2 * r), tb = __ldg(quad_tgt + 2 * r + 1);
+        const int t8[8] = {ta.x, ta.y, ta.z, ta.w, tb.x, tb.y, tb.z, tb.w};
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            float pr, pi, qr, qi;
+            if (t8[i] >= 0) {
+                fft::unpk2(PA[i], pr, pi);
+                fft::unpk2(QA[i], qr, qi);
+                Uc[(size_t)t8[i] * CH + lane] = make_float2(pr - qi, pi + qr);
+            }
+            if (t8[4 + i] >= 0) {
+                fft::unpk2(PB[i], pr, pi);
+                fft::unpk2(QB[i], qr, qi);
+                Uc[(size_t)t8[4 + i] * CH + lane] = make_float2(pr - qi, pi + qr);
+            }
+        }
+    }
+    pdl_trigger();
+}
+
 // Inverse: one thread block per (target block, component): z, y (keeping the first
 // 16 outputs of each), then C2R in x with two rows per complex line; adds
 // mul * result (the target window of the circular convolution) to dst, which holds the
@@ -911,6 +993,9 @@ void free_split(SplitPlan *sp)
     cudaFree(sp->d_run_tgt);
     cudaFree(sp->d_run_row);
     cudaFree(sp->d_rows);
+    cudaFree(sp->d_quad_tgt);
+    cudaFree(sp->d_quad_row);
+    cudaFree(sp->d_qrows);
     cudaFree(sp->d_Q);
     cudaFree(sp->d_q);
     cudaFree(sp->d_v);
@@ -1134,8 +1219,77 @@ static lgf_status plan_split_level(lgf_plan *p, const lgf_solve_desc &d, double 
         LGF_TRY(upload_v(sp->d_run_tgt, rt, s));
         LGF_TRY(upload_v(sp->d_run_row, run_row, s));
         if (!rows.empty()) LGF_TRY(upload_v(sp->d_rows, rows, s));
+
+        // quads of 4 x 2 target slots (x0 a multiple of 4, y0 even), when the windows are the
+        // 125 offsets in canonical order: row-steps over (oz, y') with y' = y0 - 2 .. y0 + 3
+        bool canonical = sp->noff == 125;
+        for (int k = 0; canonical && k < 125; k++)
+            canonical = offs[3 * k] == k % 5 - 2 && offs[3 * k + 1] == (k / 5) % 5 - 2 && offs[3 * k + 2] == k / 25 - 2;
+        if (canonical) {
+            auto fdiv2 = [](int v) { return v >= 0 ? v / 2 : -((-v + 1) / 2); };
+            std::unordered_map<int64_t, int> qmap;
+            std::vector<int4> qt;  // 2 per quad
+            for (int t = 0; t < d.n_dst; t++) {
+                const int x = d.dst_blocks[3 * t], y = d.dst_blocks[3 * t + 1], z = d.dst_blocks[3 * t + 2];
+                const int x0 = 4 * fdiv4(x), y0 = 2 * fdiv2(y);
+                auto it = qmap.find(key3(x0, y0, z));
+                if (it == qmap.end()) {
+                    it = qmap.emplace(key3(x0, y0, z), (int)(qt.size() / 2)).first;
+                    qt.push_back(make_int4(-1, -1, -1, -1));
+                    qt.push_back(make_int4(-1, -1, -1, -1));
+                }
+                int *slot = &qt[2 * (size_t)it->second].x;
+                slot[(y - y0) * 4 + (x - x0)] = t;
+            }
+            const size_t nq = qt.size() / 2;
+            std::vector<int> quad_row(nq + 1, 0);
+            std::vector<int4> qrows;
+            for (size_t r = 0; r < nq; r++) {
+                quad_row[r] = (int)(qrows.size() / 3);
+                const int *slot = &qt[2 * r].x;
+                int t = -1;
+                bool rowj[2] = {false, false};
+                for (int k = 0; k < 8; k++)
+                    if (slot[k] >= 0) {
+                        t = slot[k];
+                        rowj[k / 4] = true;
+                    }
+                const int x0 = 4 * fdiv4(d.dst_blocks[3 * t]), y0 = 2 * fdiv2(d.dst_blocks[3 * t + 1]),
+                          z = d.dst_blocks[3 * t + 2];
+                for (int oz = -RNEAR; oz <= RNEAR; oz++)
+                    for (int yp = y0 - RNEAR; yp <= y0 + 1 + RNEAR; yp++) {
+                        int src[8];
+                        bool any = false;
+                        for (int k = 0; k < 8; k++) {
+                            auto it = smap.find(key3(x0 - 2 + k, yp, z - oz));
+                            src[k] = it == smap.end() ? -1 : it->second;
+                            any = any || src[k] >= 0;
+                        }
+                        if (!any) continue;
+                        int wb[2];
+                        for (int j = 0; j < 2; j++) {
+                            const int oy = y0 + j - yp;
+                            wb[j] = rowj[j] && oy >= -RNEAR && oy <= RNEAR ? 5 * (oy + 2) + 25 * (oz + 2) : -1;
+                        }
+                        if (wb[0] < 0 && wb[1] < 0) continue;
+                        qrows.push_back(make_int4(src[0], src[1], src[2], src[3]));
+                        qrows.push_back(make_int4(src[4], src[5], src[6], src[7]));
+                        qrows.push_back(make_int4(wb[0], wb[1], 0, 0));
+                    }
+            }
+            quad_row[nq] = (int)(qrows.size() / 3);
+            sp->nquads = (int)nq;
+            sp->nqrows = (int)(qrows.size() / 3);
+            LGF_TRY(dalloc_n(&sp->d_quad_tgt, qt.size(), bytes));
+            LGF_TRY(dalloc_n(&sp->d_quad_row, quad_row.size(), bytes));
+            LGF_TRY(dalloc_n(&sp->d_qrows, std::max<size_t>(qrows.size(), 3), bytes));
+            LGF_TRY(upload_v(sp->d_quad_tgt, qt, s));
+            LGF_TRY(upload_v(sp->d_quad_row, quad_row, s));
+            if (!qrows.empty()) LGF_TRY(upload_v(sp->d_qrows, qrows, s));
+        }
     }
     LGF_TRY(dalloc_n(&sp->d_S, (size_t)d.ncomp * NFREQ * d.n_src, bytes));
+
     LGF_TRY(dalloc_n(&sp->d_U, (size_t)d.ncomp * NFREQ * d.n_dst, bytes));
     LGF_TRY(choose_near_mac(sp, near_form, s));
 
@@ -1309,14 +1463,21 @@ lgf_status split_check(lgf_plan *p, cudaStream_t s)
     return LGF_OK;
 }
 
-// The near-field multiply-accumulate in the form the plan chose (runs: 4 x-adjacent
-// targets per warp, RUNS_PER_WARP runs per warp; pairs: one target per warp over its
-// (offset, source) list).
+// The near-field multiply-accumulate in the form the plan chose (0 pairs: one target per
+// warp over its (offset, source) list; 1 runs: 4 x-adjacent targets per warp; 2 quads: 4 x 2
+// targets per warp; RUNS_PER_WARP runs or quads per warp).
 constexpr int RUNS_PER_WARP = 2;
-static lgf_status launch_near_mac(const SplitPlan *sp, bool runs, cudaStream_t s)
+static lgf_status launch_near_mac(const SplitPlan *sp, int form, cudaStream_t s)
 {
     const int nc = sp->ncomp;
-    if (runs)
+    if (form == 2)
+        LGF_CUDA_TRY(launch_pdl_smem(k_near_mac_quads,
+                                     dim3(NCHUNK, (sp->nquads + 8 * RUNS_PER_WARP - 1) / (8 * RUNS_PER_WARP), nc),
+                                     dim3(256), (size_t)sp->noff * CH * sizeof(float2), s, (const float2 *)sp->d_W,
+                                     sp->noff, (const float2 *)sp->d_S, sp->nsrc, (const int4 *)sp->d_quad_tgt,
+                                     (const int *)sp->d_quad_row, (const int4 *)sp->d_qrows, sp->nquads, sp->ndst,
+                                     sp->d_U, sp->d_err));
+    else if (form == 1)
         LGF_CUDA_TRY(launch_pdl_smem(k_near_mac_runs,
                                      dim3(NCHUNK, (sp->nruns + 8 * RUNS_PER_WARP - 1) / (8 * RUNS_PER_WARP), nc),
                                      dim3(256), (size_t)(sp->noff + 1) * CH * sizeof(float2), s,
@@ -1331,14 +1492,16 @@ static lgf_status launch_near_mac(const SplitPlan *sp, bool runs, cudaStream_t s
     return LGF_OK;
 }
 
-// Plan time (near_form 0): time both forms (three launches each, on zeroed spectra) and
-// keep the faster; near_form 1 / 2 takes the pair / run form.
-// The run form does 20 multiply-adds per 13 row loads, dense over each run's rows, so it
-// wins where targets fill their runs (the 256^3 shell) and loses where they are sparse.
+// Plan time (near_form 0): time the forms (three launches each, on zeroed spectra) and keep
+// the fastest; near_form 1 / 2 / 3 takes the pair / run / quad form.  The run and quad forms
+// do their multiply-adds dense over each run's or quad's rows, so they win where targets fill
+// them (the 256^3 shell) and can lose where they are sparse.  The quad form needs the 125
+// offsets in canonical order (without them near_form 3 takes the run form).
 static lgf_status choose_near_mac(SplitPlan *sp, int near_form, cudaStream_t s)
 {
     if (near_form != 0) {  // the caller's choice
-        sp->mac_runs = near_form == 2;
+        sp->mac_form = near_form - 1;
+        if (sp->mac_form == 2 && sp->nquads == 0) sp->mac_form = 1;
         return LGF_OK;
     }
     LGF_CUDA_TRY(cudaMemsetAsync(sp->d_S, 0, (size_t)sp->ncomp * NFREQ * sp->nsrc * sizeof(float2), s));
@@ -1350,10 +1513,11 @@ static lgf_status choose_near_mac(SplitPlan *sp, int near_form, cudaStream_t s)
         return LGF_ERR_CUDA;
     }
     lgf_status st = LGF_OK;
-    for (int form = 0; form < 2 && st == LGF_OK; form++) {
-        st = launch_near_mac(sp, form == 1, s);  // warm-up
+    const int nforms = sp->nquads > 0 ? 3 : 2;
+    for (int form = 0; form < nforms && st == LGF_OK; form++) {
+        st = launch_near_mac(sp, form, s);  // warm-up
         if (st == LGF_OK && cudaEventRecord(e[0], s) != cudaSuccess) st = LGF_ERR_CUDA;
-        for (int k = 0; k < 3 && st == LGF_OK; k++) st = launch_near_mac(sp, form == 1, s);
+        for (int k = 0; k < 3 && st == LGF_OK; k++) st = launch_near_mac(sp, form, s);
         if (st == LGF_OK && cudaEventRecord(e[1], s) != cudaSuccess) st = LGF_ERR_CUDA;
         if (st == LGF_OK && cudaEventSynchronize(e[1]) != cudaSuccess) st = LGF_ERR_CUDA;
         float ms = 0.f;
@@ -1366,7 +1530,9 @@ static lgf_status choose_near_mac(SplitPlan *sp, int near_form, cudaStream_t s)
         if (st == LGF_ERR_CUDA) set_error("timing the near-field forms failed");
         return st;
     }
-    sp->mac_runs = sp->mac_ms[1] < sp->mac_ms[0];
+    sp->mac_form = 0;
+    for (int form = 1; form < nforms; form++)
+        if (sp->mac_ms[form] < sp->mac_ms[sp->mac_form]) sp->mac_form = form;
     return LGF_OK;
 }
 
@@ -1432,7 +1598,7 @@ lgf_status run_split(lgf_plan *p, const float *src, float *dst, cudaStream_t s, 
     if (P) prof->end("far_interp", fs);
     if (!P) LGF_CUDA_TRY(cudaEventRecord(sp->ev_far, fs));
     if (P) prof->begin(s);
-    LGF_TRY(launch_near_mac(sp, sp->mac_runs, s));
+    LGF_TRY(launch_near_mac(sp, sp->mac_form, s));
     if (P) prof->end("near_mac", s);
     // near field: inverse transforms, dst += u_near
     if (!P) LGF_CUDA_TRY(cudaStreamWaitEvent(s, sp->ev_far, 0));

@@ -41,12 +41,12 @@ def _dilate(blocks, r=1):
     return np.array(sorted(out), dtype=np.int32)
 
 
-@pytest.mark.parametrize("seed,near_form", [(0, 0), (1, 0), (0, 1), (0, 2)])
+@pytest.mark.parametrize("seed,near_form", [(0, 0), (1, 0), (0, 1), (0, 2), (0, 3), (1, 3)])
 def test_split_random_blocks_full(seed, near_form):
     """White-noise sources on a holed set of 16^3 blocks, targets on their two-block
     dilation (every near offset and the far field), two components, dx != 1, scale -1:
     every target point against the direct sum; with the near-field multiply-accumulate
-    chosen at plan time, and in each of its two forms (pairs, runs of 4 targets)."""
+    chosen at plan time, and in each of its forms (pairs, runs of 4 targets, quads of 4 x 2)."""
     lgf = built()
     B = 16
     rng = np.random.default_rng(200 + seed)
