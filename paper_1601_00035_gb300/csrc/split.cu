@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(256) k_near_mac_runs(const float2 *__restrict_
 // offsets in canonical order, (ox + 2) + 5 (oy + 2) + 25 (oz + 2); a row-step names the first
 // window row of each half (its ox = -2), or -1 where that half has no target.
 // Row-step entry: int4 sources 0-3, int4 sources 4-7, int4 (wa, wb, 0, 0).
-__global__ void __launch_bounds__(256) k_near_mac_quads(const float2 *__restrict__ W, int noff,
+__global__ void __launch_bounds__(256, 4) k_near_mac_quads(const float2 *__restrict__ W, int noff,
                                                          const float2 *__restrict__ S, int nsrc,
                                                          const int4 *__restrict__ quad_tgt,
                                                          const int *__restrict__ quad_row,
