@@ -216,7 +216,12 @@ class Solve:
 
 
 class Plan:
-    """lgf_conv_plan over one or more solves."""
+    """lgf_conv_plan over one or more solves.
+
+    The keyword options are the fields of lgf_plan_opts: method 0 (whole-box FFT convolution),
+    1 (block-sparse split solve) or 2 (plan both, keep the faster); split_alpha, far_precision
+    (0 CUDA cores, 1 tensor cores) and near_form (0 time the forms, 1 pairs, 2 runs of 4 targets,
+    3 quads of 4 x 2 targets) for the split solve."""
 
     def __init__(self, table: Table, solves: Sequence[Solve], use_graph: bool = False, stream=None,
                  precision: int = 0, method: int = 0, split_alpha: float = 0.0, far_precision: int = 0,
