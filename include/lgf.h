@@ -186,7 +186,10 @@ lgf_status lgf_plan_workspace_bytes(const lgf_plan *p, size_t *bytes);
  * plan with more than one (solve, component) unit runs the units on its own
  * worker streams, forked from and joined back to `stream` with events; with
  * opts->use_graph the whole sequence is captured once per set of buffers
- * and replayed. */
+ * and replayed.  dst[i] may be the buffer src[i] for a solve with ncomp = 1
+ * (every source value is read before the first result is written; the
+ * IF-HERK projection solves in place this way), and for a split plan; the
+ * buffers of different solves must not overlap. */
 lgf_status lgf_conv_execute(lgf_plan *p, const float *const *src, float *const *dst, void *stream);
 
 /* FP64 variant for plans built with opts->precision = 1: src[i], dst[i] are
